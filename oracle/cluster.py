@@ -1,0 +1,107 @@
+"""D2-clustering outer loop (oracle; test infrastructure only).
+
+Algorithm 1 (D2 Clustering) of Section 2 with the implementation choices of
+Section 5: centroids initialised from randomly chosen distributions reduced by
+Eq. (merge); the assignment step by exact W (Eq. primal); the update step by
+B-ADMM (Algorithm badmm) with a fixed iteration count, warm-starting the plan
+of every member whose label did not change.
+
+Readings where the paper is silent:
+  * random choices use SplitMix64 (Steele, Lea & Flood, OOPSLA 2014), seeded by
+    the caller: K distinct members with m_k >= m are drawn by a partial
+    Fisher-Yates shuffle of the eligible member ids (ascending), index
+    t + (next() mod (E - t)) at step t;
+  * argmin ties go to the lowest centroid index;
+  * an empty cluster keeps its previous centroid;
+  * a fixed number of rounds replaces the label-change stopping rule;
+  * obj_per_round[r] = (1/N) sum_k W^2(Q_{l_k}, P^(k)) at the assignment of
+    round r (the within-cluster variation of Section 2).
+"""
+import numpy as np
+
+from .badmm import badmm_barycenter
+from .merge import merge_reduce
+from .ot import w2_exact
+
+MASK64 = (1 << 64) - 1
+
+
+def splitmix64(state):
+    """One SplitMix64 step: returns (new_state, output), all arithmetic mod 2^64."""
+    state = (state + 0x9E3779B97F4A7C15) & MASK64
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+    return state, z ^ (z >> 31)
+
+
+def init_pick(sizes, K, m, seed):
+    """Ids of the K members whose merged supports seed the centroids."""
+    eligible = [k for k, s in enumerate(sizes) if s >= m]
+    if len(eligible) < K:
+        raise ValueError("fewer than K distributions have at least m support points")
+    state = seed & MASK64
+    E = len(eligible)
+    for t in range(K):
+        state, z = splitmix64(state)
+        j = t + int(z % (E - t))
+        eligible[t], eligible[j] = eligible[j], eligible[t]
+    return eligible[:K]
+
+
+def d2_assign(bags_list, cents):
+    """Assignment step of Algorithm 1: l_k = argmin_i W(Q_i, P_k) (ties -> lowest i).
+
+    bags_list: list of (y, w); cents: list of (x, w).  Returns (labels, dists, D)
+    with D the full N x K matrix of W^2.
+    """
+    N, K = len(bags_list), len(cents)
+    D = np.empty((N, K))
+    for k, (y, wy) in enumerate(bags_list):
+        for i, (x, wx) in enumerate(cents):
+            D[k, i] = w2_exact(x, wx, y, wy)
+    labels = np.argmin(D, axis=1)            # first minimum = lowest index
+    return labels, D[np.arange(N), labels], D
+
+
+def d2_cluster(bags_list, K, m, seed, rounds, *, rho0=2.0, T=100, tau=10, eps=1e-16,
+               rule="R1", labels_in=None):
+    """Algorithm 1 with the Section 5 choices.
+
+    labels_in: optional list of per-round label arrays; when given, round r uses
+    labels_in[r] instead of its own assignment (teacher forcing, so a single
+    near-tie flip does not make later rounds incomparable).
+    Returns dict(x (K,m,d), w (K,m), labels, obj_per_round, dists).
+    """
+    sizes = [y.shape[0] for y, _ in bags_list]
+    picks = init_pick(sizes, K, m, seed)
+    cents = [merge_reduce(bags_list[k][0], bags_list[k][1], m) for k in picks]
+    N = len(bags_list)
+    prev_labels = None
+    cache = [None] * N
+    objs, all_labels = [], []
+    for r in range(rounds):
+        labels, dists, _ = d2_assign(bags_list, cents)
+        objs.append(float(np.mean(dists)))
+        if labels_in is not None:
+            labels = np.asarray(labels_in[r])
+        all_labels.append(labels.copy())
+        new_cents = []
+        for i in range(K):
+            ids = [k for k in range(N) if labels[k] == i]
+            if not ids:
+                new_cents.append(cents[i])
+                continue
+            warm = [prev_labels is not None and prev_labels[k] == i and cache[k] is not None
+                    for k in ids]
+            res = badmm_barycenter([bags_list[k] for k in ids], cents[i][0], cents[i][1],
+                                   rho0=rho0, T=T, tau=tau, eps=eps, rule=rule,
+                                   plan0=[cache[k] for k in ids], warm=warm)
+            for t, k in enumerate(ids):
+                cache[k] = res["P2"][t]
+            new_cents.append((res["x"], res["w"]))
+        cents = new_cents
+        prev_labels = labels
+    return dict(x=np.array([c[0] for c in cents]), w=np.array([c[1] for c in cents]),
+                labels=prev_labels, obj_per_round=objs, labels_per_round=all_labels,
+                picks=picks)

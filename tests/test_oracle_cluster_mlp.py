@@ -1,0 +1,166 @@
+"""Pins of the oracle's merge initialisation, D2-clustering loop and pruning MLP.
+
+  * Eq. (merge): hand-derived golden example; brute-force re-derivation of the
+    chosen pair; merging preserves total weight and the weighted mean (first
+    moment) exactly; m >= m_k is the identity; m = 1 gives the weighted mean;
+  * Algorithm 1 with m = 1 is exactly Lloyd's K-means on the distribution
+    means (Section 1 and Section 7 make this reduction): labels and centroids
+    are compared with an independent K-means written here;
+  * SplitMix64 against the published reference outputs for seed 1234567;
+  * MLP: finite-difference gradients, a hand-worked 1-D example, translation
+    invariance of the centred embedding.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import merge_reduce, d2_cluster, splitmix64, init_pick, w2_exact
+from oracle import mlp
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_merge_golden():
+    g = json.load(open(os.path.join(GOLD, "merge_three_points.json")))
+    x, w = merge_reduce(np.array(g["x"]), np.array(g["w"]), g["m"])
+    np.testing.assert_allclose(x, np.array(g["x_out"]), atol=1e-15)
+    np.testing.assert_allclose(w, np.array(g["w_out"]), atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_merge_invariants(seed):
+    rng = np.random.default_rng(seed)
+    mk = int(rng.integers(5, 12))
+    y = rng.normal(size=(mk, 3))
+    w = rng.dirichlet(np.ones(mk))
+    for m in (1, 2, mk - 1, mk, mk + 3):
+        x, v = merge_reduce(y, w, m)
+        assert x.shape[0] == min(m, mk)
+        assert abs(v.sum() - w.sum()) < 1e-14
+        np.testing.assert_allclose(v @ x, w @ y, atol=1e-13)
+        if m >= mk:
+            np.testing.assert_array_equal(x, y)
+    # the first merge is the brute-force minimiser of the criterion
+    best = min(((w[i] * w[j] * np.sum((y[i] - y[j]) ** 2) / (w[i] + w[j]), i, j)
+                for i in range(mk) for j in range(i + 1, mk)))
+    _, i, j = best
+    x, v = merge_reduce(y, w, mk - 1)
+    np.testing.assert_allclose(x[i], (w[i] * y[i] + w[j] * y[j]) / (w[i] + w[j]), atol=1e-14)
+    assert abs(v[i] - (w[i] + w[j])) < 1e-15
+
+
+def test_splitmix64_reference_vector():
+    # outputs of the reference splitmix64.c (Vigna) for state 1234567
+    expect = [6457827717110365317, 3203168211198807973, 9817491932198370423,
+              4593380528125082431, 16408922859458223821]
+    s = 1234567
+    got = []
+    for _ in range(5):
+        s, z = splitmix64(s)
+        got.append(z)
+    assert got == expect
+
+
+def lloyd_on_means(means, init_means, rounds):
+    c = init_means.copy()
+    labels_all = []
+    for _ in range(rounds):
+        d = ((means[:, None, :] - c[None, :, :]) ** 2).sum(-1)
+        lab = np.argmin(d, axis=1)
+        labels_all.append(lab)
+        for i in range(len(c)):
+            if (lab == i).any():
+                c[i] = means[lab == i].mean(0)
+    return labels_all, c
+
+
+def test_d2_with_m1_is_kmeans_on_means():
+    rng = np.random.default_rng(21)
+    bags = []
+    centers = rng.normal(size=(3, 2)) * 4
+    for k in range(24):
+        mk = int(rng.integers(2, 5))
+        y = centers[k % 3] + rng.normal(size=(mk, 2))
+        bags.append((y, rng.dirichlet(np.ones(mk))))
+    K, rounds = 3, 3
+    res = d2_cluster(bags, K, 1, seed=99, rounds=rounds, T=25, tau=10)
+    means = np.array([w @ y for y, w in bags])
+    picks = init_pick([y.shape[0] for y, _ in bags], K, 1, 99)
+    labels_ref, cent_ref = lloyd_on_means(means, means[picks], rounds)
+    for r in range(rounds):
+        np.testing.assert_array_equal(res["labels_per_round"][r], labels_ref[r])
+    np.testing.assert_allclose(res["x"][:, 0, :], cent_ref, atol=1e-10)
+    # the objective is the mean of W^2 = ||mean - c||^2 + variance
+    var = np.array([w @ np.sum((y - w @ y) ** 2, 1) for y, w in bags])
+    assert res["obj_per_round"][0] >= var.mean() - 1e-12
+
+
+def small_params(seed, d, H=6, E=4):
+    rng = np.random.default_rng(seed)
+    return dict(W1=rng.normal(size=(H, d)) * 0.7, b1=rng.normal(size=H) * 0.1,
+                W2=rng.normal(size=(H, H)) * 0.5, b2=rng.normal(size=H) * 0.1,
+                W3=rng.normal(size=(E, H)) * 0.5)
+
+
+def test_mlp_gradient_finite_differences():
+    rng = np.random.default_rng(3)
+    d = 3
+    params = small_params(4, d)
+    bags = [(rng.normal(size=(int(rng.integers(2, 6)), d)), None) for _ in range(4)]
+    bags = [(y, rng.dirichlet(np.ones(len(y)))) for y, _ in bags]
+    cents = [(rng.normal(size=(3, d)), rng.dirichlet(np.ones(3))) for _ in range(2)]
+    pairs = [(0, 0), (1, 1), (2, 0), (3, 1), (0, 1)]
+    targets = [w2_exact(cents[q][0], cents[q][1], *bags[a]) for a, q in pairs]
+    L, g = mlp.pair_loss_and_grad(params, bags, cents, pairs, targets)
+    h = 1e-6
+    for name in mlp.PARAM_NAMES:
+        P = params[name]
+        flat = P.reshape(-1)
+        for idx in range(0, flat.size, max(1, flat.size // 7)):
+            old = flat[idx]
+            flat[idx] = old + h
+            Lp, _ = mlp.pair_loss_and_grad(params, bags, cents, pairs, targets)
+            flat[idx] = old - h
+            Lm, _ = mlp.pair_loss_and_grad(params, bags, cents, pairs, targets)
+            flat[idx] = old
+            fd = (Lp - Lm) / (2 * h)
+            assert abs(fd - g[name].reshape(-1)[idx]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_mlp_hand_example():
+    # d = 1, H = 1, E = 1: W1 = 2, b1 = 0.5, W2 = 3, b2 = -1, W3 = 0.5.
+    # P = {(0.25, -1), (0.75, 3)}: mean 2, centred u = (-3, 1);
+    # a1 = (-5.5, 2.5) -> h1 = (0, 2.5); a2 = (-1, 6.5) -> h2 = (0, 6.5);
+    # g = 0.75 * 6.5 = 4.875; f = 0.5 * 4.875 = 2.4375.
+    params = dict(W1=np.array([[2.0]]), b1=np.array([0.5]), W2=np.array([[3.0]]),
+                  b2=np.array([-1.0]), W3=np.array([[0.5]]))
+    f = mlp.embed(params, np.array([[-1.0], [3.0]]), np.array([0.25, 0.75]))
+    assert abs(f[0] - 2.4375) < 1e-15
+
+
+def test_mlp_translation_invariant_and_predictor_bound():
+    rng = np.random.default_rng(5)
+    params = small_params(6, 2)
+    y = rng.normal(size=(5, 2))
+    w = rng.dirichlet(np.ones(5))
+    np.testing.assert_allclose(mlp.embed(params, y + 7.0, w), mlp.embed(params, y, w), atol=1e-12)
+    cents = [(rng.normal(size=(3, 2)), rng.dirichlet(np.ones(3))) for _ in range(4)]
+    pred, mt = mlp.predict(params, (y, w), cents)
+    assert (pred >= mt - 1e-15).all()
+    for i, (x, wx) in enumerate(cents):
+        assert w2_exact(x, wx, y, w) >= mt[i] - 1e-12
+
+
+def test_prune_assign_exact_when_margin_holds_and_falls_back():
+    exact = [5.0, 1.0, 3.0, 0.5]
+    # predictions rank centroid 3 and 1 first; bounds of 0 and 2 exceed b = 0.5
+    lab, b, fb, n = mlp.prune_assign_one(np.array([6.0, 1.1, 3.5, 0.6]), np.array([4.0, 0.2, 2.0, 0.1]),
+                                         lambda i: exact[i], r=2, delta=0.1)
+    assert (lab, b, fb, n) == (3, 0.5, False, 2)
+    # the true best (3) is outside the candidates {0, 1}; its bound
+    # max(0.1, 1.5 - 1.0) = 0.5 does not exceed b = 1.0, so all K are solved
+    lab, b, fb, n = mlp.prune_assign_one(np.array([0.4, 1.1, 3.5, 1.5]), np.array([0.1, 0.2, 2.0, 0.1]),
+                                         lambda i: exact[i], r=2, delta=1.0)
+    assert (lab, b, fb, n) == (3, 0.5, True, 4)
