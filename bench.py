@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark of the B-ADMM barycenter hot path on one GB300 per rank.
+
+Workload (default ``ragged4096``): 4,096 clusters whose member counts are
+log-uniform in [16, 4096] (~3.0M distributions), d = 64, m_k ~ U{16..64},
+supports N(mu_c, I) with mu_c ~ N(0, 9I), Dirichlet(1) weights, barycenters of
+m = 32 points; one step = one badmm_barycenter call of T = 100 iterations
+(tau = 10, rule R1) over every cluster, started from the same synthetic
+barycenters.  Metric: plan-entry updates per second = sum_c m * n_c * T / step
+time.  With N ranks (torchrun) every rank solves its own independent problem
+of the same size (weak scaling; the clusters shard with no collective).
+
+Prints ONE JSON line on rank 0.  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import hashlib
+import json
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "B-ADMM plan-entry updates/s; D2-clustering s/round vs plain form @1e-4 obj"
+UNIT = "plan-entry updates/s"
+BYTES_PER_ENTRY = 20  # fused sweep: read Pi, Lambda, C; write Pi, Lambda (FP32)
+
+WORKLOADS = {
+    "ragged4096": dict(clusters=4096, d=64, nc=(16, 4096), mk=(16, 64), m=32, iters=100, tau=10,
+                       desc="batched ragged barycenters: 4096 clusters, member counts log-uniform "
+                            "in [16,4096], d=64, m_k~U{16..64}, m=32, N(mu_c,I) with mu_c~N(0,9I), "
+                            "Dirichlet(1) weights, T=100, tau=10, R1"),
+    "ragged256": dict(clusters=256, d=64, nc=(16, 4096), mk=(16, 64), m=32, iters=100, tau=10,
+                      desc="256 clusters of the ragged recipe (profiling size)"),
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            j = json.load(open(p))
+            return float(j["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def sweep_traffic_per_entry():
+    """DRAM bytes per plan entry of one fused-sweep launch from the committed
+    ncu summary, valid only while the sweep source is unchanged."""
+    src = os.path.join(ROOT, "paper_1510_00012_gb300", "csrc", "badmm.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    p = os.path.join(ROOT, "profiles", "k_sweep_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        parts = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if parts.get("badmm_cu_sha256_16") == digest and "dram_bytes_per_entry" in parts:
+            return float(parts["dram_bytes_per_entry"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.proc = None
+        self.lines = []
+        sel = []
+        try:
+            uuid = str(torch.cuda.get_device_properties(device).uuid)
+            sel = ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            sel = []
+        self.cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                    "-lms", "200"] + sel
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def make_workload(name, seed, device):
+    W = WORKLOADS[name]
+    bags, co, mem = synth.ragged_cluster_bags(seed, W["clusters"], d=W["d"], nc=W["nc"], mk=W["mk"],
+                                              mu_sigma=3.0, device=device)
+    x0, w0 = synth.sample_initial_barycenters(seed + 1, bags, co, mem, W["m"])
+    return bags, co, mem, x0, w0
+
+
+def oracle_sample(name, seed, budget_s):
+    """Times the FP64 oracle on whole clusters of a CPU draw of the workload
+    (smallest clusters first) for about budget_s seconds; returns
+    (entry-updates/s, description)."""
+    from oracle import badmm_barycenter as oracle_badmm
+    W = WORKLOADS[name]
+    n_cl = 64
+    bags, co, mem = synth.ragged_cluster_bags(seed, n_cl, d=W["d"], nc=W["nc"], mk=W["mk"], mu_sigma=3.0,
+                                              device="cpu")
+    x0, w0 = synth.sample_initial_barycenters(seed + 1, bags, co, mem, W["m"])
+    sizes = (co[1:] - co[:-1]).tolist()
+    order = sorted(range(n_cl), key=lambda c: sizes[c])
+    T, tau, m = W["iters"], W["tau"], W["m"]
+    done_entries, spent, used = 0, 0.0, 0
+    for c in order:
+        ids = mem[int(co[c]):int(co[c + 1])].tolist()
+        members = [bags.bag(k) for k in ids]
+        t0 = time.perf_counter()
+        oracle_badmm(members, x0[c].double().numpy(), w0[c].double().numpy(), T=T, tau=tau)
+        spent += time.perf_counter() - t0
+        done_entries += m * sum(y.shape[0] for y, _ in members) * T
+        used += 1
+        if spent >= budget_s:
+            break
+    desc = ("%d whole clusters (%d..%d members) of a CPU draw of the same recipe, T=%d, tau=%d, "
+            "single-threaded numpy FP64" % (used, sizes[order[0]], sizes[order[used - 1]], T, tau))
+    return done_entries / spent, desc, spent
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    name = args.workload
+    W = WORKLOADS[name]
+    vals = []
+    for s in range(args.warmup + args.steps):
+        v, desc, spent = oracle_sample(name, 1234, args.ref_budget)
+        if s >= args.warmup:
+            vals.append((v, spent))
+    value = statistics.median(v for v, _ in vals)
+    ms = statistics.median(t for _, t in vals) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": W["desc"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--workload", default="ragged4096", choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=2024)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    import paper_1510_00012_gb300 as d2
+    from paper_1510_00012_gb300 import build
+    build.build()
+    W = WORKLOADS[args.workload]
+
+    t0 = time.time()
+    bags, co, mem, x0, w0 = make_workload(args.workload, args.seed + 7919 * rank, dev)
+    torch.cuda.synchronize()
+    log("[bench] rank %d: generated %d distributions, %d support rows in %.1fs"
+        % (rank, bags.N, bags.n, time.time() - t0))
+    db = d2.DeviceBags(bags.offsets, bags.wt, bags.d, supp=bags.supp)
+    K, m, T = W["clusters"], W["m"], W["iters"]
+    entries = m * bags.n
+    x = x0.clone()
+    w = w0.clone()
+    plan = torch.empty(bags.n, m, dtype=torch.float32, device=dev)
+    obj = torch.empty(K, dtype=torch.float64, device=dev)
+    opts = d2.badmm_opts(iters=T, tau=W["tau"])
+    ctx = d2.Context(local)
+
+    def step():
+        x.copy_(x0)
+        w.copy_(w0)
+        d2.badmm_barycenter(ctx, db, co, mem, x, w, plan, None, opts, obj)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert torch.isfinite(obj).all(), "non-finite objective"
+
+    sampler = ClockSampler(dev)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.start()
+    time.sleep(0.3)
+    ctx.timing(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = ctx.launch_count()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = ctx.launch_count() - l0
+    clocks = sampler.stop()
+    kt = ctx.timing_read()
+    ctx.timing(False)
+    ms_total = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * entries * T / (ms_step * 1e-3)
+
+    # roofline of the dominant kernel (the fused plan sweep)
+    f_ms, f_n = kt["sweep_fused"]
+    peak, peak_kind = load_peaks()
+    roof = None
+    if f_n:
+        avg_s = f_ms / f_n * 1e-3
+        achieved = BYTES_PER_ENTRY * entries / avg_s / 1e9
+        tpe = sweep_traffic_per_entry()
+        roof = {"bound": "hbm", "kernel": "k_sweep (fused B+A pass)", "achieved": achieved,
+                "peak": peak, "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None if tpe is None else tpe * entries,
+                "algorithmic_bytes_per_launch": BYTES_PER_ENTRY * entries,
+                "avg_launch_ms": f_ms / f_n, "launches": f_n,
+                "share_of_step": f_ms / max(ms_total, 1e-9)}
+    breakdown = {k: {"ms": v[0] / args.steps, "launches": v[1] // max(args.steps, 1)} for k, v in kt.items()
+                 if v[1]}
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        h = {k: t.cpu().pin_memory() for k, t in (("offsets", bags.offsets), ("wt", bags.wt),
+                                                  ("supp", bags.supp), ("co", co), ("mem", mem),
+                                                  ("x0", x0), ("w0", w0))}
+        out_x = torch.empty_like(x, device="cpu").pin_memory()
+        out_w = torch.empty_like(w, device="cpu").pin_memory()
+        out_o = torch.empty_like(obj, device="cpu").pin_memory()
+        d_off, d_wt, d_supp = torch.empty_like(bags.offsets), torch.empty_like(bags.wt), torch.empty_like(bags.supp)
+        d_co, d_mem = torch.empty_like(co), torch.empty_like(mem)
+        bi = sum(t.numel() * t.element_size() for t in h.values())
+        bo = sum(t.numel() * t.element_size() for t in (out_x, out_w, out_o))
+        del bags, db
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            d_off.copy_(h["offsets"], non_blocking=True)
+            d_wt.copy_(h["wt"], non_blocking=True)
+            d_supp.copy_(h["supp"], non_blocking=True)
+            d_co.copy_(h["co"], non_blocking=True)
+            d_mem.copy_(h["mem"], non_blocking=True)
+            x.copy_(h["x0"], non_blocking=True)
+            w.copy_(h["w0"], non_blocking=True)
+            eb = d2.DeviceBags(d_off, d_wt, W["d"], supp=d_supp, max_mk=W["mk"][1])
+            d2.badmm_barycenter(ctx, eb, d_co, d_mem, x, w, plan, None, opts, obj)
+            out_x.copy_(x, non_blocking=True)
+            out_w.copy_(w, non_blocking=True)
+            out_o.copy_(obj, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e_step = e_ms / args.e2e_steps
+        e2e = {"value": world * entries * T / (e_step * 1e-3), "unit": UNIT, "ms_per_step": e_step,
+               "steps": args.e2e_steps, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, desc, _ = oracle_sample(args.workload, args.seed, args.cpu_budget)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": W["desc"], "clusters": K, "distributions_per_gpu": int(mem.numel()),
+                           "support_rows_per_gpu": int(entries // m), "plan_entries_per_gpu": int(entries),
+                           "iters": T, "l2": "inputs larger than L2 (Pi, Lambda, C: %.1f GB per GPU)"
+                           % (12 * entries / 1e9),
+                           "parallelism": "independent problem per GPU" if world > 1 else "single GPU"},
+                "roofline": roof, "kernel_breakdown_ms_per_step": breakdown, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,258 @@
+/*
+ * libd2 -- single-GPU (GB300, sm_103a) D2-clustering hot path.
+ *
+ * C ABI of the library.  Method: Ye, Wu, Wang & Li, "Fast Discrete
+ * Distribution Clustering Using Wasserstein Barycenter with Sparse Support"
+ * (arXiv 1510.00012).  Each entry point cites the passage that defines the
+ * operation it computes.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  * All array pointers are DEVICE pointers owned by the caller unless a
+ *    parameter says "host".  The library never frees caller memory.
+ *  * `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on it unless they write a host output
+ *    or validation is requested (D2_VALIDATE), in which case they synchronise
+ *    the stream before returning.
+ *  * Return value: D2_OK (0) or a negative status.  No C++ exception crosses
+ *    the ABI.  d2_last_error() returns a message for the last failure on the
+ *    context.  A context is not re-entrant: one host thread at a time.
+ *  * Distributions ("bags") are stored raggedly (Section 2, notation list):
+ *    bag k owns support rows offsets[k] .. offsets[k+1]-1 of the stacked
+ *    matrix X^T (n x d, row-major) and the same entries of the weight vector.
+ *  * Per-entry matrices (costs C and plans Pi) are stored "j-major": one row
+ *    of m contiguous floats per SUPPORT ROW of a bag, i.e. the paper's
+ *    Pi^(k) in R^{m x m_k} transposed, at rows offsets[k] .. offsets[k+1]-1 of
+ *    an n x m array indexed by the global support row.  Entry (i, j) of
+ *    Pi^(k) is at [(offsets[k] + j) * m + i].
+ */
+#ifndef D2_H
+#define D2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define D2_OK        0
+#define D2_EINVAL   (-1)  /* bad shape / pointer / weights (see d2_check_bags) */
+#define D2_ENOMEM   (-2)  /* device allocation failed                          */
+#define D2_ECUDA    (-3)  /* a CUDA runtime call or kernel launch failed       */
+#define D2_ETIMEOUT (-4)  /* a bounded device-side wait expired                */
+#define D2_ENOTSUP  (-5)  /* valid request outside what this build implements  */
+#define D2_ENOCONV  (-6)  /* exact OT hit its pivot limit on some pair          */
+
+/* ---- options flags ---------------------------------------------------- */
+#define D2_RULE_R1   1    /* Eq. (badmmw):  w_i  prop. to (1/N) sum_k wtilde_i^(k)        */
+#define D2_RULE_R2   2    /* Eq. (badmmw2): sqrt(w_i) prop. to (1/N) sum_k sqrt(wtilde_i^(k)) */
+
+#define D2_FIX_X     0x1  /* never move the support (pre-fixed support track, Section 4)  */
+#define D2_FIX_W     0x2  /* keep w fixed: each member then solves OT(w, w^(k)) by B-ADMM  */
+#define D2_VALIDATE  0x4  /* validate the bags on the device first (synchronises)          */
+#define D2_NO_GRAPH  0x8  /* launch kernels directly instead of replaying a CUDA graph    */
+
+typedef struct d2_ctx d2_ctx;
+
+/* A set of N discrete distributions (Section 2).  Supports are either dense
+ * (`supp`, n x d) or indices into a shared table (`vocab_idx` into `vocab`,
+ * V x d): the grid/symbolic storage of Section 5. */
+typedef struct {
+    int64_t        N;          /* number of distributions                         */
+    int64_t        n;          /* total support rows = offsets[N] (host copy)     */
+    int32_t        d;          /* support dimension, >= 1                         */
+    int32_t        max_mk;     /* host copy of max_k m_k (launch sizing), >= 1     */
+    const int64_t* offsets;    /* device, N+1, offsets[0] = 0, non-decreasing     */
+    const float*   supp;       /* device, n x d row-major, or NULL with vocab     */
+    const int32_t* vocab_idx;  /* device, n, or NULL                              */
+    const float*   vocab;      /* device, V x d row-major, or NULL                */
+    int64_t        V;          /* vocabulary rows                                 */
+    const float*   wt;         /* device, n; each bag's weights >= 0, sum 1       */
+} d2_bags;
+
+/* Options of Algorithm badmm (Section 3.3). */
+typedef struct {
+    double  rho0;      /* Eq. (rho) scale, default 2 (Section 4, Fig. 1 setting)        */
+    double  rho;       /* > 0: use this rho for every cluster instead of Eq. (rho)     */
+    double  eps;       /* added after the exponential scalings, default 1e-16           */
+    int32_t iters;     /* T, B-ADMM iterations per call, default 100 (Section 3.3)      */
+    int32_t tau;       /* support update every tau iterations, default 10               */
+    int32_t rule;      /* D2_RULE_R1 (default) or D2_RULE_R2                            */
+    int32_t flags;     /* D2_FIX_X | D2_FIX_W | D2_VALIDATE | D2_NO_GRAPH               */
+} d2_badmm_opts;
+
+/* Fill `o` with the defaults above. */
+void d2_badmm_opts_default(d2_badmm_opts* o);
+
+/* Create a context on CUDA device `device`.  It owns the device workspaces
+ * (duals, cost matrices, per-member partials) that the calls below grow on
+ * demand and reuse.  Returns NULL on failure. */
+d2_ctx* d2_create(int device);
+
+/* Free a context and every workspace it owns (NULL is a no-op). */
+void d2_destroy(d2_ctx* ctx);
+
+/* Message describing the last failure on `ctx` ("" if none).  The string is
+ * owned by the context and valid until the next call on it. */
+const char* d2_last_error(const d2_ctx* ctx);
+
+/* Bytes of device workspace the context currently holds. */
+size_t d2_workspace_bytes(const d2_ctx* ctx);
+
+/* ---- instrumentation ----------------------------------------------------
+ * When timing is on, the context brackets each launch of the kinds below with
+ * CUDA events recorded on the launching stream; d2_timing_read() waits for
+ * them and returns the summed milliseconds and launch counts per kind. */
+#define D2_KT_SWEEP_FUSED 0  /* plan sweep carrying both halves of an iteration      */
+#define D2_KT_SWEEP_HALF  1  /* plan sweep carrying one half (first/last/support it.) */
+#define D2_KT_COST        2  /* cost-matrix build                                     */
+#define D2_KT_SUPPORT     3  /* support update, Eq. (updatex)                         */
+#define D2_KT_ASSIGN      4  /* exact assignment                                      */
+#define D2_KT_PRUNE       5  /* pruning network                                       */
+#define D2_KT_OTHER       6
+#define D2_KT_COUNT       7
+/* Turn per-launch timing on (1) or off (0); either way the totals restart. */
+int d2_timing_enable(d2_ctx* ctx, int on);
+/* Summed device milliseconds and launch counts per kind since the last
+ * d2_timing_enable (arrays of D2_KT_COUNT; either may be NULL). Synchronous. */
+int d2_timing_read(d2_ctx* ctx, double* ms, int64_t* launches);
+/* Number of kernels this context has launched since it was created. */
+int64_t d2_launch_count(const d2_ctx* ctx);
+
+/* Validate a bag set on the device (synchronous): offsets non-decreasing with
+ * offsets[N] == n and every m_k in [1, max_mk]; weights finite, >= 0 and each
+ * bag's sum within 1e-5 of 1 (Section 2: w in the simplex); vocabulary indices
+ * in [0, V).  Returns D2_OK or D2_EINVAL with the first problem described. */
+int d2_check_bags(d2_ctx* ctx, const d2_bags* bags, void* stream);
+
+/* Squared-Euclidean cost matrices C(x_c, x^(k)) = (||x_i - x_j^(k)||^2)_{i,j}
+ * (Section 2 notation list; c(.,.) under Eq. (primal) with p = 2) between the
+ * barycenter support of each cluster and each of its members.
+ *
+ *   cluster_offsets : device, K+1; members[cluster_offsets[c] ..
+ *                     cluster_offsets[c+1]-1] are the bag ids of cluster c
+ *   members         : device, P bag ids (a bag may appear at most once)
+ *   x               : device, K x m x d, barycenter supports (row-major)
+ *   C_out           : device, n x m; the j-major rows of every listed member
+ *                     are written, other rows are left untouched
+ * Requires 1 <= m <= 256.  FP32 arithmetic on centred coordinates. */
+int d2_cost(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_offsets,
+            const int64_t* members, int64_t P, int32_t K, int32_t m,
+            const float* x, float* C_out, void* stream);
+
+/* Centroid update with B-ADMM (Algorithm badmm, Section 3.3) for K clusters
+ * at once, every cluster advancing through the same T iterations:
+ *   Lambda := 0; Pi^(2),0 := warm plan or w_i w_j^(k) (Section 5);
+ *   repeat T times: x by Eq. (updatex) every tau iterations (n > 0);
+ *   Pi^(k,1) by Eqs. (badmmc0b, badmmc0); wtilde^(k) from Eq. (badmmc1b);
+ *   w by Eq. (badmmw) or (badmmw2); Pi^(k,2) by Eq. (badmmc1);
+ *   Lambda by Eq. (badmm2).   rho by Eq. (rho) per cluster (rho0 x mean C).
+ *
+ *   cluster_offsets, members, P : the clustering, as for d2_cost; P host
+ *   x      : device, K x m x d, in: initial support, out: final support
+ *   w      : device, K x m, in: initial weights (simplex), out: final w
+ *   plan   : device, n x m (j-major, see above).  In: cached Pi^(k,2) rows of
+ *            members whose warm_mask entry is non-zero.  Out: the final
+ *            Pi^(k,2) of every listed member.  Rows of unlisted bags are left
+ *            untouched.  Between calls it is the warm-start cache of Section 5.
+ *   warm_mask : device, N bytes (indexed by bag id) or NULL = all cold
+ *   obj    : device, K doubles, out: (1/N_c) sum_k <C_k, Pi^(k,1)> with the
+ *            final support (0 for an empty cluster)
+ * Clusters with no member keep x and w unchanged.  Requires 1 <= m <= 256,
+ * iters >= 1, tau >= 1.  Plans, duals and exponentials are FP32; the
+ * cross-member weight sums and the objective are FP64 and deterministic. */
+int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_offsets,
+                     const int64_t* members, int64_t P, int32_t K, int32_t m,
+                     float* x, float* w, float* plan, const uint8_t* warm_mask,
+                     const d2_badmm_opts* opts, double* obj, void* stream);
+
+/* ---- learned candidate pruning (no counterpart in the paper) --------------
+ * An MLP embedding f of a distribution (per-point d -> H -> H with ReLU,
+ * weight-pooled, then H -> E), used to rank centroids by
+ *   What^2(P, Q) = ||mu_P - mu_Q||^2 + ||f(P) - f(Q)||^2
+ * before the exact assignment; see d2_assign.  Parameters are FP32 masters,
+ * the forward/backward GEMMs take FP16 inputs with FP32 accumulation. */
+typedef struct d2_prune d2_prune;
+
+/* Create a pruner for support dimension d with hidden width H and embedding
+ * width E (H, E multiples of 16, <= 256).  `init` (host, optional) holds the
+ * parameters W1 (H x d), b1 (H), W2 (H x H), b2 (H), W3 (E x H) packed in that
+ * order; NULL draws them from SplitMix64(seed) (uniform +-sqrt(6/fan_in)). */
+d2_prune* d2_prune_create(d2_ctx* ctx, int32_t d, int32_t H, int32_t E,
+                          const float* init, uint64_t seed);
+void d2_prune_destroy(d2_prune* p);
+/* Number of packed parameters. */
+int64_t d2_prune_param_count(const d2_prune* p);
+/* Copy the packed parameters to / from host memory (synchronous). */
+int d2_prune_get_params(d2_ctx* ctx, const d2_prune* p, float* host_out);
+int d2_prune_set_params(d2_ctx* ctx, d2_prune* p, const float* host_in);
+/* Candidate count r (>= 1) and margin delta (>= 0) of the margin test. */
+int d2_prune_set_margin(d2_prune* p, int32_t r, float delta);
+
+/* Embeddings f(P) of the bags listed in `ids` (device, cnt) -> emb (device,
+ * cnt x E) and their means mu (device, cnt x d). */
+int d2_prune_embed(d2_ctx* ctx, const d2_prune* p, const d2_bags* bags,
+                   const int64_t* ids, int64_t cnt, float* emb, float* mu, void* stream);
+
+/* Loss L = (1/B) sum_b (||f(P_a) - f(Q_q)||^2 - (t_b - ||mu_a - mu_q||^2))^2
+ * over B pairs (bag a_b of `bags`, centroid q_b of (x, w)) and its gradient
+ * (device, packed like the parameters).  loss (device, 1 double). */
+int d2_prune_loss_grad(d2_ctx* ctx, const d2_prune* p, const d2_bags* bags,
+                       int32_t K, int32_t m, const float* x, const float* w,
+                       const int64_t* pair_bag, const int32_t* pair_cent,
+                       const float* target, int64_t B, double* loss, float* grad,
+                       void* stream);
+
+/* Train with Adam (lr, beta1 0.9, beta2 0.999) for `steps` minibatches of
+ * `batch` pairs drawn by SplitMix64(seed) from the npairs training pairs;
+ * loss_out (host, steps) receives each minibatch loss.  Synchronous. */
+int d2_prune_train(d2_ctx* ctx, d2_prune* p, const d2_bags* bags,
+                   int32_t K, int32_t m, const float* x, const float* w,
+                   const int64_t* pair_bag, const int32_t* pair_cent,
+                   const float* target, int64_t npairs, int32_t steps, int32_t batch,
+                   float lr, uint64_t seed, float* loss_out);
+
+/* Assignment step of Algorithm 1: labels[k] = argmin_i W^2(Q_i, P^(k)) with
+ * W^2 the exact transportation LP of Eq. (primal) (ties -> lowest i), and
+ * dist[k] that minimum.
+ *   x, w   : device, K x m x d and K x m, the centroids Q_i
+ *   prune  : NULL = solve all K pairs exactly.  Otherwise solve the r
+ *            centroids of smallest What^2 exactly and accept the best b
+ *            among them when every other centroid has
+ *            max(||mu_P - mu_Qi||^2, What^2_i - delta) > b; else solve all K.
+ *   labels : device, N int32;  dist : device, N floats
+ *   stats  : optional host int64[3]: exact solves, fall-backs, pairs that hit
+ *            the pivot limit (synchronises when given)
+ * The exact solver is a transportation simplex per pair in FP32 with the
+ * final cost summed in FP64.  Requires m + max_mk <= 256 and m*max_mk <= 8192. */
+int d2_assign(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,
+              const float* x, const float* w, const d2_prune* prune,
+              int32_t* labels, float* dist, int64_t* stats, void* stream);
+
+/* Greedy merge of Eq. (merge) (Section 5): reduce bag ids[c] to m support
+ * points for c = 0..cnt-1 -> x (device cnt x m x d), w (device cnt x m).
+ * Ties: first minimum in lexicographic (i, j) order.  A bag with fewer than
+ * m points is copied and padded with zero-weight copies of its last point. */
+int d2_merge_init(d2_ctx* ctx, const d2_bags* bags, const int64_t* ids, int64_t cnt,
+                  int32_t m, float* x, float* w, void* stream);
+
+/* D2-clustering (Algorithm 1 with the Section 5 choices), all on the device:
+ * K distinct bags with m_k >= m chosen by a partial Fisher-Yates shuffle
+ * driven by SplitMix64(seed) and reduced by Eq. (merge); then `rounds` rounds
+ * of { d2_assign (with `prune` if non-NULL); badmm_barycenter over all K
+ * clusters, warm-starting Pi^(k,2) of every bag whose label is unchanged }.
+ *   x_out, w_out, labels_out : device, K x m x d, K x m, N
+ *   obj_per_round : host, rounds doubles: (1/N) sum_k W^2(Q_{l_k}, P^(k)) at
+ *                   each round's assignment
+ * Synchronous.  Empty clusters keep their previous centroid. */
+int d2_cluster(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, uint64_t seed,
+               int32_t rounds, const d2_badmm_opts* opts, const d2_prune* prune,
+               float* x_out, float* w_out, int32_t* labels_out, double* obj_per_round,
+               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* D2_H */

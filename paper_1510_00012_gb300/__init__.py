@@ -1,0 +1,247 @@
+"""Python binding of libd2, the GB300 (sm_103a) D2-clustering hot path.
+
+Thin ctypes marshalling over the C ABI declared in include/d2.h: every
+function below has the name of the C entry point it calls, takes torch CUDA
+tensors, checks dtypes/shapes/contiguity, and passes raw device pointers and
+the current CUDA stream.  All computation happens in the library's CUDA
+kernels; there is no CPU fallback.  If libd2.so has not been built (see
+``paper_1510_00012_gb300.build``) the first call raises ``D2Error``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import c_double, c_float, c_int, c_int32, c_int64, c_size_t, c_uint64, c_void_p, c_char_p
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libd2.so")
+
+D2_OK, D2_EINVAL, D2_ENOMEM, D2_ECUDA, D2_ETIMEOUT, D2_ENOTSUP, D2_ENOCONV = 0, -1, -2, -3, -4, -5, -6
+D2_RULE_R1, D2_RULE_R2 = 1, 2
+D2_FIX_X, D2_FIX_W, D2_VALIDATE, D2_NO_GRAPH = 0x1, 0x2, 0x4, 0x8
+KT_NAMES = ("sweep_fused", "sweep_half", "cost", "support", "assign", "prune", "other")
+KT_COUNT = len(KT_NAMES)
+
+
+class D2Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libd2 error %d: %s" % (code, msg))
+        self.code = code
+
+
+class _Bags(ctypes.Structure):
+    _fields_ = [("N", c_int64), ("n", c_int64), ("d", c_int32), ("max_mk", c_int32),
+                ("offsets", c_void_p), ("supp", c_void_p), ("vocab_idx", c_void_p),
+                ("vocab", c_void_p), ("V", c_int64), ("wt", c_void_p)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("rho0", c_double), ("rho", c_double), ("eps", c_double), ("iters", c_int32),
+                ("tau", c_int32), ("rule", c_int32), ("flags", c_int32)]
+
+
+_SIGS = {
+    "d2_create": (c_void_p, [c_int]),
+    "d2_destroy": (None, [c_void_p]),
+    "d2_last_error": (c_char_p, [c_void_p]),
+    "d2_workspace_bytes": (c_size_t, [c_void_p]),
+    "d2_badmm_opts_default": (None, [c_void_p]),
+    "d2_check_bags": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "d2_timing_enable": (c_int, [c_void_p, c_int]),
+    "d2_timing_read": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "d2_launch_count": (c_int64, [c_void_p]),
+    "d2_cost": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32,
+                        c_void_p, c_void_p, c_void_p]),
+    "badmm_barycenter": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32,
+                                 c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "d2_assign": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
+                          c_void_p, c_void_p, c_void_p, c_void_p]),
+    "d2_merge_init": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p,
+                              c_void_p]),
+    "d2_cluster": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_uint64, c_int32, c_void_p,
+                           c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "d2_prune_create": (c_void_p, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_uint64]),
+    "d2_prune_destroy": (None, [c_void_p]),
+    "d2_prune_param_count": (c_int64, [c_void_p]),
+    "d2_prune_get_params": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "d2_prune_set_params": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "d2_prune_set_margin": (c_int, [c_void_p, c_int32, c_float]),
+    "d2_prune_embed": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p,
+                               c_void_p]),
+    "d2_prune_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
+                                   c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    "d2_prune_train": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
+                               c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_float,
+                               c_uint64, c_void_p]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libd2 (raises D2Error if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise D2Error(D2_ENOTSUP, "libd2.so is not built (%s); run paper_1510_00012_gb300.build.build()"
+                          % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _need(t, dtype, name, device=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return t
+
+
+class Context:
+    """Owns a d2_ctx (device workspaces, last error)."""
+
+    def __init__(self, device=None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        torch.cuda.init()
+        self.h = lib().d2_create(self.device)
+        if not self.h:
+            raise D2Error(D2_ECUDA, "d2_create(%d) failed" % self.device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().d2_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc):
+        if rc != D2_OK:
+            raise D2Error(rc, lib().d2_last_error(self.h).decode())
+        return rc
+
+    def workspace_bytes(self):
+        return int(lib().d2_workspace_bytes(self.h))
+
+    def timing(self, on=True):
+        """Start (or stop) per-launch CUDA-event timing; totals restart."""
+        self.check(lib().d2_timing_enable(self.h, 1 if on else 0))
+
+    def timing_read(self):
+        """{kind: (total_ms, launches)} since the last timing() call."""
+        ms = (c_double * KT_COUNT)()
+        n = (c_int64 * KT_COUNT)()
+        self.check(lib().d2_timing_read(self.h, ms, n))
+        return {KT_NAMES[k]: (ms[k], n[k]) for k in range(KT_COUNT)}
+
+    def launch_count(self):
+        return int(lib().d2_launch_count(self.h))
+
+
+class DeviceBags:
+    """Device-resident bag set in the layout of d2_bags (see include/d2.h)."""
+
+    def __init__(self, offsets, wt, d, supp=None, vocab_idx=None, vocab=None, max_mk=None):
+        self.offsets = _need(offsets, torch.int64, "offsets")
+        self.wt = _need(wt, torch.float32, "wt")
+        self.supp = None if supp is None else _need(supp, torch.float32, "supp")
+        self.vocab_idx = None if vocab_idx is None else _need(vocab_idx, torch.int32, "vocab_idx")
+        self.vocab = None if vocab is None else _need(vocab, torch.float32, "vocab")
+        self.d = int(d)
+        self.N = offsets.numel() - 1
+        self.n = wt.numel()
+        if max_mk is None:
+            max_mk = int((offsets[1:] - offsets[:-1]).max().item()) if self.N > 0 else 1
+        self.max_mk = int(max_mk)
+        self.V = 0 if vocab is None else vocab.shape[0]
+        self.c = _Bags(self.N, self.n, self.d, self.max_mk, _ptr(self.offsets), _ptr(self.supp),
+                       _ptr(self.vocab_idx), _ptr(self.vocab), self.V, _ptr(self.wt))
+
+    @classmethod
+    def from_synth(cls, b, device="cuda"):
+        mv = lambda t, dt: None if t is None else t.to(device=device, dtype=dt).contiguous()
+        return cls(mv(b.offsets, torch.int64), mv(b.wt, torch.float32), b.d,
+                   supp=mv(b.supp, torch.float32), vocab_idx=mv(b.vocab_idx, torch.int32),
+                   vocab=mv(b.vocab, torch.float32))
+
+    def ref(self):
+        return ctypes.byref(self.c)
+
+
+def badmm_opts(rho0=2.0, iters=100, tau=10, eps=1e-16, rule="R1", fix_x=False, fix_w=False,
+               validate=False, rho=0.0, graph=True):
+    o = _Opts()
+    lib().d2_badmm_opts_default(ctypes.byref(o))
+    o.rho0, o.iters, o.tau, o.eps, o.rho = float(rho0), int(iters), int(tau), float(eps), float(rho)
+    o.rule = D2_RULE_R2 if rule == "R2" else D2_RULE_R1
+    o.flags = ((D2_FIX_X if fix_x else 0) | (D2_FIX_W if fix_w else 0) | (D2_VALIDATE if validate else 0)
+               | (0 if graph else D2_NO_GRAPH))
+    return o
+
+
+def d2_check_bags(ctx, bags):
+    return ctx.check(lib().d2_check_bags(ctx.h, bags.ref(), _stream()))
+
+
+def d2_cost(ctx, bags, cluster_offsets, members, x, C_out=None):
+    """C (n x m, j-major rows) between each cluster's support x[c] and its members."""
+    _need(cluster_offsets, torch.int64, "cluster_offsets")
+    _need(members, torch.int64, "members")
+    _need(x, torch.float32, "x")
+    K, m = x.shape[0], x.shape[1]
+    if C_out is None:
+        C_out = torch.zeros(bags.n, m, dtype=torch.float32, device=x.device)
+    _need(C_out, torch.float32, "C_out")
+    ctx.check(lib().d2_cost(ctx.h, bags.ref(), _ptr(cluster_offsets), _ptr(members), members.numel(),
+                            K, m, _ptr(x), _ptr(C_out), _stream()))
+    return C_out
+
+
+def badmm_barycenter(ctx, bags, cluster_offsets, members, x, w, plan=None, warm_mask=None,
+                     opts=None, obj=None):
+    """Algorithm badmm on every cluster; updates x (K,m,d), w (K,m), plan (n,m) in place.
+
+    Returns (x, w, plan, obj) with obj (K,) float64 on the device."""
+    _need(cluster_offsets, torch.int64, "cluster_offsets")
+    _need(members, torch.int64, "members")
+    _need(x, torch.float32, "x")
+    _need(w, torch.float32, "w")
+    K, m = x.shape[0], x.shape[1]
+    if plan is None:
+        plan = torch.empty(bags.n, m, dtype=torch.float32, device=x.device)
+    _need(plan, torch.float32, "plan")
+    if warm_mask is not None:
+        _need(warm_mask, torch.uint8, "warm_mask")
+    if obj is None:
+        obj = torch.empty(K, dtype=torch.float64, device=x.device)
+    _need(obj, torch.float64, "obj")
+    if opts is None:
+        opts = badmm_opts()
+    ctx.check(lib().badmm_barycenter(ctx.h, bags.ref(), _ptr(cluster_offsets), _ptr(members),
+                                     members.numel(), K, m, _ptr(x), _ptr(w), _ptr(plan),
+                                     _ptr(warm_mask), ctypes.byref(opts), _ptr(obj), _stream()))
+    return x, w, plan, obj

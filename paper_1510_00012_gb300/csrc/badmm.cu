@@ -1,0 +1,634 @@
+// Centroid update with B-ADMM (Algorithm badmm, Section 3.3) for all clusters
+// at once.
+//
+// Plan sweep.  Between launches the only per-entry state is two n x m FP32
+// arrays (the plan buffer and Lambda) plus the cost C; every launch streams
+// them once.  One warp owns one member (one cluster position) and walks its
+// m_k j-major rows; a row of m entries is split over LPR lanes holding NV
+// vectors of VEC floats each, so the column normalisation of Eq. (badmmc0)
+// (over the m barycenter points) is a shuffle reduction inside a lane group
+// and the row sums r_{k,i} of Eq. (badmmc1b) (over the member's m_k points)
+// are per-lane accumulators folded once per member.
+//
+// The iteration is re-associated so that the dual update of iteration n-1 and
+// the plan update of iteration n share one pass (FUSED):
+//   in : Pi1^n (plan buffer), Lambda^{n-1}, C, r^n_k, w^n
+//   B  : Pt = Pi1 exp(Lambda/rho) + eps;  Pi2^n = Pt w_i / r_{k,i};
+//        Lambda^n = Lambda^{n-1} + rho (Pi1^n - Pi2^n)                (Eqs. badmmc1, badmm2)
+//   A  : T1 = Pi2^n exp(-(C + Lambda^n)/rho) + eps;
+//        Pi1^{n+1} = T1 w_j^(k) / sum_i T1;                             (Eqs. badmmc0b, badmmc0)
+//        r^{n+1}_{k,i} = sum_j (Pi1^{n+1} exp(Lambda^n/rho) + eps)     (Eq. badmmc1b)
+//   out: Pi1^{n+1}, Lambda^n, r^{n+1}_k, wtilde^(k) = r_k / sum_i r_{k,i}
+// so each iteration reads Pi, Lambda, C and writes Pi, Lambda: 20 bytes per
+// entry.  The exponent of the A step is shifted by its row maximum s in the
+// log2 domain and eps is scaled by 2^-s, which leaves Pi1 unchanged in exact
+// arithmetic and keeps FP32 from underflowing on far-away points.
+//
+// Weight consensus (Eq. badmmw / badmmw2).  Each warp writes its member's
+// wtilde^(k) in FP64; the last CTA to finish a cluster (arrival counter per
+// cluster, no waiting) sums the cluster's members in a fixed order in FP64,
+// normalises, and publishes w^{n+1} for the next launch.  The result does not
+// depend on CTA scheduling.
+#include "d2_internal.cuh"
+
+#define SWEEP_WARPS 8
+#define SWEEP_THREADS (SWEEP_WARPS * 32)
+
+enum SweepFlags {
+    SW_B = 1,            // input plan buffer holds Pi1^n: do the B step
+    SW_A = 2,            // do the A step
+    SW_LAM_ZERO = 4,     // Lambda input is identically zero (not read)
+    SW_LAM_OUT = 8,      // write Lambda^n
+    SW_COLD = 16,        // (A only) Pi2^0 = w_i w_j^(k) unless warm_mask[k]
+    SW_OBJ = 32,         // accumulate <C, Pi1^{n+1}> per member
+    SW_R2 = 64,          // consensus rule R2 (store sqrt of wtilde)
+};
+
+struct SweepArgs {
+    const int64_t* members;
+    const int32_t* pos_cluster;
+    int64_t P;
+    const int64_t* offsets;
+    const float* wt;
+    float* plan;
+    float* lam;
+    const float* cost;
+    float* pos_r;
+    double* pos_part;
+    double* pos_obj;
+    const float* w_cur;
+    float* w_next;       // null: weights fixed, no consensus
+    double* w_next64;
+    const float* beta;   // per cluster log2(e) / rho
+    const float* rho;
+    int* counters;
+    const int64_t* cofs;
+    const uint8_t* warm_mask;
+    int m;
+    float eps;
+    float log2eps;
+    int flags;
+};
+
+template <int VEC>
+struct VecIO;
+template <>
+struct VecIO<4> {
+    static __device__ __forceinline__ void ld(const float* p, float* v) {
+        float4 t = *reinterpret_cast<const float4*>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    static __device__ __forceinline__ void st(float* p, const float* v) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <>
+struct VecIO<1> {
+    static __device__ __forceinline__ void ld(const float* p, float* v) { v[0] = *p; }
+    static __device__ __forceinline__ void st(float* p, const float* v) { *p = v[0]; }
+};
+
+// fixed-order FP64 consensus of cluster c by the whole CTA
+__device__ void consensus_cluster(const SweepArgs& a, int c, double* s_acc) {
+    const int m = a.m;
+    const int G = SWEEP_THREADS / m;  // position groups (m <= 256)
+    const int t = threadIdx.x;
+    const int i = t % m, g = t / m;
+    const int64_t p0 = a.cofs[c], p1 = a.cofs[c + 1];
+    double acc = 0.0;
+    if (g < G) {
+        for (int64_t p = p0 + g; p < p1; p += G) acc += __ldcg(a.pos_part + p * m + i);
+        s_acc[g * m + i] = acc;
+    }
+    __syncthreads();
+    if (t < m) {
+        double s = 0.0;
+        for (int h = 0; h < G; ++h) s += s_acc[h * m + t];
+        s_acc[SWEEP_THREADS + t] = (a.flags & SW_R2) ? s * s : s;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double tot = 0.0;
+        for (int h = 0; h < m; ++h) tot += s_acc[SWEEP_THREADS + h];
+        s_acc[SWEEP_THREADS + 256] = tot;
+    }
+    __syncthreads();
+    if (t < m) {
+        double wv = s_acc[SWEEP_THREADS + t] / s_acc[SWEEP_THREADS + 256];
+        a.w_next64[(int64_t)c * m + t] = wv;
+        a.w_next[(int64_t)c * m + t] = (float)wv;
+    }
+    if (t == 0) a.counters[c] = 0;
+    __syncthreads();
+}
+
+template <int VEC, int LPR, int NV>
+__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
+    constexpr int RPW = 32 / LPR;   // rows per warp step
+    constexpr int NE = VEC * NV;    // floats per lane per row
+    __shared__ int s_list[SWEEP_WARPS];
+    __shared__ int s_nlist;
+    __shared__ double s_acc[SWEEP_THREADS + 257];
+
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int sub = lane / LPR, cl = lane % LPR;
+    const int64_t p = (int64_t)blockIdx.x * SWEEP_WARPS + wib;
+    const int m = a.m;
+    const int fl = a.flags;
+    const bool doA = fl & SW_A, doB = fl & SW_B;
+
+    if (p < a.P) {
+        const int64_t k = a.members[p];
+        const int c = a.pos_cluster[p];
+        const int64_t row0 = a.offsets[k];
+        const int mk = (int)(a.offsets[k + 1] - row0);
+        const float beta = a.beta[c];
+        const float rho = a.rho[c];
+        const float eps = a.eps;
+        const bool cold = (fl & SW_COLD) && !(a.warm_mask && a.warm_mask[k]);
+
+        // per-lane column constants
+        float coef[NE], wcol[NE];
+        bool ok[NE];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const int col = (cl + LPR * v) * VEC + e;
+                const int x = v * VEC + e;
+                ok[x] = col < m;
+                float wc = ok[x] ? a.w_cur[(int64_t)c * m + col] : 0.f;
+                wcol[x] = wc;
+                coef[x] = (doB && ok[x]) ? wc / a.pos_r[p * m + col] : 0.f;
+            }
+
+        float racc[NE];
+#pragma unroll
+        for (int x = 0; x < NE; ++x) racc[x] = 0.f;
+        float objacc = 0.f;
+
+        for (int base = 0; base < mk; base += RPW) {
+            const int j = base + sub;
+            const bool rv = j < mk;
+            const int64_t rowoff = (row0 + (rv ? j : 0)) * (int64_t)m;
+            float pin[NE], lin[NE], cin[NE];
+#pragma unroll
+            for (int x = 0; x < NE; ++x) { pin[x] = 0.f; lin[x] = 0.f; cin[x] = 0.f; }
+            const float wkj = rv ? a.wt[row0 + j] : 0.f;
+            if (rv) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const int col0 = (cl + LPR * v) * VEC;
+                    if (col0 < m) {
+                        if (doB || !cold) VecIO<VEC>::ld(a.plan + rowoff + col0, pin + v * VEC);
+                        if (!(fl & SW_LAM_ZERO)) VecIO<VEC>::ld(a.lam + rowoff + col0, lin + v * VEC);
+                        if (doA) VecIO<VEC>::ld(a.cost + rowoff + col0, cin + v * VEC);
+                    }
+                }
+            }
+            // ---- B step: Pi2^n and Lambda^n from Pi1^n and Lambda^{n-1}
+            float p2[NE], l2[NE];
+#pragma unroll
+            for (int x = 0; x < NE; ++x) {
+                if (doB) {
+                    const float pt = fmaf(pin[x], exp2f(lin[x] * beta), eps);
+                    p2[x] = pt * coef[x];
+                    l2[x] = fmaf(rho, pin[x] - p2[x], lin[x]);
+                } else {
+                    p2[x] = cold ? wcol[x] * wkj : pin[x];
+                    l2[x] = lin[x];
+                }
+            }
+            if (doA) {
+                // ---- A step: Pi1^{n+1} with a row-max shift in the log2 domain
+                float ex[NE];
+                float s = -INFINITY;
+#pragma unroll
+                for (int x = 0; x < NE; ++x) {
+                    ex[x] = -(cin[x] + l2[x]) * beta;
+                    if (ok[x]) s = fmaxf(s, ex[x]);
+                }
+                s = group_max<LPR>(s);
+                const float epss = exp2f(fminf(a.log2eps - s, 126.f));
+                float t1[NE];
+                float rs = 0.f;
+#pragma unroll
+                for (int x = 0; x < NE; ++x) {
+                    t1[x] = ok[x] ? fmaf(p2[x], exp2f(ex[x] - s), epss) : 0.f;
+                    rs += t1[x];
+                }
+                rs = group_sum<LPR>(rs);
+                const float scale = rs > 0.f ? wkj / rs : 0.f;
+                float p1n[NE];
+#pragma unroll
+                for (int x = 0; x < NE; ++x) {
+                    p1n[x] = t1[x] * scale;
+                    if (rv && ok[x]) {
+                        racc[x] += fmaf(p1n[x], exp2f(l2[x] * beta), eps);
+                        objacc = fmaf(cin[x], p1n[x], objacc);
+                    }
+                }
+                if (rv) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        const int col0 = (cl + LPR * v) * VEC;
+                        if (col0 < m) {
+                            VecIO<VEC>::st(a.plan + rowoff + col0, p1n + v * VEC);
+                            if (fl & SW_LAM_OUT) VecIO<VEC>::st(a.lam + rowoff + col0, l2 + v * VEC);
+                        }
+                    }
+                }
+            } else if (rv) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const int col0 = (cl + LPR * v) * VEC;
+                    if (col0 < m) {
+                        VecIO<VEC>::st(a.plan + rowoff + col0, p2 + v * VEC);
+                        if (fl & SW_LAM_OUT) VecIO<VEC>::st(a.lam + rowoff + col0, l2 + v * VEC);
+                    }
+                }
+            }
+        }
+
+        if (doA) {
+            // fold the row sums of the RPW row groups of the warp
+#pragma unroll
+            for (int x = 0; x < NE; ++x)
+#pragma unroll
+                for (int o = LPR; o < 32; o <<= 1) racc[x] += __shfl_xor_sync(0xffffffffu, racc[x], o);
+            double tl = 0.0;
+#pragma unroll
+            for (int x = 0; x < NE; ++x)
+                if (ok[x]) tl += (double)racc[x];
+            tl = group_sum_d<LPR>(tl);
+            if (sub == 0) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        const int col = (cl + LPR * v) * VEC + e;
+                        const int x = v * VEC + e;
+                        if (ok[x]) {
+                            a.pos_r[p * m + col] = racc[x];
+                            double wtl = (double)racc[x] / tl;
+                            a.pos_part[p * m + col] = (fl & SW_R2) ? sqrt(wtl) : wtl;
+                        }
+                    }
+            }
+            if (fl & SW_OBJ) {
+                double ov = group_sum_d<32>((double)objacc);
+                if (lane == 0) a.pos_obj[p] = ov;
+            }
+        }
+    }
+
+    // ---- weight consensus by the last CTA to finish each cluster
+    if (doA && a.w_next) {
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int nl = 0;
+            const int64_t p0 = (int64_t)blockIdx.x * SWEEP_WARPS;
+            const int64_t p1 = min(p0 + SWEEP_WARPS, a.P);
+            int64_t q = p0;
+            while (q < p1) {
+                const int c = a.pos_cluster[q];
+                int64_t e = q;
+                while (e < p1 && a.pos_cluster[e] == c) ++e;
+                const int cnt = (int)(e - q);
+                const int total = (int)(a.cofs[c + 1] - a.cofs[c]);
+                const int old = atomicAdd(&a.counters[c], cnt);
+                if (old + cnt == total) s_list[nl++] = c;
+                q = e;
+            }
+            s_nlist = nl;
+        }
+        __syncthreads();
+        const int nl = s_nlist;
+        for (int r = 0; r < nl; ++r) {
+            __threadfence();
+            consensus_cluster(a, s_list[r], s_acc);
+        }
+    }
+}
+
+typedef void (*SweepFn)(SweepArgs);
+
+static SweepFn pick_sweep(int m) {
+    if (m % 4 == 0) {
+        if (m <= 4) return k_sweep<4, 1, 1>;
+        if (m <= 8) return k_sweep<4, 2, 1>;
+        if (m <= 16) return k_sweep<4, 4, 1>;
+        if (m <= 32) return k_sweep<4, 8, 1>;
+        if (m <= 64) return k_sweep<4, 16, 1>;
+        if (m <= 128) return k_sweep<4, 32, 1>;
+        return k_sweep<4, 32, 2>;
+    }
+    if (m <= 1) return k_sweep<1, 1, 1>;
+    if (m <= 2) return k_sweep<1, 2, 1>;
+    if (m <= 4) return k_sweep<1, 4, 1>;
+    if (m <= 8) return k_sweep<1, 8, 1>;
+    if (m <= 16) return k_sweep<1, 16, 1>;
+    if (m <= 32) return k_sweep<1, 32, 1>;
+    if (m <= 64) return k_sweep<1, 32, 2>;
+    if (m <= 128) return k_sweep<1, 32, 4>;
+    return k_sweep<1, 32, 8>;
+}
+
+// ---------------------------------------------------------------------------
+// rho per cluster (Eq. rho, rho0 x mean cost) from the per-chunk FP64 sums
+// ---------------------------------------------------------------------------
+__global__ void k_rho(int K, int m, const int64_t* chunk_first, const double* chunk_sum,
+                      const int64_t* chunk_rows, double rho0, double rho_fixed, float* rho, float* beta,
+                      int64_t* nrows) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= K) return;
+    double s = 0.0;
+    int64_t r = 0;
+    if (chunk_sum) {
+        for (int64_t q = chunk_first[c]; q < chunk_first[c + 1]; ++q) {
+            s += chunk_sum[q];
+            r += chunk_rows[q];
+        }
+    }
+    double v;
+    if (rho_fixed > 0.0) v = rho_fixed;
+    else v = (r > 0) ? rho0 * s / ((double)m * (double)r) : 1.0;
+    if (!(v > 0.0) || !isfinite(v)) v = 1.0;   // all costs zero: any rho gives the same plans
+    rho[c] = (float)v;
+    beta[c] = (float)(D2_LOG2E / v);
+    nrows[c] = r;
+}
+
+// ---------------------------------------------------------------------------
+// support update (Eq. updatex): per-chunk partial sums of Pi2^T Y, then a
+// fixed-order combine per cluster and the division by N_c w_i
+// ---------------------------------------------------------------------------
+#define XU_THREADS 256
+#define XU_ROWS 32
+#define XU_DT 64
+#define XU_MT 32
+
+__global__ void __launch_bounds__(XU_THREADS) k_xpartial(const int64_t* members, const int64_t* offsets,
+                                                         const float* supp, const int32_t* vidx,
+                                                         const float* vocab, int d, int m, const float* plan,
+                                                         const Chunk* chunks, const int64_t* nchunks,
+                                                         float* xpart) {
+    __shared__ float ps[XU_ROWS][XU_MT + 1];
+    __shared__ float ys[XU_ROWS][XU_DT + 1];
+    __shared__ int64_t s_rs[D2_CHUNK];
+    __shared__ int s_pre[D2_CHUNK + 1];
+    __shared__ int64_t s_row[XU_ROWS];
+    const int64_t q = blockIdx.x;
+    if (q >= *nchunks) return;
+    const int d0 = blockIdx.y * XU_DT, i0 = blockIdx.z * XU_MT;
+    if (d0 >= d || i0 >= m) return;
+    const Chunk ch = chunks[q];
+    const int nm = (int)(ch.p1 - ch.p0);
+    const int tid = threadIdx.x;
+    if (tid < nm) {
+        int64_t k = members[ch.p0 + tid];
+        s_rs[tid] = offsets[k];
+        s_pre[tid + 1] = (int)(offsets[k + 1] - offsets[k]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        s_pre[0] = 0;
+        for (int t = 0; t < nm; ++t) s_pre[t + 1] += s_pre[t];
+    }
+    __syncthreads();
+    const int R = s_pre[nm];
+    const int dd = tid % XU_DT, ig = tid / XU_DT;  // 4 groups of i
+    constexpr int NA = XU_MT / (XU_THREADS / XU_DT);
+    float acc[NA];
+#pragma unroll
+    for (int t = 0; t < NA; ++t) acc[t] = 0.f;
+    for (int rb = 0; rb < R; rb += XU_ROWS) {
+        __syncthreads();
+        if (tid < XU_ROWS) {
+            int lr = rb + tid;
+            int64_t g = -1;
+            if (lr < R) {
+                int lo = 0, hi = nm - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (s_pre[mid] <= lr) lo = mid; else hi = mid - 1;
+                }
+                g = s_rs[lo] + (lr - s_pre[lo]);
+            }
+            s_row[tid] = g;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < XU_ROWS * XU_MT; idx += XU_THREADS) {
+            int r = idx / XU_MT, i = idx % XU_MT;
+            int64_t g = s_row[r];
+            ps[r][i] = (g >= 0 && i0 + i < m) ? plan[g * m + i0 + i] : 0.f;
+        }
+        for (int idx = tid; idx < XU_ROWS * XU_DT; idx += XU_THREADS) {
+            int r = idx / XU_DT, t = idx % XU_DT;
+            int64_t g = s_row[r];
+            ys[r][t] = (g >= 0 && d0 + t < d) ? d2_row_ptr(supp, vidx, vocab, d, g)[d0 + t] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int r = 0; r < XU_ROWS; ++r) {
+            const float yv = ys[r][dd];
+#pragma unroll
+            for (int t = 0; t < NA; ++t) acc[t] = fmaf(ps[r][ig + 4 * t], yv, acc[t]);
+        }
+    }
+    float* out = xpart + q * (int64_t)m * d;
+    if (d0 + dd < d) {
+#pragma unroll
+        for (int t = 0; t < NA; ++t) {
+            int i = i0 + ig + 4 * t;
+            if (i < m) out[(int64_t)i * d + d0 + dd] = acc[t];
+        }
+    }
+}
+
+__global__ void k_xfinal(int m, int d, const int64_t* cofs, const int64_t* chunk_first, const float* xpart,
+                         const float* w, float* x) {
+    const int c = blockIdx.x;
+    const int64_t Nc = cofs[c + 1] - cofs[c];
+    if (Nc == 0) return;
+    const int64_t q0 = chunk_first[c], q1 = chunk_first[c + 1];
+    for (int idx = threadIdx.x; idx < m * d; idx += blockDim.x) {
+        const int i = idx / d;
+        float s = 0.f;
+        for (int64_t q = q0; q < q1; ++q) s += xpart[q * (int64_t)m * d + idx];
+        const float mass = (float)Nc * w[(int64_t)c * m + i];
+        if (mass > 0.f) x[(int64_t)c * m * d + idx] = s / mass;
+    }
+}
+
+// objective (1/N_c) sum_k <C_k, Pi^(k,1)> in fixed member order; final weights out
+__global__ void k_finish(int K, int m, const int64_t* cofs, const double* pos_obj, const float* wfin,
+                         float* w_out, double* obj, bool want_obj) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= K) return;
+    const int64_t p0 = cofs[c], p1 = cofs[c + 1];
+    if (p1 == p0) {
+        if (obj) obj[c] = 0.0;
+        return;
+    }
+    if (want_obj && obj) {
+        double s = 0.0;
+        for (int64_t p = p0; p < p1; ++p) s += pos_obj[p];
+        obj[c] = s / (double)(p1 - p0);
+    }
+    if (wfin != w_out)
+        for (int i = 0; i < m; ++i) w_out[(int64_t)c * m + i] = wfin[(int64_t)c * m + i];
+}
+
+// ---------------------------------------------------------------------------
+// entry point
+// ---------------------------------------------------------------------------
+
+extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_offsets,
+                                const int64_t* members, int64_t P, int32_t K, int32_t m, float* x,
+                                float* w, float* plan, const uint8_t* warm_mask, const d2_badmm_opts* opts_in,
+                                double* obj, void* stream) {
+    if (!ctx) return D2_EINVAL;
+    int rc = d2_check_bags_host(ctx, bags);
+    if (rc) return rc;
+    d2_badmm_opts opts;
+    if (opts_in) opts = *opts_in; else d2_badmm_opts_default(&opts);
+    if (K < 1 || m < 1 || m > 256 || P < 0 || !cluster_offsets || (P > 0 && !members) || !x || !w || !plan)
+        return d2_fail(ctx, D2_EINVAL, "badmm_barycenter: need K >= 1, 1 <= m <= 256 and non-NULL arrays");
+    if (opts.iters < 1 || opts.tau < 1 || !(opts.eps >= 0.0) || !(opts.rho0 > 0.0) ||
+        (opts.rule != D2_RULE_R1 && opts.rule != D2_RULE_R2))
+        return d2_fail(ctx, D2_EINVAL, "badmm_barycenter: need iters >= 1, tau >= 1, eps >= 0, rho0 > 0, rule R1/R2");
+    if ((reinterpret_cast<uintptr_t>(plan) & 15) || (reinterpret_cast<uintptr_t>(x) & 3))
+        return d2_fail(ctx, D2_EINVAL, "badmm_barycenter: plan must be 16-byte aligned");
+    cudaStream_t st = d2_stream(stream);
+    if (opts.flags & D2_VALIDATE) {
+        rc = d2_check_bags(ctx, bags, stream);
+        if (rc) return rc;
+    }
+    if (P == 0) return D2_OK;
+    const int d = bags->d;
+    const int64_t n = bags->n;
+
+    // workspaces
+    ClusterWs cw;
+    rc = d2_cluster_ws(ctx, K, m, d, P, &cw);
+    if (rc) return rc;
+    void *vlam, *vcost, *vr, *vpart, *vobj, *vxp;
+    if ((rc = d2_ws(ctx, WS_LAM, (size_t)n * m * 4, &vlam))) return rc;
+    if ((rc = d2_ws(ctx, WS_COST, (size_t)n * m * 4, &vcost))) return rc;
+    if ((rc = d2_ws(ctx, WS_POS_R, (size_t)P * m * 4, &vr))) return rc;
+    if ((rc = d2_ws(ctx, WS_POS_PART, (size_t)P * m * 8, &vpart))) return rc;
+    if ((rc = d2_ws(ctx, WS_POS_OBJ, (size_t)P * 8, &vobj))) return rc;
+    const int64_t maxch = d2_ceil_div(P, D2_CHUNK) + K + 1;
+    const bool fix_x = opts.flags & D2_FIX_X, fix_w = opts.flags & D2_FIX_W;
+    if (!fix_x) {
+        if ((rc = d2_ws(ctx, WS_XPART, (size_t)maxch * m * d * 4, &vxp))) return rc;
+    }
+    // the cluster workspace may have moved while growing the others
+    rc = d2_cluster_ws(ctx, K, m, d, P, &cw);
+    if (rc) return rc;
+
+    int32_t* pos_cluster = nullptr;
+    rc = d2_setup_clusters(ctx, cluster_offsets, P, K, &pos_cluster, &cw, st);
+    if (rc) return rc;
+    D2_CK(ctx, cudaMemsetAsync(cw.counters, 0, (size_t)K * 4, st));
+    D2_CK(ctx, cudaMemcpyAsync(cw.wb[0], w, (size_t)K * m * 4, cudaMemcpyDeviceToDevice, st));
+
+    float* lam = static_cast<float*>(vlam);
+    float* cost = static_cast<float*>(vcost);
+
+    // initial cost and rho (Eq. rho)
+    if ((rc = d2_prep_x(ctx, x, K, m, d, cw, st))) return rc;
+    const bool need_sums = !(opts.rho > 0.0);
+    if ((rc = d2_cost_rows(ctx, bags, members, P, K, m, cw, cost, need_sums, st))) return rc;
+    {
+        void* cs = nullptr;
+        double* chunk_sum = nullptr;
+        int64_t* chunk_rows = nullptr;
+        if (need_sums) {
+            if ((rc = d2_ws(ctx, WS_CHUNK_SUM, (size_t)maxch * 16, &cs))) return rc;
+            chunk_sum = static_cast<double*>(cs);
+            chunk_rows = reinterpret_cast<int64_t*>(static_cast<char*>(cs) + (size_t)maxch * 8);
+        }
+        k_rho<<<(unsigned)d2_ceil_div(K, 128), 128, 0, st>>>(K, m, cw.chunk_first, chunk_sum, chunk_rows,
+                                                            opts.rho0, opts.rho, cw.rho, cw.beta, cw.nrows);
+        D2_LAUNCH_CK(ctx, "k_rho");
+    }
+
+    SweepArgs sa;
+    sa.members = members;
+    sa.pos_cluster = pos_cluster;
+    sa.P = P;
+    sa.offsets = bags->offsets;
+    sa.wt = bags->wt;
+    sa.plan = plan;
+    sa.lam = lam;
+    sa.cost = cost;
+    sa.pos_r = static_cast<float*>(vr);
+    sa.pos_part = static_cast<double*>(vpart);
+    sa.pos_obj = static_cast<double*>(vobj);
+    sa.beta = cw.beta;
+    sa.rho = cw.rho;
+    sa.counters = cw.counters;
+    sa.cofs = cluster_offsets;
+    sa.warm_mask = warm_mask;
+    sa.m = m;
+    sa.eps = (float)opts.eps;
+    sa.log2eps = opts.eps > 0.0 ? (float)log2(opts.eps) : -INFINITY;
+    sa.w_next64 = cw.w64;
+    const int rflag = (opts.rule == D2_RULE_R2) ? SW_R2 : 0;
+    SweepFn sweep = pick_sweep(m);
+    const unsigned grid = (unsigned)d2_ceil_div(P, SWEEP_WARPS);
+    const int T = opts.iters, tau = opts.tau;
+
+    auto launch = [&](int flags, const float* wcur, float* wnext) -> int {
+        SweepArgs s = sa;
+        s.flags = flags | rflag;
+        s.w_cur = wcur;
+        s.w_next = fix_w ? nullptr : wnext;
+        d2_time_begin(ctx, ((flags & SW_A) && (flags & SW_B)) ? D2_KT_SWEEP_FUSED : D2_KT_SWEEP_HALF, st);
+        sweep<<<grid, SWEEP_THREADS, 0, st>>>(s);
+        d2_time_end(ctx, st);
+        D2_LAUNCH_CK(ctx, "k_sweep");
+        return D2_OK;
+    };
+    auto wbuf = [&](int n) -> float* { return fix_w ? cw.wb[0] : cw.wb[n & 1]; };
+
+    // n = 0: A step from Pi2^0 (cold w_i w_j^(k) or the cached plan), Lambda = 0
+    if ((rc = launch(SW_A | SW_LAM_ZERO | SW_COLD | (T == 1 ? SW_OBJ : 0), wbuf(0), wbuf(1)))) return rc;
+    bool lam_valid = false;
+    for (int it = 1; it < T; ++it) {
+        const int objf = (it == T - 1) ? SW_OBJ : 0;
+        const int lamz = lam_valid ? 0 : SW_LAM_ZERO;
+        if (!fix_x && it % tau == 0) {
+            // B step alone: Pi2^n into the plan buffer, Lambda^n
+            if ((rc = launch(SW_B | SW_LAM_OUT | lamz, wbuf(it), nullptr))) return rc;
+            lam_valid = true;
+            // Eq. (updatex) with Pi2^n and w^n, then the new cost
+            dim3 g((unsigned)maxch, (unsigned)d2_ceil_div(d, XU_DT), (unsigned)d2_ceil_div(m, XU_MT));
+            d2_time_begin(ctx, D2_KT_SUPPORT, st);
+            k_xpartial<<<g, XU_THREADS, 0, st>>>(members, bags->offsets, bags->supp, bags->vocab_idx,
+                                                  bags->vocab, d, m, plan, cw.chunks, cw.nchunks,
+                                                  static_cast<float*>(vxp));
+            D2_LAUNCH_CK(ctx, "k_xpartial");
+            k_xfinal<<<K, 256, 0, st>>>(m, d, cluster_offsets, cw.chunk_first, static_cast<float*>(vxp),
+                                        wbuf(it), x);
+            d2_time_end(ctx, st);
+            D2_LAUNCH_CK(ctx, "k_xfinal");
+            if ((rc = d2_prep_x(ctx, x, K, m, d, cw, st))) return rc;
+            if ((rc = d2_cost_rows(ctx, bags, members, P, K, m, cw, cost, false, st))) return rc;
+            // A step from Pi2^n
+            if ((rc = launch(SW_A | objf, wbuf(it), wbuf(it + 1)))) return rc;
+        } else {
+            if ((rc = launch(SW_B | SW_A | SW_LAM_OUT | lamz | objf, wbuf(it), wbuf(it + 1)))) return rc;
+            lam_valid = true;
+        }
+    }
+    // final B step: Pi2^T into the plan buffer (Lambda^T is not needed)
+    if ((rc = launch(SW_B | (lam_valid ? 0 : SW_LAM_ZERO), wbuf(T), nullptr))) return rc;
+    k_finish<<<(unsigned)d2_ceil_div(K, 128), 128, 0, st>>>(K, m, cluster_offsets, sa.pos_obj, wbuf(T), w,
+                                                            obj, true);
+    D2_LAUNCH_CK(ctx, "k_finish");
+    return D2_OK;
+}

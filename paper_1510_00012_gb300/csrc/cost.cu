@@ -1,0 +1,241 @@
+// Ragged squared-Euclidean cost matrices C(x_c, x^(k)) (Section 2 notation
+// list, c(.,.) under Eq. primal with p = 2) for every member of every cluster.
+//
+// One CTA per chunk of <= D2_CHUNK consecutive member positions of one
+// cluster.  The cluster's centred barycenter support xt = x_c - mu_c is staged
+// transposed in shared memory once per column tile; member rows are streamed
+// through a transposed, padded shared tile, centred by the same mu_c, and each
+// thread produces one full j-major row of C:
+//     C[j, i] = ||xt_i||^2 + ||y_j - mu_c||^2 - 2 <xt_i, y_j - mu_c>.
+// Centring removes the catastrophic cancellation of the plain norm expansion
+// when the data sit far from the origin.
+#include "d2_internal.cuh"
+
+#define COST_THREADS 256
+#define COST_DT 32
+#define COST_YPAD (COST_THREADS + 1)
+
+struct CostArgs {
+    const int64_t* members;
+    const int64_t* offsets;
+    const float* supp;
+    const int32_t* vidx;
+    const float* vocab;
+    int d, m;
+    const float* xt;   // K x m x d
+    const float* xn;   // K x m
+    const float* mu;   // K x d
+    const Chunk* chunks;
+    const int64_t* nchunks;
+    float* C;          // n x m
+    double* chunk_sum; // per chunk (or null)
+    int64_t* chunk_rows;
+};
+
+template <int MT>
+__global__ void __launch_bounds__(COST_THREADS) k_cost(CostArgs a) {
+    extern __shared__ float4 dyn4[];
+    float* xs = reinterpret_cast<float*>(dyn4);          // d x MT (transposed tile of xt)
+    float* ys = xs + (size_t)a.d * MT;                    // COST_DT x COST_YPAD
+    __shared__ int64_t s_rs[D2_CHUNK];
+    __shared__ int s_pre[D2_CHUNK + 1];
+    __shared__ int64_t s_row[COST_THREADS];
+    __shared__ double s_red[COST_THREADS / 32];
+
+    const int64_t q = blockIdx.x;
+    if (q >= *a.nchunks) return;
+    const Chunk ch = a.chunks[q];
+    const int c = ch.c;
+    const int nm = (int)(ch.p1 - ch.p0);
+    const int d = a.d, m = a.m;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    if (tid < nm) {
+        int64_t k = a.members[ch.p0 + tid];
+        s_rs[tid] = a.offsets[k];
+        s_pre[tid + 1] = (int)(a.offsets[k + 1] - a.offsets[k]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        s_pre[0] = 0;
+        for (int t = 0; t < nm; ++t) s_pre[t + 1] += s_pre[t];
+    }
+    __syncthreads();
+    const int R = s_pre[nm];
+    const float* mu = a.mu + (int64_t)c * d;
+    double rowsum_acc = 0.0;
+
+    for (int ct = 0; ct < m; ct += MT) {
+        __syncthreads();
+        for (int idx = tid; idx < d * MT; idx += COST_THREADS) {
+            int dd = idx / MT, i = idx - dd * MT;
+            xs[idx] = (ct + i < m) ? a.xt[((int64_t)c * m + ct + i) * d + dd] : 0.f;
+        }
+
+        for (int rbase = 0; rbase < R; rbase += COST_THREADS) {
+            __syncthreads();
+            {
+                int lr = rbase + tid;
+                int64_t grow = -1;
+                if (lr < R) {
+                    int lo = 0, hi = nm - 1;
+                    while (lo < hi) {
+                        int mid = (lo + hi + 1) >> 1;
+                        if (s_pre[mid] <= lr) lo = mid; else hi = mid - 1;
+                    }
+                    grow = s_rs[lo] + (lr - s_pre[lo]);
+                }
+                s_row[tid] = grow;
+            }
+            const bool valid = rbase + tid < R;
+            float acc[MT];
+#pragma unroll
+            for (int i = 0; i < MT; ++i) acc[i] = 0.f;
+            float yn = 0.f;
+            for (int d0 = 0; d0 < d; d0 += COST_DT) {
+                const int dt = min(COST_DT, d - d0);
+                __syncthreads();
+                for (int r = warp; r < COST_THREADS; r += COST_THREADS / 32) {
+                    int64_t g = s_row[r];
+                    if (g < 0) break;  // rows beyond R are at the end
+                    const float* yp = d2_row_ptr(a.supp, a.vidx, a.vocab, d, g);
+                    if (lane < dt) ys[lane * COST_YPAD + r] = yp[d0 + lane] - mu[d0 + lane];
+                }
+                __syncthreads();
+                if (valid) {
+                    for (int dd = 0; dd < dt; ++dd) {
+                        const float yv = ys[dd * COST_YPAD + tid];
+                        yn = fmaf(yv, yv, yn);
+                        const float* xr = xs + (size_t)(d0 + dd) * MT;
+                        if constexpr (MT % 4 == 0) {
+#pragma unroll
+                            for (int i = 0; i < MT; i += 4) {
+                                float4 xv = *reinterpret_cast<const float4*>(xr + i);
+                                acc[i] = fmaf(xv.x, yv, acc[i]);
+                                acc[i + 1] = fmaf(xv.y, yv, acc[i + 1]);
+                                acc[i + 2] = fmaf(xv.z, yv, acc[i + 2]);
+                                acc[i + 3] = fmaf(xv.w, yv, acc[i + 3]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < MT; ++i) acc[i] = fmaf(xr[i], yv, acc[i]);
+                        }
+                    }
+                }
+            }
+            if (valid) {
+                const int64_t g = s_row[tid];
+                float* out = a.C + g * m + ct;
+                const float* xnr = a.xn + (int64_t)c * m + ct;
+                const int nv = min(MT, m - ct);
+                float rs = 0.f;
+                if ((m & 3) == 0 && (MT % 4) == 0) {
+#pragma unroll
+                    for (int i = 0; i < MT; i += 4) {
+                        if (i < nv) {
+                            float4 v;
+                            v.x = fmaxf(fmaf(-2.f, acc[i], xnr[i] + yn), 0.f);
+                            v.y = fmaxf(fmaf(-2.f, acc[i + 1], xnr[i + 1] + yn), 0.f);
+                            v.z = fmaxf(fmaf(-2.f, acc[i + 2], xnr[i + 2] + yn), 0.f);
+                            v.w = fmaxf(fmaf(-2.f, acc[i + 3], xnr[i + 3] + yn), 0.f);
+                            *reinterpret_cast<float4*>(out + i) = v;
+                            rs += (v.x + v.y) + (v.z + v.w);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < MT; ++i) {
+                        if (i < nv) {
+                            float v = fmaxf(fmaf(-2.f, acc[i], xnr[i] + yn), 0.f);
+                            out[i] = v;
+                            rs += v;
+                        }
+                    }
+                }
+                rowsum_acc += (double)rs;
+            }
+        }
+    }
+    if (a.chunk_sum) {
+        double v = group_sum_d<32>(rowsum_acc);
+        __syncthreads();
+        if (lane == 0) s_red[warp] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int w = 0; w < COST_THREADS / 32; ++w) s += s_red[w];
+            a.chunk_sum[q] = s;
+            a.chunk_rows[q] = R;
+        }
+    }
+}
+
+template <int MT>
+static int launch_cost(d2_ctx* ctx, const CostArgs& a, int64_t maxch, cudaStream_t st) {
+    size_t smem = ((size_t)a.d * MT + (size_t)COST_DT * COST_YPAD) * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_cost<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return d2_cuda_fail(ctx, e, "k_cost smem attribute");
+    }
+    d2_time_begin(ctx, D2_KT_COST, st);
+    k_cost<MT><<<(unsigned)maxch, COST_THREADS, smem, st>>>(a);
+    d2_time_end(ctx, st);
+    D2_LAUNCH_CK(ctx, "k_cost");
+    return D2_OK;
+}
+
+int d2_cost_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t P, int K, int m,
+                 const ClusterWs& cw, float* C, bool want_sums, cudaStream_t st) {
+    int64_t maxch = d2_ceil_div(P, D2_CHUNK) + K + 1;
+    CostArgs a;
+    a.members = members;
+    a.offsets = b->offsets;
+    a.supp = b->supp;
+    a.vidx = b->vocab_idx;
+    a.vocab = b->vocab;
+    a.d = b->d;
+    a.m = m;
+    a.xt = cw.xt;
+    a.xn = cw.xn;
+    a.mu = cw.mu;
+    a.chunks = cw.chunks;
+    a.nchunks = cw.nchunks;
+    a.C = C;
+    a.chunk_sum = nullptr;
+    a.chunk_rows = nullptr;
+    if (want_sums) {
+        void* p = nullptr;
+        int rc = d2_ws(ctx, WS_CHUNK_SUM, (size_t)maxch * 16, &p);
+        if (rc) return rc;
+        a.chunk_sum = static_cast<double*>(p);
+        a.chunk_rows = reinterpret_cast<int64_t*>(static_cast<char*>(p) + (size_t)maxch * 8);
+    }
+    if ((size_t)b->d * 64 * 4 + COST_DT * COST_YPAD * 4 > 200 * 1024)
+        return d2_fail(ctx, D2_ENOTSUP, "d2_cost: support dimension %d too large for the cost tile", b->d);
+    if (m <= 8) return launch_cost<8>(ctx, a, maxch, st);
+    if (m <= 16) return launch_cost<16>(ctx, a, maxch, st);
+    if (m <= 32) return launch_cost<32>(ctx, a, maxch, st);
+    return launch_cost<64>(ctx, a, maxch, st);
+}
+
+extern "C" int d2_cost(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_offsets,
+                       const int64_t* members, int64_t P, int32_t K, int32_t m, const float* x,
+                       float* C_out, void* stream) {
+    if (!ctx) return D2_EINVAL;
+    int rc = d2_check_bags_host(ctx, bags);
+    if (rc) return rc;
+    if (K < 1 || m < 1 || m > 256 || P < 0 || !cluster_offsets || (P > 0 && !members) || !x || !C_out)
+        return d2_fail(ctx, D2_EINVAL, "d2_cost: need K >= 1, 1 <= m <= 256 and non-NULL arrays");
+    if (reinterpret_cast<uintptr_t>(C_out) & 15)
+        return d2_fail(ctx, D2_EINVAL, "d2_cost: C_out must be 16-byte aligned");
+    cudaStream_t st = d2_stream(stream);
+    ClusterWs cw;
+    rc = d2_cluster_ws(ctx, K, m, bags->d, P, &cw);
+    if (rc) return rc;
+    int32_t* pos_cluster = nullptr;
+    rc = d2_setup_clusters(ctx, cluster_offsets, P, K, &pos_cluster, &cw, st);
+    if (rc) return rc;
+    rc = d2_prep_x(ctx, x, K, m, bags->d, cw, st);
+    if (rc) return rc;
+    return d2_cost_rows(ctx, bags, members, P, K, m, cw, C_out, false, st);
+}

@@ -1,0 +1,160 @@
+// Internal definitions of libd2: the context, its device workspaces, error
+// plumbing and small device helpers shared by the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/d2.h"
+
+#define D2_LOG2E 1.4426950408889634
+
+// Workspace slots owned by a context; each grows on demand and is reused.
+enum WsSlot {
+    WS_LAM = 0,      // n x m floats: duals Lambda (j-major)
+    WS_COST,         // n x m floats: cost matrices C (j-major)
+    WS_POS_CLUSTER,  // P int32: cluster of each member position
+    WS_POS_R,        // P x m floats: member row sums r_k of Pi-tilde^(k,1)
+    WS_POS_PART,     // P x m doubles: per-member wtilde^(k) (or its sqrt)
+    WS_POS_OBJ,      // P doubles: per-member <C_k, Pi^(k,1)>
+    WS_CHUNKS,       // chunk table + per-cluster chunk ranges
+    WS_CHUNK_SUM,    // per-chunk FP64 cost sum and row count
+    WS_XPART,        // per-chunk partial support sums (m x d floats)
+    WS_CLUSTER,      // per-cluster small arrays (rho, beta, mu, xt, norms, w buffers, counters)
+    WS_SCAN,         // scratch for scans
+    WS_ASSIGN,       // assignment scratch
+    WS_CLUSTER_LOOP, // d2_cluster state (labels, plan cache, ...)
+    WS_PRUNE,        // pruning scratch
+    WS_NSLOTS
+};
+
+struct TimedLaunch {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+struct d2_ctx {
+    int device = 0;
+    std::string err;
+    void* ws[WS_NSLOTS] = {};
+    size_t ws_bytes[WS_NSLOTS] = {};
+    int* dev_flags = nullptr;       // device-side error flags (see D2F_*)
+    unsigned long long generation = 0;  // bumps whenever a workspace moves
+    int64_t launches = 0;           // kernels launched so far
+    bool timing = false;
+    std::vector<TimedLaunch> timed;     // pending event pairs
+    std::vector<cudaEvent_t> ev_pool;   // recycled events
+    double t_ms[D2_KT_COUNT] = {};
+    int64_t t_n[D2_KT_COUNT] = {};
+};
+
+// Event bracket around one launch when timing is on (no-ops otherwise).
+void d2_time_begin(d2_ctx* ctx, int kind, cudaStream_t st);
+void d2_time_end(d2_ctx* ctx, cudaStream_t st);
+
+// Device error flags (atomicOr'ed by kernels instead of faulting).
+#define D2F_BAD_OFFSETS   0x01
+#define D2F_BAD_WEIGHTS   0x02
+#define D2F_BAD_VOCAB     0x04
+#define D2F_BAD_MEMBER    0x08
+#define D2F_PIVOT_LIMIT   0x10
+#define D2F_BAD_SIZE      0x20
+
+int d2_fail(d2_ctx* ctx, int code, const char* fmt, ...);
+int d2_cuda_fail(d2_ctx* ctx, cudaError_t e, const char* what);
+// Pointer to workspace `slot` with at least `bytes` bytes (grows on demand).
+int d2_ws(d2_ctx* ctx, int slot, size_t bytes, void** out);
+
+#define D2_CK(ctx, call)                                          \
+    do {                                                          \
+        cudaError_t e__ = (call);                                 \
+        if (e__ != cudaSuccess) return d2_cuda_fail(ctx, e__, #call); \
+    } while (0)
+
+#define D2_LAUNCH_CK(ctx, what)                                   \
+    do {                                                          \
+        (ctx)->launches++;                                        \
+        cudaError_t e__ = cudaGetLastError();                     \
+        if (e__ != cudaSuccess) return d2_cuda_fail(ctx, e__, what); \
+    } while (0)
+
+static inline cudaStream_t d2_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+static inline int64_t d2_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Host-side validation of a bag descriptor (pointers and sizes only).
+int d2_check_bags_host(d2_ctx* ctx, const d2_bags* b);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+// Support row `row` of a bag set, dense or through the vocabulary.
+__device__ __forceinline__ const float* d2_row_ptr(const float* supp, const int32_t* vidx,
+                                                   const float* vocab, int d, int64_t row) {
+    return supp ? supp + row * (int64_t)d : vocab + (int64_t)vidx[row] * d;
+}
+
+template <int W>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int W>
+__device__ __forceinline__ float group_max(float v) {
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <int W>
+__device__ __forceinline__ double group_sum_d(double v) {
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Chunk of consecutive member positions [p0, p1) that all belong to cluster c.
+struct Chunk {
+    int64_t p0, p1;
+    int32_t c, pad;
+};
+
+// Members per chunk for the per-chunk kernels (cost build, support update).
+#define D2_CHUNK 64
+
+// Per-cluster layout inside WS_CLUSTER (offsets in bytes computed on host).
+struct ClusterWs {
+    float* rho;       // K
+    float* beta;      // K   log2(e) / rho
+    float* mu;        // K x d      centre used for the cost (mean of x_c)
+    float* xt;        // K x m x d  x_c - mu_c
+    float* xn;        // K x m      ||x_c,i - mu_c||^2
+    float* wb[2];     // K x m      double-buffered barycenter weights (FP32)
+    double* w64;      // K x m      FP64 weights of the last consensus
+    int* counters;    // K          arrivals per cluster in the current sweep
+    double* csum;     // K          FP64 cost sum (rho)
+    int64_t* nrows;   // K          support rows per cluster
+    int64_t* chunk_first;  // K+1   chunk range of each cluster
+    int64_t* nchunks;      // 1     total chunks
+    Chunk* chunks;         // chunk table (bound: ceil(P/CH) + K)
+};
+
+int d2_cluster_ws(d2_ctx* ctx, int64_t K, int m, int d, int64_t P, ClusterWs* cw);
+
+// Builds the member-position -> cluster map and the chunk table.
+int d2_setup_clusters(d2_ctx* ctx, const int64_t* cofs, int64_t P, int K, int32_t** pos_cluster,
+                      ClusterWs* cw, cudaStream_t st);
+
+// Centre and norms of each barycenter (mu_c, x_c - mu_c, ||x_c,i - mu_c||^2).
+int d2_prep_x(d2_ctx* ctx, const float* x, int K, int m, int d, const ClusterWs& cw, cudaStream_t st);
+
+// Cost rows of every member position; accumulates FP64 sums per cluster when csum.
+int d2_cost_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t P, int K, int m,
+                 const ClusterWs& cw, float* C, bool want_sums, cudaStream_t st);

@@ -1,0 +1,224 @@
+"""GPU parity of d2_cost and badmm_barycenter (through the C ABI) against the
+FP64 oracle on the same seeded inputs.
+
+Tolerances (stated by the target): plan entries and barycenter weights within
+1e-5 absolute, the objective within 1e-4 relative.  Supports are compared
+within 2e-4 x (1 + max |x|): they are plan-weighted means of FP32 data.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import badmm_barycenter as oracle_badmm, cost_matrix
+from tests.helpers import (cluster_members, compare_cluster, member_plan, run_gpu_badmm,
+                           split_clusters)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def d2():
+    import paper_1510_00012_gb300 as d2mod
+    from paper_1510_00012_gb300 import build
+    build.build()
+    return d2mod
+
+
+@pytest.fixture(scope="module")
+def ctx(d2):
+    return d2.Context(0)
+
+
+def x_tol(ref):
+    return 2e-4 * (1.0 + float(np.abs(ref["x"]).max()))
+
+
+def test_single_barycenter_circle_mixture(d2, ctx):
+    """N=64 distributions in d=2, m_k ~ U{4..16}, m=8, 200 iterations."""
+    bags = synth.circle_mixture_bags(0)
+    co = torch.tensor([0, bags.N], dtype=torch.int64)
+    mem = torch.arange(bags.N, dtype=torch.int64)
+    x0, w0 = synth.sample_initial_barycenters(1, bags, co, mem, 8)
+    gx, gw, gplan, gobj = run_gpu_badmm(d2, ctx, bags, co, mem, x0, w0, iters=200, tau=10)
+    _, members = cluster_members(bags, co, mem, 0)
+    ref = oracle_badmm(members, x0[0].double().numpy(), w0[0].double().numpy(), T=200, tau=10)
+    compare_cluster(bags, co, mem, 0, gx, gw, gplan, gobj, ref, x_tol=x_tol(ref))
+
+
+def ragged_case(seed, K, m, d=16, N=150, mk=(1, 24)):
+    bags = synth.gaussian_class_bags(seed, N, d, K - 2, mk=mk)
+    lab = bags.labels.clone()
+    lab[0] = K - 2                      # a single-member cluster
+    # cluster K-1 stays empty
+    co, mem = split_clusters(lab, K)
+    x0, w0 = synth.sample_initial_barycenters(seed + 1, bags, co, mem, m)
+    return bags, co, mem, x0, w0
+
+
+@pytest.mark.parametrize("m", [16, 12, 5, 32, 1])
+def test_batched_ragged_clusters(d2, ctx, m):
+    K = 7
+    bags, co, mem, x0, w0 = ragged_case(3, K, m)
+    gx, gw, gplan, gobj = run_gpu_badmm(d2, ctx, bags, co, mem, x0, w0, iters=31, tau=10)
+    for c in range(K):
+        ids, members = cluster_members(bags, co, mem, c)
+        if not ids:
+            assert torch.equal(gx[c], x0[c]) and torch.equal(gw[c], w0[c])
+            assert float(gobj[c]) == 0.0
+            continue
+        ref = oracle_badmm(members, x0[c].double().numpy(), w0[c].double().numpy(), T=31, tau=10)
+        compare_cluster(bags, co, mem, c, gx, gw, gplan, gobj, ref, x_tol=x_tol(ref))
+
+
+@pytest.mark.parametrize("variant", ["R2", "fix_x", "fix_w", "tau1", "T1"])
+def test_rules_and_modes(d2, ctx, variant):
+    K, m = 4, 8
+    bags, co, mem, x0, w0 = ragged_case(11, K, m, d=5, N=60, mk=(2, 12))
+    kw = dict(iters=25, tau=10)
+    okw = dict(T=25, tau=10)
+    if variant == "R2":
+        kw["rule"] = okw["rule"] = "R2"
+    elif variant == "fix_x":
+        kw["fix_x"] = okw["fix_x"] = True
+    elif variant == "fix_w":
+        kw["fix_w"] = okw["fix_w"] = True
+    elif variant == "tau1":
+        kw["tau"] = okw["tau"] = 1
+    elif variant == "T1":
+        kw["iters"] = okw["T"] = 1
+    gx, gw, gplan, gobj = run_gpu_badmm(d2, ctx, bags, co, mem, x0, w0, **kw)
+    for c in range(K):
+        ids, members = cluster_members(bags, co, mem, c)
+        if not ids:
+            continue
+        ref = oracle_badmm(members, x0[c].double().numpy(), w0[c].double().numpy(), **okw)
+        compare_cluster(bags, co, mem, c, gx, gw, gplan, gobj, ref, x_tol=x_tol(ref))
+
+
+def test_fixed_rho_override(d2, ctx):
+    K, m = 3, 8
+    bags, co, mem, x0, w0 = ragged_case(12, K, m, d=4, N=40, mk=(2, 10))
+    gx, gw, gplan, gobj = run_gpu_badmm(d2, ctx, bags, co, mem, x0, w0, iters=12, tau=5, rho=3.5)
+    for c in range(K):
+        ids, members = cluster_members(bags, co, mem, c)
+        if ids:
+            ref = oracle_badmm(members, x0[c].double().numpy(), w0[c].double().numpy(), T=12, tau=5,
+                               rho=3.5)
+            compare_cluster(bags, co, mem, c, gx, gw, gplan, gobj, ref, x_tol=x_tol(ref))
+
+
+def test_warm_start_chain(d2, ctx):
+    """Second call warm-starts half the members from each side's own first call."""
+    K, m = 3, 8
+    bags, co, mem, x0, w0 = ragged_case(13, K, m, d=6, N=50, mk=(2, 10))
+    gx, gw, gplan, gobj = run_gpu_badmm(d2, ctx, bags, co, mem, x0, w0, iters=20, tau=10)
+    warm = torch.zeros(bags.N, dtype=torch.bool)
+    warm[::2] = True
+    gx2, gw2, gplan2, gobj2 = run_gpu_badmm(d2, ctx, bags, co, mem, gx, gw, plan0=gplan, warm=warm,
+                                            iters=15, tau=10)
+    for c in range(K):
+        ids, members = cluster_members(bags, co, mem, c)
+        if not ids:
+            continue
+        r1 = oracle_badmm(members, x0[c].double().numpy(), w0[c].double().numpy(), T=20, tau=10)
+        r2 = oracle_badmm(members, r1["x"], r1["w"], T=15, tau=10, plan0=r1["P2"],
+                          warm=[bool(warm[k]) for k in ids])
+        compare_cluster(bags, co, mem, c, gx2, gw2, gplan2, gobj2, r2, x_tol=x_tol(r2))
+
+
+def test_vocabulary_bags(d2, ctx):
+    """Supports stored as indices into a word table (d=48)."""
+    bags = synth.document_bags(5, 80, V=400, d=48, mk=(3, 20))
+    K, m = 3, 8
+    lab = torch.arange(bags.N) % K
+    co, mem = split_clusters(lab, K)
+    x0, w0 = synth.sample_initial_barycenters(6, bags, co, mem, m)
+    gx, gw, gplan, gobj = run_gpu_badmm(d2, ctx, bags, co, mem, x0, w0, iters=25, tau=10)
+    for c in range(K):
+        ids, members = cluster_members(bags, co, mem, c)
+        ref = oracle_badmm(members, x0[c].double().numpy(), w0[c].double().numpy(), T=25, tau=10)
+        compare_cluster(bags, co, mem, c, gx, gw, gplan, gobj, ref, x_tol=x_tol(ref))
+
+
+def test_deterministic(d2, ctx):
+    K, m = 5, 16
+    bags, co, mem, x0, w0 = ragged_case(14, K, m)
+    a = run_gpu_badmm(d2, ctx, bags, co, mem, x0, w0, iters=21, tau=10)
+    b = run_gpu_badmm(d2, ctx, bags, co, mem, x0, w0, iters=21, tau=10)
+    for u, v in zip(a, b):
+        assert torch.equal(u, v)
+
+
+@pytest.mark.parametrize("m,d", [(8, 2), (16, 16), (12, 7), (64, 300), (100, 3)])
+def test_cost_matches_definition(d2, ctx, m, d):
+    K = 3
+    bags = synth.gaussian_class_bags(20 + m, 40, d, K, mk=(1, 30), mu_sigma=4.0)
+    co, mem = split_clusters(bags.labels, K)
+    x0, _ = synth.sample_initial_barycenters(21, bags, co, mem, m)
+    x0 = x0 + 3.0  # off-centre barycenters
+    db = d2.DeviceBags.from_synth(bags)
+    C = d2.d2_cost(ctx, db, co.cuda(), mem.cuda(), x0.cuda()).cpu()
+    for c in range(K):
+        ids, members = cluster_members(bags, co, mem, c)
+        for k, (y, _) in zip(ids, members):
+            ref = cost_matrix(x0[c].double().numpy(), y)
+            got = member_plan(C, bags.offsets, k)
+            np.testing.assert_allclose(got, ref, rtol=2e-5, atol=2e-5 * (1 + ref.max()))
+
+
+def test_invalid_arguments(d2, ctx):
+    bags = synth.circle_mixture_bags(1, N=4)
+    db = d2.DeviceBags.from_synth(bags)
+    co = torch.tensor([0, 4], dtype=torch.int64, device="cuda")
+    mem = torch.arange(4, dtype=torch.int64, device="cuda")
+    x = torch.zeros(1, 300, 2, device="cuda")
+    w = torch.full((1, 300), 1 / 300, device="cuda")
+    with pytest.raises(d2.D2Error) as e:
+        d2.badmm_barycenter(ctx, db, co, mem, x, w)
+    assert e.value.code == d2.D2_EINVAL
+    bad = bags.wt.clone()
+    bad[0] += 0.5
+    db2 = d2.DeviceBags(db.offsets, bad.cuda(), db.d, supp=db.supp)
+    with pytest.raises(d2.D2Error) as e:
+        d2.d2_check_bags(ctx, db2)
+    assert e.value.code == d2.D2_EINVAL
+    d2.d2_check_bags(ctx, db)
+
+
+def test_full_size_ragged_clusters(d2, ctx):
+    """4,096 clusters with log-uniform member counts in [16, 4096] (~3M
+    distributions), d=64, m_k ~ U{16..64}, m=32, T=100: the launch
+    configuration the benchmark times.  Checks plan marginals on every cluster
+    and full parity on three sampled clusters against the oracle."""
+    bags, co, mem = synth.ragged_cluster_bags(7, 4096, device="cuda")
+    m = 32
+    x0, w0 = synth.sample_initial_barycenters(8, bags, co, mem, m)
+    db = d2.DeviceBags.from_synth(bags)
+    x, w = x0.clone(), w0.clone()
+    plan = torch.empty(bags.n, m, dtype=torch.float32, device="cuda")
+    d2.badmm_barycenter(ctx, db, co, mem, x, w, plan, None, d2.badmm_opts(iters=100, tau=10),
+                        obj := torch.empty(4096, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    # Pi^(k,2) row sums equal w_i for every member (Eq. badmmc1), w in the simplex
+    owner = torch.repeat_interleave(torch.arange(bags.N, device="cuda"), bags.offsets[1:] - bags.offsets[:-1])
+    rows = torch.zeros(bags.N, m, dtype=torch.float64, device="cuda").index_add_(0, owner, plan.double())
+    clus = torch.repeat_interleave(torch.arange(4096, device="cuda"), co[1:] - co[:-1])
+    assert torch.allclose(rows, w[clus].double(), atol=1e-6, rtol=0)
+    assert torch.allclose(w.double().sum(1), torch.ones(4096, dtype=torch.float64, device="cuda"), atol=1e-6)
+    assert torch.isfinite(obj).all() and (obj > 0).all()
+    sizes = (co[1:] - co[:-1]).cpu()
+    order = torch.argsort(sizes)
+    picks = [int(order[0]), int(order[2048]), int(order[3000])]
+    host = bags.to("cpu")
+    gx, gw, gplan, gobj = x.cpu(), w.cpu(), None, obj.cpu()
+    for c in picks:
+        ids, members = cluster_members(host, co, mem, c)
+        ref = oracle_badmm(members, x0[c].double().cpu().numpy(), w0[c].double().cpu().numpy(),
+                           T=100, tau=10)
+        np.testing.assert_allclose(gw[c].double().numpy(), ref["w"], atol=1e-5, rtol=0)
+        assert abs(float(gobj[c]) - ref["obj"]) <= 1e-4 * ref["obj"]
+        for t, k in enumerate(ids):
+            a, b = int(host.offsets[k]), int(host.offsets[k + 1])
+            got = plan[a:b].double().cpu().numpy().T
+            np.testing.assert_allclose(got, ref["P2"][t], atol=1e-5, rtol=0)
