@@ -245,3 +245,44 @@ def badmm_barycenter(ctx, bags, cluster_offsets, members, x, w, plan=None, warm_
                                      members.numel(), K, m, _ptr(x), _ptr(w), _ptr(plan),
                                      _ptr(warm_mask), ctypes.byref(opts), _ptr(obj), _stream()))
     return x, w, plan, obj
+
+
+def d2_merge_init(ctx, bags, ids, m):
+    """Eq. (merge) reduction of the bags `ids` to m points -> x (cnt, m, d), w (cnt, m)."""
+    _need(ids, torch.int64, "ids")
+    cnt = ids.numel()
+    x = torch.empty(cnt, m, bags.d, dtype=torch.float32, device=ids.device)
+    w = torch.empty(cnt, m, dtype=torch.float32, device=ids.device)
+    ctx.check(lib().d2_merge_init(ctx.h, bags.ref(), _ptr(ids), cnt, m, _ptr(x), _ptr(w), _stream()))
+    return x, w
+
+
+def d2_assign(ctx, bags, x, w, prune=None, want_stats=False):
+    """Exact (or pruned) assignment: labels (N int32), W^2 to the chosen centroid (N float32)[, stats]."""
+    _need(x, torch.float32, "x")
+    _need(w, torch.float32, "w")
+    K, m = x.shape[0], x.shape[1]
+    labels = torch.empty(bags.N, dtype=torch.int32, device=x.device)
+    dist = torch.empty(bags.N, dtype=torch.float32, device=x.device)
+    st = (c_int64 * 3)() if want_stats else None
+    ctx.check(lib().d2_assign(ctx.h, bags.ref(), K, m, _ptr(x), _ptr(w),
+                              None if prune is None else prune.h, _ptr(labels), _ptr(dist),
+                              st, _stream()))
+    if want_stats:
+        return labels, dist, dict(exact_solves=st[0], fallbacks=st[1], limit_hits=st[2])
+    return labels, dist
+
+
+def d2_cluster(ctx, bags, K, m, seed, rounds, opts=None, prune=None):
+    """Algorithm 1 on the device -> (x (K,m,d), w (K,m), labels (N), obj_per_round list)."""
+    dev = bags.offsets.device
+    x = torch.empty(K, m, bags.d, dtype=torch.float32, device=dev)
+    w = torch.empty(K, m, dtype=torch.float32, device=dev)
+    labels = torch.empty(bags.N, dtype=torch.int32, device=dev)
+    objs = (c_double * rounds)()
+    if opts is None:
+        opts = badmm_opts()
+    ctx.check(lib().d2_cluster(ctx.h, bags.ref(), K, m, c_uint64(seed), rounds, ctypes.byref(opts),
+                               None if prune is None else prune.h, _ptr(x), _ptr(w), _ptr(labels),
+                               objs, _stream()))
+    return x, w, labels, list(objs)

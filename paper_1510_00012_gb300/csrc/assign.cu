@@ -1,0 +1,412 @@
+// Exact W^2 (the transportation LP of Eq. primal) for many (centroid, bag)
+// pairs, and the assignment step of Algorithm 1 (argmin over centroids).
+//
+// One warp solves one pair with successive shortest paths on the residual
+// bipartite graph (sources: the m centroid points with supplies w_i; sinks:
+// the m_k bag points with demands w_j^(k)).  Node potentials keep every
+// residual arc's reduced cost non-negative, so each phase is a dense Dijkstra
+// (warp argmin over unvisited nodes, lanes relax one node's arcs in
+// parallel) from all sources with remaining supply to the nearest sink with
+// remaining demand, followed by an augmentation of the largest feasible amount
+// along that path.  Reduced-cost optimality holds throughout, so the final
+// flow is optimal; unlike a simplex there are no degenerate pivots.  Start:
+// pot_i = 0, pot_j = min_i C_ij and every sink sends what it can to its
+// cheapest source (those arcs have zero reduced cost).  Costs, flows and
+// potentials are FP32; the final cost sum_ij f_ij C_ij is accumulated in FP64.
+#include <algorithm>
+#include <cstring>
+
+#include "d2_internal.cuh"
+
+#define AS_DC 8        // support dimensions staged per step of the cost build
+#define AS_INF 3.0e38f
+
+struct AssignArgs {
+    const int64_t* offsets;
+    const float* supp;
+    const int32_t* vidx;
+    const float* vocab;
+    const float* wt;
+    int d;
+    const float* x;    // K x m x d
+    const float* w;    // K x m
+    int m, K, nmax;
+    // pair enumeration
+    int mode;                  // 0: all N*K pairs; 1: explicit list; 2: all K for listed bags
+    int64_t npairs;            // mode 0/1 host count (mode 1: upper bound if npairs_dev)
+    const int64_t* npairs_dev; // mode 1/2: device count (pairs, or bags for mode 2)
+    const int64_t* pair_bag;   // mode 1
+    const int32_t* pair_cent;  // mode 1
+    const int64_t* bag_list;   // mode 2
+    float* out;                // mode 0/2: out[bag*K + cent]; mode 1: out[pair]
+    int* flags;
+    int64_t* pivot_fail;       // count of pairs that hit the phase limit
+    int max_phase;
+    size_t warp_bytes;
+};
+
+struct WarpMem {
+    float* C;      // m x n
+    float* F;      // m x n
+    float* pot;    // V
+    float* dist;   // V
+    float* exc;    // V
+    short* pred;   // V
+    unsigned char* vis;  // V
+    float* xs;     // AS_DC x m
+    float* ys;     // AS_DC x n
+};
+
+__device__ __forceinline__ void warp_argmin(float& v, int& idx) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float ov = __shfl_xor_sync(0xffffffffu, v, o);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ov < v || (ov == v && oi < idx)) {
+            v = ov;
+            idx = oi;
+        }
+    }
+}
+
+// Solve one pair; returns W^2 (all lanes).
+__device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int cent, bool& hit_limit) {
+    const int lane = threadIdx.x & 31;
+    const int m = a.m, d = a.d;
+    const int64_t r0 = a.offsets[bag];
+    const int n = (int)(a.offsets[bag + 1] - r0);
+    const int V = m + n;
+    const float* xc = a.x + (int64_t)cent * m * d;
+
+    // ---- cost C[i][j] = sum_dd (x_i - y_j)^2 by direct differences
+    for (int e = lane; e < m * n; e += 32) s.C[e] = 0.f;
+    for (int d0 = 0; d0 < d; d0 += AS_DC) {
+        const int dc = min(AS_DC, d - d0);
+        __syncwarp();
+        for (int e = lane; e < dc * m; e += 32) {
+            int t = e / m, i = e - t * m;
+            s.xs[t * m + i] = xc[(int64_t)i * d + d0 + t];
+        }
+        for (int e = lane; e < dc * n; e += 32) {
+            int t = e / n, j = e - t * n;
+            s.ys[t * n + j] = d2_row_ptr(a.supp, a.vidx, a.vocab, d, r0 + j)[d0 + t];
+        }
+        __syncwarp();
+        for (int e = lane; e < m * n; e += 32) {
+            int i = e / n, j = e - i * n;
+            float acc = s.C[e];
+            for (int t = 0; t < dc; ++t) {
+                float df = s.xs[t * m + i] - s.ys[t * n + j];
+                acc = fmaf(df, df, acc);
+            }
+            s.C[e] = acc;
+        }
+    }
+    // ---- initial state
+    for (int e = lane; e < m * n; e += 32) s.F[e] = 0.f;
+    for (int v = lane; v < V; v += 32) {
+        s.exc[v] = (v < m) ? a.w[(int64_t)cent * m + v] : a.wt[r0 + (v - m)];
+        s.pot[v] = 0.f;
+    }
+    __syncwarp();
+    // pot_j = min_i C_ij; column-minimum argmin per sink (first minimum)
+    for (int j = lane; j < n; j += 32) {
+        float mn = AS_INF;
+        int am = 0;
+        for (int i = 0; i < m; ++i) {
+            float c = s.C[i * n + j];
+            if (c < mn) {
+                mn = c;
+                am = i;
+            }
+        }
+        s.pot[m + j] = mn;
+        s.pred[m + j] = (short)am;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        for (int j = 0; j < n; ++j) {
+            int i = s.pred[m + j];
+            float f = fminf(s.exc[m + j], s.exc[i]);
+            if (f > 0.f) {
+                s.F[i * n + j] += f;
+                s.exc[m + j] -= f;
+                s.exc[i] -= f;
+            }
+        }
+    }
+    __syncwarp();
+    const float tol = 1e-9f;
+    int phase = 0;
+    hit_limit = false;
+    for (;;) {
+        // anything left to route?
+        bool src = false, snk = false;
+        for (int v = lane; v < V; v += 32) {
+            if (s.exc[v] > tol) {
+                if (v < m) src = true; else snk = true;
+            }
+        }
+        src = __any_sync(0xffffffffu, src);
+        snk = __any_sync(0xffffffffu, snk);
+        if (!src || !snk) break;
+        if (++phase > a.max_phase) {
+            hit_limit = true;
+            break;
+        }
+        // ---- Dijkstra from every source with remaining supply
+        for (int v = lane; v < V; v += 32) {
+            s.dist[v] = (v < m && s.exc[v] > tol) ? 0.f : AS_INF;
+            s.vis[v] = 0;
+            s.pred[v] = -1;
+        }
+        __syncwarp();
+        int target = -1;
+        for (int it = 0; it < V; ++it) {
+            float bv = AS_INF;
+            int bi = 0x7fffffff;
+            for (int v = lane; v < V; v += 32) {
+                if (!s.vis[v]) {
+                    float dv = s.dist[v];
+                    if (dv < bv) {
+                        bv = dv;
+                        bi = v;
+                    }
+                }
+            }
+            warp_argmin(bv, bi);
+            if (bv >= AS_INF) break;
+            const int u = bi;
+            const float du = bv;
+            __syncwarp();
+            if (lane == 0) s.vis[u] = 1;
+            if (u >= m && s.exc[u] > tol) {
+                target = u;
+                break;
+            }
+            if (u < m) {
+                const float pu = s.pot[u];
+                for (int j = lane; j < n; j += 32) {
+                    const int v = m + j;
+                    if (!s.vis[v]) {
+                        float rc = fmaxf(s.C[u * n + j] + pu - s.pot[v], 0.f);
+                        float nd = du + rc;
+                        if (nd < s.dist[v]) {
+                            s.dist[v] = nd;
+                            s.pred[v] = (short)u;
+                        }
+                    }
+                }
+            } else {
+                const int j = u - m;
+                const float pu = s.pot[u];
+                for (int i = lane; i < m; i += 32) {
+                    if (!s.vis[i] && s.F[i * n + j] > tol) {
+                        float rc = fmaxf(-s.C[i * n + j] + pu - s.pot[i], 0.f);
+                        float nd = du + rc;
+                        if (nd < s.dist[i]) {
+                            s.dist[i] = nd;
+                            s.pred[i] = (short)u;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        __syncwarp();
+        if (target < 0) {
+            hit_limit = true;  // no augmenting path (cannot happen with balanced supplies)
+            break;
+        }
+        // ---- potentials: pot += min(dist, dist[target])
+        const float dt = s.dist[target];
+        for (int v = lane; v < V; v += 32) s.pot[v] += s.vis[v] ? fminf(s.dist[v], dt) : dt;
+        __syncwarp();
+        // ---- augment along the path (lane 0)
+        if (lane == 0) {
+            float delta = s.exc[target];
+            int v = target, src_node = target;
+            for (int guard = 0; guard <= V; ++guard) {
+                int p = s.pred[v];
+                if (p < 0) {
+                    src_node = v;
+                    break;
+                }
+                if (v < m) {  // reached source v by the backward arc (v, p - m)
+                    delta = fminf(delta, s.F[v * n + (p - m)]);
+                }
+                v = p;
+            }
+            delta = fminf(delta, s.exc[src_node]);
+            v = target;
+            for (int guard = 0; guard <= V; ++guard) {
+                int p = s.pred[v];
+                if (p < 0) break;
+                if (v >= m) {  // forward arc p -> v
+                    s.F[p * n + (v - m)] += delta;
+                } else {       // backward arc: flow on (v, p - m) decreases
+                    float f = s.F[v * n + (p - m)] - delta;
+                    s.F[v * n + (p - m)] = f > 0.f ? f : 0.f;
+                }
+                v = p;
+            }
+            s.exc[target] -= delta;
+            s.exc[src_node] -= delta;
+        }
+        __syncwarp();
+    }
+    // ---- cost of the flow, FP64
+    double acc = 0.0;
+    for (int e = lane; e < m * n; e += 32) acc += (double)s.F[e] * (double)s.C[e];
+    acc = group_sum_d<32>(acc);
+    return acc;
+}
+
+__global__ void k_w2_pairs(AssignArgs a) {
+    extern __shared__ float4 dyn4[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    char* base = reinterpret_cast<char*>(dyn4) + (size_t)wib * a.warp_bytes;
+    const int m = a.m, n = a.nmax, V = m + n;
+    WarpMem s;
+    s.C = reinterpret_cast<float*>(base);
+    s.F = s.C + m * n;
+    s.pot = s.F + m * n;
+    s.dist = s.pot + V;
+    s.exc = s.dist + V;
+    s.xs = s.exc + V;
+    s.ys = s.xs + AS_DC * m;
+    s.pred = reinterpret_cast<short*>(s.ys + AS_DC * n);
+    s.vis = reinterpret_cast<unsigned char*>(s.pred + V);
+
+    int64_t total;
+    if (a.mode == 0) total = a.npairs;
+    else if (a.mode == 1) total = a.npairs_dev ? min(*a.npairs_dev, a.npairs) : a.npairs;
+    else total = (*a.npairs_dev) * a.K;
+    const int64_t nwarps = (int64_t)gridDim.x * wpb;
+    for (int64_t p = (int64_t)blockIdx.x * wpb + wib; p < total; p += nwarps) {
+        int64_t bag;
+        int cent;
+        int64_t slot;
+        if (a.mode == 0) {
+            bag = p / a.K;
+            cent = (int)(p - bag * a.K);
+            slot = p;
+        } else if (a.mode == 1) {
+            bag = a.pair_bag[p];
+            cent = a.pair_cent[p];
+            slot = p;
+        } else {
+            int64_t b = p / a.K;
+            cent = (int)(p - b * a.K);
+            bag = a.bag_list[b];
+            slot = bag * a.K + cent;
+        }
+        bool lim = false;
+        double v = solve_pair(a, s, bag, cent, lim);
+        if (lane == 0) {
+            a.out[slot] = (float)v;
+            if (lim) {
+                atomicOr(a.flags, D2F_PIVOT_LIMIT);
+                atomicAdd(reinterpret_cast<unsigned long long*>(a.pivot_fail), 1ull);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// labels[k] = argmin_i D[k][i] (ties -> lowest i), dist[k] = min
+__global__ void k_argmin_rows(const float* D, int64_t N, int K, int32_t* labels, float* dist) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const float* r = D + k * K;
+    float b = r[0];
+    int bi = 0;
+    for (int i = 1; i < K; ++i) {
+        float v = r[i];
+        if (v < b) {
+            b = v;
+            bi = i;
+        }
+    }
+    labels[k] = bi;
+    dist[k] = b;
+}
+
+size_t d2_assign_warp_bytes(int m, int nmax) {
+    const int V = m + nmax;
+    size_t b = (size_t)(2 * m * nmax + 3 * V + AS_DC * (m + nmax)) * 4 + (size_t)V * 2 + V;
+    return (b + 15) & ~(size_t)15;
+}
+
+// Launch the pair solver; grid is a bound (persistent stride loop).
+int d2_launch_pairs(d2_ctx* ctx, AssignArgs a, int64_t max_units, cudaStream_t st) {
+    a.warp_bytes = d2_assign_warp_bytes(a.m, a.nmax);
+    if (a.warp_bytes > 200 * 1024)
+        return d2_fail(ctx, D2_ENOTSUP, "d2_assign: m * max_mk too large for the per-warp tableau");
+    int wpb = (int)std::min<size_t>(4, std::max<size_t>(1, (200 * 1024) / a.warp_bytes));
+    size_t smem = a.warp_bytes * wpb;
+    cudaError_t e = cudaFuncSetAttribute(k_w2_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return d2_cuda_fail(ctx, e, "k_w2_pairs smem attribute");
+    int dev_sms = 152;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_w2_pairs, wpb * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t want = d2_ceil_div(std::max<int64_t>(max_units, 1), wpb);
+    int64_t cap = (int64_t)dev_sms * per_sm * 8;
+    unsigned grid = (unsigned)std::max<int64_t>(1, std::min(want, cap));
+    a.max_phase = 8 * (a.m + a.nmax) + 64;
+    d2_time_begin(ctx, D2_KT_ASSIGN, st);
+    k_w2_pairs<<<grid, wpb * 32, smem, st>>>(a);
+    d2_time_end(ctx, st);
+    D2_LAUNCH_CK(ctx, "k_w2_pairs");
+    return D2_OK;
+}
+
+AssignArgs d2_assign_args(const d2_bags* b, int K, int m, const float* x, const float* w, int* flags,
+                          int64_t* pivot_fail) {
+    AssignArgs a;
+    memset(&a, 0, sizeof(a));
+    a.offsets = b->offsets;
+    a.supp = b->supp;
+    a.vidx = b->vocab_idx;
+    a.vocab = b->vocab;
+    a.wt = b->wt;
+    a.d = b->d;
+    a.x = x;
+    a.w = w;
+    a.m = m;
+    a.K = K;
+    a.nmax = b->max_mk;
+    a.flags = flags;
+    a.pivot_fail = pivot_fail;
+    return a;
+}
+
+int d2_argmin_rows(d2_ctx* ctx, const float* D, int64_t N, int K, int32_t* labels, float* dist,
+                   cudaStream_t st) {
+    k_argmin_rows<<<(unsigned)d2_ceil_div(N, 256), 256, 0, st>>>(D, N, K, labels, dist);
+    D2_LAUNCH_CK(ctx, "k_argmin_rows");
+    return D2_OK;
+}
+
+__global__ void k_add_i64(int64_t* p, int64_t v) { *p += v; }
+
+// all N x K pairs, then argmin per bag
+int d2_assign_exact(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w,
+                    int32_t* labels, float* dist, int64_t* counters, cudaStream_t st) {
+    const int64_t N = b->N;
+    void* pD = nullptr;
+    int rc = d2_ws(ctx, WS_ASSIGN, (size_t)N * K * 4, &pD);
+    if (rc) return rc;
+    float* D = static_cast<float*>(pD);
+    AssignArgs a = d2_assign_args(b, K, m, x, w, ctx->dev_flags, counters + 2);
+    a.mode = 0;
+    a.npairs = N * K;
+    a.out = D;
+    if ((rc = d2_launch_pairs(ctx, a, N * K, st))) return rc;
+    k_add_i64<<<1, 1, 0, st>>>(counters, N * K);
+    D2_LAUNCH_CK(ctx, "k_add_i64");
+    return d2_argmin_rows(ctx, D, N, K, labels, dist, st);
+}

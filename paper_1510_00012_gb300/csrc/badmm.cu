@@ -25,7 +25,7 @@
 // arithmetic and keeps FP32 from underflowing on far-away points.
 //
 // Weight consensus (Eq. badmmw / badmmw2).  Each warp writes its member's
-// wtilde^(k) in FP64; the last CTA to finish a cluster (arrival counter per
+// wtilde^(k) (FP32, normalised by one reciprocal); the last CTA to finish a cluster (arrival counter per
 // cluster, no waiting) sums the cluster's members in a fixed order in FP64,
 // normalises, and publishes w^{n+1} for the next launch.  The result does not
 // depend on CTA scheduling.
@@ -54,7 +54,7 @@ struct SweepArgs {
     float* lam;
     const float* cost;
     float* pos_r;
-    double* pos_part;
+    float* pos_part;
     double* pos_obj;
     const float* w_cur;
     float* w_next;       // null: weights fixed, no consensus
@@ -72,21 +72,31 @@ struct SweepArgs {
 
 template <int VEC>
 struct VecIO;
+// plan, dual and cost rows are touched once per launch: stream them past L1
+// and mark them evict-first in L2
 template <>
 struct VecIO<4> {
     static __device__ __forceinline__ void ld(const float* p, float* v) {
-        float4 t = *reinterpret_cast<const float4*>(p);
+        float4 t = __ldcs(reinterpret_cast<const float4*>(p));
         v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
     }
     static __device__ __forceinline__ void st(float* p, const float* v) {
-        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+        __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
     }
 };
 template <>
 struct VecIO<1> {
-    static __device__ __forceinline__ void ld(const float* p, float* v) { v[0] = *p; }
-    static __device__ __forceinline__ void st(float* p, const float* v) { *p = v[0]; }
+    static __device__ __forceinline__ void ld(const float* p, float* v) { v[0] = __ldcs(p); }
+    static __device__ __forceinline__ void st(float* p, const float* v) { __stcs(p, v[0]); }
 };
+
+// 2^x by the hardware approximation (relative error ~2^-22, flushes
+// subnormal results to zero)
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // fixed-order FP64 consensus of cluster c by the whole CTA
 __device__ void consensus_cluster(const SweepArgs& a, int c, double* s_acc) {
@@ -97,7 +107,7 @@ __device__ void consensus_cluster(const SweepArgs& a, int c, double* s_acc) {
     const int64_t p0 = a.cofs[c], p1 = a.cofs[c + 1];
     double acc = 0.0;
     if (g < G) {
-        for (int64_t p = p0 + g; p < p1; p += G) acc += __ldcg(a.pos_part + p * m + i);
+        for (int64_t p = p0 + g; p < p1; p += G) acc += (double)__ldcg(a.pos_part + p * m + i);
         s_acc[g * m + i] = acc;
     }
     __syncthreads();
@@ -167,31 +177,42 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
         for (int x = 0; x < NE; ++x) racc[x] = 0.f;
         float objacc = 0.f;
 
-        for (int base = 0; base < mk; base += RPW) {
+        // one row group (RPW rows) per step; the next group's loads are issued
+        // before the current group is computed
+        const bool ldP = doB || !cold, ldL = !(fl & SW_LAM_ZERO);
+        float pin[NE], lin[NE], cin[NE], wkj;
+        auto load_step = [&](int base, float* P, float* L, float* Cc, float& wk) {
             const int j = base + sub;
-            const bool rv = j < mk;
-            const int64_t rowoff = (row0 + (rv ? j : 0)) * (int64_t)m;
-            float pin[NE], lin[NE], cin[NE];
 #pragma unroll
-            for (int x = 0; x < NE; ++x) { pin[x] = 0.f; lin[x] = 0.f; cin[x] = 0.f; }
-            const float wkj = rv ? a.wt[row0 + j] : 0.f;
-            if (rv) {
+            for (int x = 0; x < NE; ++x) { P[x] = 0.f; L[x] = 0.f; Cc[x] = 0.f; }
+            wk = 0.f;
+            if (j < mk) {
+                const int64_t ro = (row0 + j) * (int64_t)m;
+                wk = __ldg(a.wt + row0 + j);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     const int col0 = (cl + LPR * v) * VEC;
                     if (col0 < m) {
-                        if (doB || !cold) VecIO<VEC>::ld(a.plan + rowoff + col0, pin + v * VEC);
-                        if (!(fl & SW_LAM_ZERO)) VecIO<VEC>::ld(a.lam + rowoff + col0, lin + v * VEC);
-                        if (doA) VecIO<VEC>::ld(a.cost + rowoff + col0, cin + v * VEC);
+                        if (ldP) VecIO<VEC>::ld(a.plan + ro + col0, P + v * VEC);
+                        if (ldL) VecIO<VEC>::ld(a.lam + ro + col0, L + v * VEC);
+                        if (doA) VecIO<VEC>::ld(a.cost + ro + col0, Cc + v * VEC);
                     }
                 }
             }
+        };
+        load_step(0, pin, lin, cin, wkj);
+        for (int base = 0; base < mk; base += RPW) {
+            float npin[NE], nlin[NE], ncin[NE], nwkj;
+            if (base + RPW < mk) load_step(base + RPW, npin, nlin, ncin, nwkj);
+            const int j = base + sub;
+            const bool rv = j < mk;
+            const int64_t rowoff = (row0 + (rv ? j : 0)) * (int64_t)m;
             // ---- B step: Pi2^n and Lambda^n from Pi1^n and Lambda^{n-1}
             float p2[NE], l2[NE];
 #pragma unroll
             for (int x = 0; x < NE; ++x) {
                 if (doB) {
-                    const float pt = fmaf(pin[x], exp2f(lin[x] * beta), eps);
+                    const float pt = fmaf(pin[x], fast_exp2(lin[x] * beta), eps);
                     p2[x] = pt * coef[x];
                     l2[x] = fmaf(rho, pin[x] - p2[x], lin[x]);
                 } else {
@@ -209,12 +230,12 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
                     if (ok[x]) s = fmaxf(s, ex[x]);
                 }
                 s = group_max<LPR>(s);
-                const float epss = exp2f(fminf(a.log2eps - s, 126.f));
+                const float epss = fast_exp2(fminf(a.log2eps - s, 126.f));
                 float t1[NE];
                 float rs = 0.f;
 #pragma unroll
                 for (int x = 0; x < NE; ++x) {
-                    t1[x] = ok[x] ? fmaf(p2[x], exp2f(ex[x] - s), epss) : 0.f;
+                    t1[x] = ok[x] ? fmaf(p2[x], fast_exp2(ex[x] - s), epss) : 0.f;
                     rs += t1[x];
                 }
                 rs = group_sum<LPR>(rs);
@@ -224,7 +245,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
                 for (int x = 0; x < NE; ++x) {
                     p1n[x] = t1[x] * scale;
                     if (rv && ok[x]) {
-                        racc[x] += fmaf(p1n[x], exp2f(l2[x] * beta), eps);
+                        racc[x] += fmaf(p1n[x], fast_exp2(l2[x] * beta), eps);
                         objacc = fmaf(cin[x], p1n[x], objacc);
                     }
                 }
@@ -248,6 +269,11 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
                     }
                 }
             }
+            if (base + RPW < mk) {
+#pragma unroll
+                for (int x = 0; x < NE; ++x) { pin[x] = npin[x]; lin[x] = nlin[x]; cin[x] = ncin[x]; }
+                wkj = nwkj;
+            }
         }
 
         if (doA) {
@@ -256,11 +282,12 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
             for (int x = 0; x < NE; ++x)
 #pragma unroll
                 for (int o = LPR; o < 32; o <<= 1) racc[x] += __shfl_xor_sync(0xffffffffu, racc[x], o);
-            double tl = 0.0;
+            float tl = 0.f;
 #pragma unroll
             for (int x = 0; x < NE; ++x)
-                if (ok[x]) tl += (double)racc[x];
-            tl = group_sum_d<LPR>(tl);
+                if (ok[x]) tl += racc[x];
+            tl = group_sum<LPR>(tl);
+            const float inv_tl = 1.0f / tl;
             if (sub == 0) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v)
@@ -270,8 +297,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
                         const int x = v * VEC + e;
                         if (ok[x]) {
                             a.pos_r[p * m + col] = racc[x];
-                            double wtl = (double)racc[x] / tl;
-                            a.pos_part[p * m + col] = (fl & SW_R2) ? sqrt(wtl) : wtl;
+                            const float wtl = racc[x] * inv_tl;
+                            a.pos_part[p * m + col] = (fl & SW_R2) ? sqrtf(wtl) : wtl;
                         }
                     }
             }
@@ -518,7 +545,7 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
     if ((rc = d2_ws(ctx, WS_LAM, (size_t)n * m * 4, &vlam))) return rc;
     if ((rc = d2_ws(ctx, WS_COST, (size_t)n * m * 4, &vcost))) return rc;
     if ((rc = d2_ws(ctx, WS_POS_R, (size_t)P * m * 4, &vr))) return rc;
-    if ((rc = d2_ws(ctx, WS_POS_PART, (size_t)P * m * 8, &vpart))) return rc;
+    if ((rc = d2_ws(ctx, WS_POS_PART, (size_t)P * m * 4, &vpart))) return rc;
     if ((rc = d2_ws(ctx, WS_POS_OBJ, (size_t)P * 8, &vobj))) return rc;
     const int64_t maxch = d2_ceil_div(P, D2_CHUNK) + K + 1;
     const bool fix_x = opts.flags & D2_FIX_X, fix_w = opts.flags & D2_FIX_W;
@@ -566,7 +593,7 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
     sa.lam = lam;
     sa.cost = cost;
     sa.pos_r = static_cast<float*>(vr);
-    sa.pos_part = static_cast<double*>(vpart);
+    sa.pos_part = static_cast<float*>(vpart);
     sa.pos_obj = static_cast<double*>(vobj);
     sa.beta = cw.beta;
     sa.rho = cw.rho;

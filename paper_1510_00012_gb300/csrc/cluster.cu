@@ -1,0 +1,340 @@
+// Assignment step and D2-clustering outer loop (Algorithm 1 with the
+// Section 5 choices), plus the greedy merge initialisation of Eq. (merge).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "d2_internal.cuh"
+
+struct AssignArgs;
+size_t d2_assign_warp_bytes(int m, int nmax);
+int d2_argmin_rows(d2_ctx* ctx, const float* D, int64_t N, int K, int32_t* labels, float* dist,
+                   cudaStream_t st);
+int d2_assign_exact(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w,
+                    int32_t* labels, float* dist, int64_t* fail_count, cudaStream_t st);
+int d2_assign_pruned(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w,
+                     const d2_prune* prune, int32_t* labels, float* dist, int64_t* counters,
+                     cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Eq. (merge): one CTA per picked bag, FP64 like the definition
+// ---------------------------------------------------------------------------
+#define MG_MAX 256
+
+__global__ void k_merge(const int64_t* offsets, const float* supp, const int32_t* vidx, const float* vocab,
+                        const float* wt, int d, const int64_t* ids, int m, float* xout, float* wout) {
+    extern __shared__ double mg[];
+    const int c = blockIdx.x;
+    const int64_t k = ids[c];
+    const int64_t r0 = offsets[k];
+    const int mk = (int)min((int64_t)MG_MAX, offsets[k + 1] - r0);
+    double* X = mg;                        // mk x d
+    double* W = X + (size_t)mk * d;        // mk
+    int* alive = reinterpret_cast<int*>(W + mk);
+    __shared__ double s_best[256];
+    __shared__ int s_bi[256], s_bj[256];
+    for (int e = threadIdx.x; e < mk * d; e += blockDim.x) {
+        int j = e / d, t = e - j * d;
+        X[e] = (double)d2_row_ptr(supp, vidx, vocab, d, r0 + j)[t];
+    }
+    for (int j = threadIdx.x; j < mk; j += blockDim.x) {
+        W[j] = (double)wt[r0 + j];
+        alive[j] = 1;
+    }
+    __syncthreads();
+    int cnt = mk;
+    while (cnt > m) {
+        // lexicographic (i, j), i < j, first minimum of w_i w_j ||x_i - x_j||^2 / (w_i + w_j)
+        double best = 1e300;
+        int bi = 0x7fffffff, bj = 0x7fffffff;
+        for (int e = threadIdx.x; e < mk * mk; e += blockDim.x) {
+            int i = e / mk, j = e - i * mk;
+            if (i >= j || !alive[i] || !alive[j]) continue;
+            double den = W[i] + W[j], dd = 0.0;
+            for (int t = 0; t < d; ++t) {
+                double df = X[i * d + t] - X[j * d + t];
+                dd += df * df;
+            }
+            double crit = den > 0.0 ? W[i] * W[j] * dd / den : 0.0;
+            if (crit < best || (crit == best && (i < bi || (i == bi && j < bj)))) {
+                best = crit;
+                bi = i;
+                bj = j;
+            }
+        }
+        s_best[threadIdx.x] = best;
+        s_bi[threadIdx.x] = bi;
+        s_bj[threadIdx.x] = bj;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int t = 1; t < (int)blockDim.x; ++t) {
+                double v = s_best[t];
+                int ti = s_bi[t], tj = s_bj[t];
+                if (v < s_best[0] || (v == s_best[0] && (ti < s_bi[0] || (ti == s_bi[0] && tj < s_bj[0])))) {
+                    s_best[0] = v;
+                    s_bi[0] = ti;
+                    s_bj[0] = tj;
+                }
+            }
+        }
+        __syncthreads();
+        const int i = s_bi[0], j = s_bj[0];
+        const double wb = W[i] + W[j];
+        for (int t = threadIdx.x; t < d; t += blockDim.x) {
+            X[i * d + t] = wb > 0.0 ? (W[i] * X[i * d + t] + W[j] * X[j * d + t]) / wb
+                                    : 0.5 * (X[i * d + t] + X[j * d + t]);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            W[i] = wb;
+            alive[j] = 0;
+        }
+        __syncthreads();
+        --cnt;
+    }
+    // write the survivors in index order; pad short bags with zero-weight copies
+    if (threadIdx.x == 0) {
+        int o = 0, last = 0;
+        for (int j = 0; j < mk; ++j) {
+            if (!alive[j]) continue;
+            for (int t = 0; t < d; ++t) xout[((int64_t)c * m + o) * d + t] = (float)X[j * d + t];
+            wout[(int64_t)c * m + o] = (float)W[j];
+            last = j;
+            ++o;
+        }
+        for (; o < m; ++o) {
+            for (int t = 0; t < d; ++t) xout[((int64_t)c * m + o) * d + t] = (float)X[last * d + t];
+            wout[(int64_t)c * m + o] = 0.f;
+        }
+    }
+}
+
+extern "C" int d2_merge_init(d2_ctx* ctx, const d2_bags* bags, const int64_t* ids, int64_t cnt, int32_t m,
+                             float* x, float* w, void* stream) {
+    if (!ctx) return D2_EINVAL;
+    int rc = d2_check_bags_host(ctx, bags);
+    if (rc) return rc;
+    if (cnt < 0 || m < 1 || !ids || !x || !w) return d2_fail(ctx, D2_EINVAL, "d2_merge_init: bad arguments");
+    if (bags->max_mk > MG_MAX) return d2_fail(ctx, D2_ENOTSUP, "d2_merge_init: m_k > %d", MG_MAX);
+    if (cnt == 0) return D2_OK;
+    size_t smem = (size_t)bags->max_mk * (bags->d + 1) * 8 + (size_t)bags->max_mk * 4 + 16;
+    if (smem > 200 * 1024) return d2_fail(ctx, D2_ENOTSUP, "d2_merge_init: m_k x d too large");
+    cudaStream_t st = d2_stream(stream);
+    D2_CK(ctx, cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_merge<<<(unsigned)cnt, 256, smem, st>>>(bags->offsets, bags->supp, bags->vocab_idx, bags->vocab, bags->wt,
+                                              bags->d, ids, m, x, w);
+    D2_LAUNCH_CK(ctx, "k_merge");
+    return D2_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stable partition of bag ids by label: cluster_offsets (K+1), members (N)
+// ---------------------------------------------------------------------------
+
+__global__ void k_label_hist(const int32_t* labels, int64_t N, int K, int64_t* counts) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < N) {
+        int l = labels[k];
+        if (l >= 0 && l < K) atomicAdd(reinterpret_cast<unsigned long long*>(counts + l), 1ull);
+    }
+}
+
+__global__ void k_excl_scan(const int64_t* counts, int K, int64_t* offs) {
+    __shared__ int64_t s[1024];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < K; base += 1024) {
+        int c = base + threadIdx.x;
+        int64_t v = c < K ? counts[c] : 0;
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            int64_t t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+            __syncthreads();
+            s[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (c < K) offs[c] = carry + s[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += s[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) offs[K] = carry;
+}
+
+// one CTA walks the bags in tiles of 1024 in id order; inside a tile the warps
+// take turns, each lane finding its rank among equal labels with match_any
+__global__ void k_stable_scatter(const int32_t* labels, int64_t N, int K, const int64_t* offs, int64_t* cursor,
+                                 int64_t* members) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = threadIdx.x; c < K; c += blockDim.x) cursor[c] = offs[c];
+    __syncthreads();
+    for (int64_t base = 0; base < N; base += blockDim.x) {
+        const int64_t k = base + threadIdx.x;
+        const int l = k < N ? labels[k] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, l);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        const int leader = __ffs(peers) - 1;
+        const int cntw = __popc(peers);
+        for (int w = 0; w < nw; ++w) {
+            if (warp == w && l >= 0 && l < K) {
+                int64_t basepos = cursor[l];  // read before the leader advances it
+                __syncwarp(peers);
+                members[basepos + rank] = k;
+                __syncwarp(peers);
+                if (lane == leader) cursor[l] = basepos + cntw;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void k_warm_mask(const int32_t* labels, const int32_t* prev, int64_t N, uint8_t* mask) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < N) mask[k] = (prev[k] >= 0 && prev[k] == labels[k]) ? 1 : 0;
+}
+
+__global__ void k_mean_dist(const float* dist, int64_t N, double* out) {
+    __shared__ double s[1024];
+    double acc = 0.0;
+    for (int64_t k = threadIdx.x; k < N; k += blockDim.x) acc += (double)dist[k];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0] / (double)N;
+}
+
+// ---------------------------------------------------------------------------
+// d2_assign
+// ---------------------------------------------------------------------------
+
+extern "C" int d2_assign(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, const float* x, const float* w,
+                         const d2_prune* prune, int32_t* labels, float* dist, int64_t* stats, void* stream) {
+    if (!ctx) return D2_EINVAL;
+    int rc = d2_check_bags_host(ctx, bags);
+    if (rc) return rc;
+    if (K < 1 || m < 1 || !x || !w || !labels || !dist)
+        return d2_fail(ctx, D2_EINVAL, "d2_assign: need K >= 1, m >= 1 and non-NULL arrays");
+    if (m + bags->max_mk > 32000) return d2_fail(ctx, D2_ENOTSUP, "d2_assign: m + max_mk too large");
+    cudaStream_t st = d2_stream(stream);
+    void* sc = nullptr;
+    if ((rc = d2_ws(ctx, WS_SCAN, 64, &sc))) return rc;
+    int64_t* counters = static_cast<int64_t*>(sc);  // [0] exact solves, [1] fall-backs, [2] limit hits
+    D2_CK(ctx, cudaMemsetAsync(counters, 0, 3 * sizeof(int64_t), st));
+    if (prune) rc = d2_assign_pruned(ctx, bags, K, m, x, w, prune, labels, dist, counters, st);
+    else rc = d2_assign_exact(ctx, bags, K, m, x, w, labels, dist, counters, st);
+    if (rc) return rc;
+    if (stats) {
+        D2_CK(ctx, cudaMemcpyAsync(stats, counters, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        D2_CK(ctx, cudaStreamSynchronize(st));
+    }
+    return D2_OK;
+}
+
+// ---------------------------------------------------------------------------
+// d2_cluster
+// ---------------------------------------------------------------------------
+
+static uint64_t splitmix64_next(uint64_t& state) {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+extern "C" int d2_cluster(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, uint64_t seed, int32_t rounds,
+                          const d2_badmm_opts* opts, const d2_prune* prune, float* x_out, float* w_out,
+                          int32_t* labels_out, double* obj_per_round, void* stream) {
+    if (!ctx) return D2_EINVAL;
+    int rc = d2_check_bags_host(ctx, bags);
+    if (rc) return rc;
+    if (K < 1 || m < 1 || m > 256 || rounds < 1 || !x_out || !w_out || !labels_out)
+        return d2_fail(ctx, D2_EINVAL, "d2_cluster: need K >= 1, 1 <= m <= 256, rounds >= 1, non-NULL outputs");
+    cudaStream_t st = d2_stream(stream);
+    const int64_t N = bags->N, n = bags->n;
+
+    // seeded pick: partial Fisher-Yates over the ids with m_k >= m (ascending)
+    std::vector<int64_t> off(N + 1);
+    D2_CK(ctx, cudaMemcpyAsync(off.data(), bags->offsets, (N + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    D2_CK(ctx, cudaStreamSynchronize(st));
+    std::vector<int64_t> elig;
+    for (int64_t k = 0; k < N; ++k)
+        if (off[k + 1] - off[k] >= m) elig.push_back(k);
+    if ((int64_t)elig.size() < K)
+        return d2_fail(ctx, D2_EINVAL, "d2_cluster: only %zu distributions have m_k >= m = %d (K = %d)",
+                       elig.size(), m, K);
+    uint64_t state = seed;
+    const uint64_t E = elig.size();
+    for (int t = 0; t < K; ++t) {
+        uint64_t z = splitmix64_next(state);
+        uint64_t j = t + z % (E - t);
+        std::swap(elig[t], elig[j]);
+    }
+
+    // state lives in one workspace slot
+    const size_t o_lab = 0;
+    const size_t o_prev = o_lab + ((N * 4 + 255) & ~255ull);
+    const size_t o_dist = o_prev + ((N * 4 + 255) & ~255ull);
+    const size_t o_mask = o_dist + ((N * 4 + 255) & ~255ull);
+    const size_t o_mem = o_mask + ((N + 255) & ~255ull);
+    const size_t o_co = o_mem + ((N * 8 + 255) & ~255ull);
+    const size_t o_cnt = o_co + (((K + 1) * 8 + 255) & ~255ull);
+    const size_t o_cur = o_cnt + ((K * 8 + 255) & ~255ull);
+    const size_t o_ids = o_cur + ((K * 8 + 255) & ~255ull);
+    const size_t o_obj = o_ids + ((K * 8 + 255) & ~255ull);
+    const size_t o_bobj = o_obj + 256;
+    const size_t o_plan = o_bobj + ((K * 8 + 255) & ~255ull);
+    const size_t total = o_plan + (size_t)n * m * 4;
+    void* base = nullptr;
+    if ((rc = d2_ws(ctx, WS_CLUSTER_LOOP, total, &base))) return rc;
+    char* b = static_cast<char*>(base);
+    int32_t* lab = reinterpret_cast<int32_t*>(b + o_lab);
+    int32_t* prev = reinterpret_cast<int32_t*>(b + o_prev);
+    float* dist = reinterpret_cast<float*>(b + o_dist);
+    uint8_t* mask = reinterpret_cast<uint8_t*>(b + o_mask);
+    int64_t* members = reinterpret_cast<int64_t*>(b + o_mem);
+    int64_t* co = reinterpret_cast<int64_t*>(b + o_co);
+    int64_t* counts = reinterpret_cast<int64_t*>(b + o_cnt);
+    int64_t* cursor = reinterpret_cast<int64_t*>(b + o_cur);
+    int64_t* ids = reinterpret_cast<int64_t*>(b + o_ids);
+    double* dobj = reinterpret_cast<double*>(b + o_obj);
+    double* bobj = reinterpret_cast<double*>(b + o_bobj);
+    float* plan = reinterpret_cast<float*>(b + o_plan);
+
+    D2_CK(ctx, cudaMemcpyAsync(ids, elig.data(), K * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if ((rc = d2_merge_init(ctx, bags, ids, K, m, x_out, w_out, stream))) return rc;
+    D2_CK(ctx, cudaMemsetAsync(prev, 0xff, N * 4, st));
+
+    d2_badmm_opts o;
+    if (opts) o = *opts; else d2_badmm_opts_default(&o);
+    o.flags &= ~D2_VALIDATE;
+    const unsigned gN = (unsigned)d2_ceil_div(N, 256);
+    for (int r = 0; r < rounds; ++r) {
+        if ((rc = d2_assign(ctx, bags, K, m, x_out, w_out, prune, lab, dist, nullptr, stream))) return rc;
+        k_mean_dist<<<1, 1024, 0, st>>>(dist, N, dobj);
+        D2_LAUNCH_CK(ctx, "k_mean_dist");
+        if (obj_per_round) {
+            D2_CK(ctx, cudaMemcpyAsync(&obj_per_round[r], dobj, sizeof(double), cudaMemcpyDeviceToHost, st));
+        }
+        k_warm_mask<<<gN, 256, 0, st>>>(lab, prev, N, mask);
+        D2_LAUNCH_CK(ctx, "k_warm_mask");
+        D2_CK(ctx, cudaMemsetAsync(counts, 0, K * 8, st));
+        k_label_hist<<<gN, 256, 0, st>>>(lab, N, K, counts);
+        D2_LAUNCH_CK(ctx, "k_label_hist");
+        k_excl_scan<<<1, 1024, 0, st>>>(counts, K, co);
+        D2_LAUNCH_CK(ctx, "k_excl_scan");
+        k_stable_scatter<<<1, 1024, 0, st>>>(lab, N, K, co, cursor, members);
+        D2_LAUNCH_CK(ctx, "k_stable_scatter");
+        if ((rc = badmm_barycenter(ctx, bags, co, members, N, K, m, x_out, w_out, plan, mask, &o, bobj, stream)))
+            return rc;
+        D2_CK(ctx, cudaMemcpyAsync(prev, lab, N * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    D2_CK(ctx, cudaMemcpyAsync(labels_out, lab, N * 4, cudaMemcpyDeviceToDevice, st));
+    D2_CK(ctx, cudaStreamSynchronize(st));
+    return D2_OK;
+}

@@ -1,0 +1,128 @@
+"""GPU parity of the exact assignment (Eq. primal + argmin of Algorithm 1),
+the merge initialisation (Eq. merge) and the D2-clustering loop against the
+FP64 oracle.  W^2 values within 1e-4 relative; labels bit-exact wherever the
+gap between the two smallest W^2 exceeds 1e-4 of the smallest."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import w2_exact, merge_reduce, d2_cluster as oracle_cluster, init_pick
+from tests.test_oracle_cluster_mlp import lloyd_on_means
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def d2():
+    import paper_1510_00012_gb300 as d2mod
+    from paper_1510_00012_gb300 import build
+    build.build()
+    return d2mod
+
+
+@pytest.fixture(scope="module")
+def ctx(d2):
+    return d2.Context(0)
+
+
+def centroids(seed, K, m, d, scale=2.0):
+    g = torch.Generator().manual_seed(seed)
+    x = torch.randn(K, m, d, generator=g) * scale
+    w = torch.rand(K, m, generator=g) + 0.05
+    w = (w / w.sum(1, keepdim=True)).float()
+    return x.float(), w
+
+
+def gpu_w2_matrix(d2, ctx, db, x, w):
+    cols = []
+    for c in range(x.shape[0]):
+        _, dist = d2.d2_assign(ctx, db, x[c:c + 1].cuda().contiguous(), w[c:c + 1].cuda().contiguous())
+        cols.append(dist.cpu().double())
+    return torch.stack(cols, 1).numpy()
+
+
+@pytest.mark.parametrize("case", ["d5_m6", "d2_m1", "d16_m16", "d1_m4", "d32_m32"])
+def test_w2_values_match_exact_lp(d2, ctx, case):
+    d, m = {"d5_m6": (5, 6), "d2_m1": (2, 1), "d16_m16": (16, 16), "d1_m4": (1, 4), "d32_m32": (32, 32)}[case]
+    bags = synth.gaussian_class_bags(40 + m, 24, d, 3, mk=(1, 40), mu_sigma=2.0)
+    db = d2.DeviceBags.from_synth(bags)
+    x, w = centroids(m + d, 3, m, d)
+    G = gpu_w2_matrix(d2, ctx, db, x, w)
+    for k in range(bags.N):
+        y, wy = bags.bag(k)
+        for c in range(3):
+            ref = w2_exact(x[c].double().numpy(), w[c].double().numpy(), y, wy)
+            assert abs(G[k, c] - ref) <= 1e-4 * ref + 1e-6, (k, c, G[k, c], ref)
+
+
+def test_w2_zero_for_identical_distribution(d2, ctx):
+    bags = synth.gaussian_class_bags(3, 5, 3, 1, mk=(4, 4))
+    db = d2.DeviceBags.from_synth(bags)
+    y, wy = bags.bag(2)
+    x = torch.tensor(y, dtype=torch.float32)[None]
+    w = torch.tensor(wy, dtype=torch.float32)[None]
+    _, dist = d2.d2_assign(ctx, db, x.cuda(), w.cuda())
+    assert abs(float(dist[2])) < 1e-6
+
+
+def test_labels_match_oracle_where_margin_is_clear(d2, ctx):
+    bags = synth.gaussian_class_bags(9, 60, 4, 4, mk=(2, 12), mu_sigma=2.5)
+    db = d2.DeviceBags.from_synth(bags)
+    x, w = centroids(10, 4, 5, 4, scale=2.5)
+    labels, dist, st = d2.d2_assign(ctx, db, x.cuda(), w.cuda(), want_stats=True)
+    labels, dist = labels.cpu().numpy(), dist.cpu().double().numpy()
+    assert st["exact_solves"] == 60 * 4 and st["limit_hits"] == 0
+    for k in range(bags.N):
+        y, wy = bags.bag(k)
+        D = np.array([w2_exact(x[c].double().numpy(), w[c].double().numpy(), y, wy) for c in range(4)])
+        order = np.argsort(D, kind="stable")
+        best = D[order[0]]
+        assert abs(dist[k] - best) <= 1e-4 * best + 1e-6
+        if D[order[1]] - best > 1e-4 * best:
+            assert labels[k] == order[0]
+
+
+def test_merge_init_matches_oracle(d2, ctx):
+    bags = synth.gaussian_class_bags(12, 30, 3, 2, mk=(1, 20))
+    db = d2.DeviceBags.from_synth(bags)
+    ids = torch.arange(0, 30, 3, dtype=torch.int64)
+    for m in (1, 4, 9):
+        x, w = d2.d2_merge_init(ctx, db, ids.cuda(), m)
+        x, w = x.cpu().double().numpy(), w.cpu().double().numpy()
+        for t, k in enumerate(ids.tolist()):
+            y, wy = bags.bag(k)
+            rx, rw = merge_reduce(y, wy, m)
+            q = rx.shape[0]
+            np.testing.assert_allclose(x[t, :q], rx, atol=1e-5, rtol=0)
+            np.testing.assert_allclose(w[t, :q], rw, atol=1e-6, rtol=0)
+            if q < m:  # padding: zero-weight copies of the last point
+                assert np.all(w[t, q:] == 0)
+
+
+def test_d2_cluster_matches_oracle(d2, ctx):
+    bags = synth.gaussian_class_bags(31, 90, 4, 3, mk=(4, 10), mu_sigma=4.0, alpha=1.0)
+    db = d2.DeviceBags.from_synth(bags)
+    K, m, rounds, T = 3, 4, 3, 20
+    x, w, labels, objs = d2.d2_cluster(ctx, db, K, m, seed=77, rounds=rounds,
+                                       opts=d2.badmm_opts(iters=T, tau=10))
+    members = [bags.bag(k) for k in range(bags.N)]
+    ref = oracle_cluster(members, K, m, seed=77, rounds=rounds, T=T, tau=10)
+    np.testing.assert_array_equal(labels.cpu().numpy(), ref["labels"])
+    for r in range(rounds):
+        assert abs(objs[r] - ref["obj_per_round"][r]) <= 1e-4 * ref["obj_per_round"][r]
+    np.testing.assert_allclose(w.cpu().double().numpy(), ref["w"], atol=1e-5, rtol=0)
+    np.testing.assert_allclose(x.cpu().double().numpy(), ref["x"], atol=2e-4 * (1 + np.abs(ref["x"]).max()))
+
+
+def test_d2_cluster_m1_is_kmeans_on_means(d2, ctx):
+    bags = synth.gaussian_class_bags(32, 120, 3, 4, mk=(1, 8), mu_sigma=3.0)
+    db = d2.DeviceBags.from_synth(bags)
+    K, rounds = 4, 4
+    x, w, labels, objs = d2.d2_cluster(ctx, db, K, 1, seed=5, rounds=rounds, opts=d2.badmm_opts(iters=12, tau=10))
+    means = np.array([wy @ y for y, wy in (bags.bag(k) for k in range(bags.N))])
+    picks = init_pick(bags.sizes().tolist(), K, 1, 5)
+    labels_ref, cent = lloyd_on_means(means, means[picks], rounds)
+    np.testing.assert_array_equal(labels.cpu().numpy(), labels_ref[-1])
+    np.testing.assert_allclose(x.cpu().double().numpy()[:, 0, :], cent, atol=1e-4)
+    assert np.allclose(w.cpu().numpy(), 1.0)
