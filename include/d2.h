@@ -53,6 +53,8 @@ extern "C" {
 #define D2_FIX_W     0x2  /* keep w fixed: each member then solves OT(w, w^(k)) by B-ADMM  */
 #define D2_VALIDATE  0x4  /* validate the bags on the device first (synchronises)          */
 #define D2_NO_GRAPH  0x8  /* launch kernels directly instead of replaying a CUDA graph    */
+#define D2_NO_PIPE   0x10 /* use the register-prefetch plan sweep instead of the
+                             shared-memory pipelined one (both compute the same)  */
 
 typedef struct d2_ctx d2_ctx;
 
@@ -80,7 +82,7 @@ typedef struct {
     int32_t iters;     /* T, B-ADMM iterations per call, default 100 (Section 3.3)      */
     int32_t tau;       /* support update every tau iterations, default 10               */
     int32_t rule;      /* D2_RULE_R1 (default) or D2_RULE_R2                            */
-    int32_t flags;     /* D2_FIX_X | D2_FIX_W | D2_VALIDATE | D2_NO_GRAPH               */
+    int32_t flags;     /* D2_FIX_X | D2_FIX_W | D2_VALIDATE | D2_NO_GRAPH | D2_NO_PIPE  */
 } d2_badmm_opts;
 
 /* Fill `o` with the defaults above. */
@@ -188,8 +190,11 @@ int64_t d2_prune_param_count(const d2_prune* p);
 /* Copy the packed parameters to / from host memory (synchronous). */
 int d2_prune_get_params(d2_ctx* ctx, const d2_prune* p, float* host_out);
 int d2_prune_set_params(d2_ctx* ctx, d2_prune* p, const float* host_in);
-/* Candidate count r (>= 1) and margin delta (>= 0) of the margin test. */
+/* Candidate count r (1..16) and margin delta (>= 0) of the margin test;
+ * d2_prune_train sets delta to the 99.9% quantile of |What^2 - W^2| on its
+ * held-out pairs. */
 int d2_prune_set_margin(d2_prune* p, int32_t r, float delta);
+int d2_prune_get_margin(const d2_prune* p, int32_t* r, float* delta);
 
 /* Embeddings f(P) of the bags listed in `ids` (device, cnt) -> emb (device,
  * cnt x E) and their means mu (device, cnt x d). */
@@ -230,6 +235,13 @@ int d2_prune_train(d2_ctx* ctx, d2_prune* p, const d2_bags* bags,
 int d2_assign(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,
               const float* x, const float* w, const d2_prune* prune,
               int32_t* labels, float* dist, int64_t* stats, void* stream);
+
+/* Exact W^2 (Eq. primal, the same solver as d2_assign) for an explicit list
+ * of npairs (bag pair_bag[p], centroid pair_cent[p]) -> out[p] (device
+ * floats).  Used to produce training targets for the pruner. */
+int d2_w2_pairs(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,
+                const float* x, const float* w, const int64_t* pair_bag,
+                const int32_t* pair_cent, int64_t npairs, float* out, void* stream);
 
 /* Greedy merge of Eq. (merge) (Section 5): reduce bag ids[c] to m support
  * points for c = 0..cnt-1 -> x (device cnt x m x d), w (device cnt x m).

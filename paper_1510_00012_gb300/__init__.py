@@ -58,6 +58,8 @@ _SIGS = {
                                  c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "d2_assign": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
                           c_void_p, c_void_p, c_void_p, c_void_p]),
+    "d2_w2_pairs": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                            c_int64, c_void_p, c_void_p]),
     "d2_merge_init": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p,
                               c_void_p]),
     "d2_cluster": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_uint64, c_int32, c_void_p,
@@ -68,6 +70,7 @@ _SIGS = {
     "d2_prune_get_params": (c_int, [c_void_p, c_void_p, c_void_p]),
     "d2_prune_set_params": (c_int, [c_void_p, c_void_p, c_void_p]),
     "d2_prune_set_margin": (c_int, [c_void_p, c_int32, c_float]),
+    "d2_prune_get_margin": (c_int, [c_void_p, c_void_p, c_void_p]),
     "d2_prune_embed": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p,
                                c_void_p]),
     "d2_prune_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
@@ -266,7 +269,7 @@ def d2_assign(ctx, bags, x, w, prune=None, want_stats=False):
     dist = torch.empty(bags.N, dtype=torch.float32, device=x.device)
     st = (c_int64 * 3)() if want_stats else None
     ctx.check(lib().d2_assign(ctx.h, bags.ref(), K, m, _ptr(x), _ptr(w),
-                              None if prune is None else prune.h, _ptr(labels), _ptr(dist),
+                              None if prune is None else c_void_p(prune.h), _ptr(labels), _ptr(dist),
                               st, _stream()))
     if want_stats:
         return labels, dist, dict(exact_solves=st[0], fallbacks=st[1], limit_hits=st[2])
@@ -283,6 +286,108 @@ def d2_cluster(ctx, bags, K, m, seed, rounds, opts=None, prune=None):
     if opts is None:
         opts = badmm_opts()
     ctx.check(lib().d2_cluster(ctx.h, bags.ref(), K, m, c_uint64(seed), rounds, ctypes.byref(opts),
-                               None if prune is None else prune.h, _ptr(x), _ptr(w), _ptr(labels),
+                               None if prune is None else c_void_p(prune.h), _ptr(x), _ptr(w), _ptr(labels),
                                objs, _stream()))
     return x, w, labels, list(objs)
+
+
+def d2_w2_pairs(ctx, bags, x, w, pair_bag, pair_cent):
+    """Exact W^2 for explicit (bag, centroid) pairs -> (npairs,) float32."""
+    _need(x, torch.float32, "x")
+    _need(w, torch.float32, "w")
+    _need(pair_bag, torch.int64, "pair_bag")
+    _need(pair_cent, torch.int32, "pair_cent")
+    out = torch.empty(pair_bag.numel(), dtype=torch.float32, device=x.device)
+    ctx.check(lib().d2_w2_pairs(ctx.h, bags.ref(), x.shape[0], x.shape[1], _ptr(x), _ptr(w), _ptr(pair_bag),
+                                _ptr(pair_cent), pair_bag.numel(), _ptr(out), _stream()))
+    return out
+
+
+class Pruner:
+    """Learned candidate pruner (d2_prune): MLP embedding trained on exact W^2."""
+
+    def __init__(self, ctx, d, hidden=128, embed=64, init=None, seed=0):
+        self.ctx = ctx
+        buf = None
+        if init is not None:
+            buf = torch.as_tensor(init, dtype=torch.float32).contiguous()
+        self.h = lib().d2_prune_create(ctx.h, d, hidden, embed, None if buf is None else ctypes.c_void_p(buf.data_ptr()),
+                                       c_uint64(seed))
+        if not self.h:
+            raise D2Error(D2_EINVAL, lib().d2_last_error(ctx.h).decode())
+        self.d, self.H, self.E = d, hidden, embed
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().d2_prune_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def nparam(self):
+        return int(lib().d2_prune_param_count(self.h))
+
+    def params(self):
+        out = torch.empty(self.nparam(), dtype=torch.float32)
+        self.ctx.check(lib().d2_prune_get_params(self.ctx.h, self.h, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def unpack(self, flat):
+        d, H, E = self.d, self.H, self.E
+        o = 0
+        out = {}
+        for name, shape in (("W1", (H, d)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (E, H))):
+            n = 1
+            for s_ in shape:
+                n *= s_
+            out[name] = flat[o:o + n].reshape(shape)
+            o += n
+        return out
+
+    def set_params(self, flat):
+        flat = torch.as_tensor(flat, dtype=torch.float32).contiguous()
+        self.ctx.check(lib().d2_prune_set_params(self.ctx.h, self.h, ctypes.c_void_p(flat.data_ptr())))
+
+    def set_margin(self, r, delta):
+        rc = lib().d2_prune_set_margin(self.h, int(r), float(delta))
+        if rc != D2_OK:
+            raise D2Error(rc, "d2_prune_set_margin: need 1 <= r <= 16 and delta >= 0")
+
+    def margin(self):
+        r, dl = c_int32(), c_float()
+        lib().d2_prune_get_margin(self.h, ctypes.byref(r), ctypes.byref(dl))
+        return int(r.value), float(dl.value)
+
+    def embed(self, bags, ids):
+        _need(ids, torch.int64, "ids")
+        emb = torch.empty(ids.numel(), self.E, dtype=torch.float32, device=ids.device)
+        mu = torch.empty(ids.numel(), bags.d, dtype=torch.float32, device=ids.device)
+        self.ctx.check(lib().d2_prune_embed(self.ctx.h, self.h, bags.ref(), _ptr(ids), ids.numel(), _ptr(emb),
+                                            _ptr(mu), _stream()))
+        return emb, mu
+
+    def loss_grad(self, bags, x, w, pair_bag, pair_cent, target):
+        _need(pair_bag, torch.int64, "pair_bag")
+        _need(pair_cent, torch.int32, "pair_cent")
+        _need(target, torch.float32, "target")
+        loss = torch.empty(1, dtype=torch.float64, device=x.device)
+        grad = torch.empty(self.nparam(), dtype=torch.float32, device=x.device)
+        self.ctx.check(lib().d2_prune_loss_grad(self.ctx.h, self.h, bags.ref(), x.shape[0], x.shape[1], _ptr(x),
+                                                _ptr(w), _ptr(pair_bag), _ptr(pair_cent), _ptr(target),
+                                                pair_bag.numel(), _ptr(loss), _ptr(grad), _stream()))
+        return loss, grad
+
+    def train(self, bags, x, w, pair_bag, pair_cent, target, steps, batch=1024, lr=1e-3, seed=0):
+        _need(pair_bag, torch.int64, "pair_bag")
+        _need(pair_cent, torch.int32, "pair_cent")
+        _need(target, torch.float32, "target")
+        losses = (c_float * steps)()
+        torch.cuda.synchronize()
+        self.ctx.check(lib().d2_prune_train(self.ctx.h, self.h, bags.ref(), x.shape[0], x.shape[1], _ptr(x), _ptr(w),
+                                            _ptr(pair_bag), _ptr(pair_cent), _ptr(target), pair_bag.numel(),
+                                            steps, batch, c_float(lr), c_uint64(seed), losses))
+        return list(losses)

@@ -32,12 +32,15 @@ struct AssignArgs {
     const float* w;    // K x m
     int m, K, nmax;
     // pair enumeration
-    int mode;                  // 0: all N*K pairs; 1: explicit list; 2: all K for listed bags
+    int mode;                  // 0: all N*K pairs; 1: explicit list; 2: all K for listed bags;
+                               // 3: r candidates per bag (bag p / r, centroid cand[p])
     int64_t npairs;            // mode 0/1 host count (mode 1: upper bound if npairs_dev)
     const int64_t* npairs_dev; // mode 1/2: device count (pairs, or bags for mode 2)
     const int64_t* pair_bag;   // mode 1
     const int32_t* pair_cent;  // mode 1
     const int64_t* bag_list;   // mode 2
+    const int32_t* cand;       // mode 3
+    int r;                     // mode 3
     float* out;                // mode 0/2: out[bag*K + cent]; mode 1: out[pair]
     int* flags;
     int64_t* pivot_fail;       // count of pairs that hit the phase limit
@@ -282,7 +285,8 @@ __global__ void k_w2_pairs(AssignArgs a) {
     int64_t total;
     if (a.mode == 0) total = a.npairs;
     else if (a.mode == 1) total = a.npairs_dev ? min(*a.npairs_dev, a.npairs) : a.npairs;
-    else total = (*a.npairs_dev) * a.K;
+    else if (a.mode == 2) total = (*a.npairs_dev) * a.K;
+    else total = a.npairs;
     const int64_t nwarps = (int64_t)gridDim.x * wpb;
     for (int64_t p = (int64_t)blockIdx.x * wpb + wib; p < total; p += nwarps) {
         int64_t bag;
@@ -296,11 +300,15 @@ __global__ void k_w2_pairs(AssignArgs a) {
             bag = a.pair_bag[p];
             cent = a.pair_cent[p];
             slot = p;
-        } else {
+        } else if (a.mode == 2) {
             int64_t b = p / a.K;
             cent = (int)(p - b * a.K);
             bag = a.bag_list[b];
             slot = bag * a.K + cent;
+        } else {
+            bag = p / a.r;
+            cent = a.cand[p];
+            slot = p;
         }
         bool lim = false;
         double v = solve_pair(a, s, bag, cent, lim);
@@ -409,4 +417,43 @@ int d2_assign_exact(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x,
     k_add_i64<<<1, 1, 0, st>>>(counters, N * K);
     D2_LAUNCH_CK(ctx, "k_add_i64");
     return d2_argmin_rows(ctx, D, N, K, labels, dist, st);
+}
+
+// pair lists for the pruned assignment (mode 2: all K for a device-counted
+// bag list; mode 3: r candidates per bag)
+int d2_prune_solve_pairs(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w, int mode,
+                         int64_t npairs, const int64_t* npairs_dev, const int32_t* cand, int r,
+                         const int64_t* bag_list, float* out, int64_t* fail_count, cudaStream_t st) {
+    AssignArgs a = d2_assign_args(b, K, m, x, w, ctx->dev_flags, fail_count);
+    a.mode = mode;
+    a.npairs = npairs;
+    a.npairs_dev = npairs_dev;
+    a.cand = cand;
+    a.r = r;
+    a.bag_list = bag_list;
+    a.out = out;
+    return d2_launch_pairs(ctx, a, npairs, st);
+}
+
+extern "C" int d2_w2_pairs(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, const float* x, const float* w,
+                           const int64_t* pair_bag, const int32_t* pair_cent, int64_t npairs, float* out,
+                           void* stream) {
+    if (!ctx) return D2_EINVAL;
+    int rc = d2_check_bags_host(ctx, bags);
+    if (rc) return rc;
+    if (K < 1 || m < 1 || npairs < 0 || !x || !w || (npairs > 0 && (!pair_bag || !pair_cent || !out)))
+        return d2_fail(ctx, D2_EINVAL, "d2_w2_pairs: bad arguments");
+    if (npairs == 0) return D2_OK;
+    cudaStream_t st = d2_stream(stream);
+    void* sc = nullptr;
+    if ((rc = d2_ws(ctx, WS_SCAN, 64, &sc))) return rc;
+    int64_t* counters = static_cast<int64_t*>(sc);
+    D2_CK(ctx, cudaMemsetAsync(counters, 0, 3 * sizeof(int64_t), st));
+    AssignArgs a = d2_assign_args(bags, K, m, x, w, ctx->dev_flags, counters + 2);
+    a.mode = 1;
+    a.npairs = npairs;
+    a.pair_bag = pair_bag;
+    a.pair_cent = pair_cent;
+    a.out = out;
+    return d2_launch_pairs(ctx, a, npairs, st);
 }

@@ -25,14 +25,22 @@
 // arithmetic and keeps FP32 from underflowing on far-away points.
 //
 // Weight consensus (Eq. badmmw / badmmw2).  Each warp writes its member's
-// wtilde^(k) (FP32, normalised by one reciprocal); the last CTA to finish a cluster (arrival counter per
-// cluster, no waiting) sums the cluster's members in a fixed order in FP64,
-// normalises, and publishes w^{n+1} for the next launch.  The result does not
-// depend on CTA scheduling.
+// wtilde^(k) (FP32, normalised by one reciprocal) and counts its arrival on
+// the cluster; the warp that brings the count to N_c (no waiting anywhere)
+// sums the cluster's members in a fixed order in FP64, normalises, and
+// publishes w^{n+1} for the next launch.  The result does not depend on the
+// order in which warps finish.  Warps are persistent and take member
+// positions round-robin, so no warp idles at a CTA barrier while a sibling
+// finishes a longer member.
+#include <algorithm>
+
 #include "d2_internal.cuh"
 
 #define SWEEP_WARPS 8
 #define SWEEP_THREADS (SWEEP_WARPS * 32)
+#ifndef D2_SWEEP_MINB
+#define D2_SWEEP_MINB 3   // resident CTAs per SM the register budget must allow
+#endif
 
 enum SweepFlags {
     SW_B = 1,            // input plan buffer holds Pi1^n: do the B step
@@ -98,56 +106,73 @@ __device__ __forceinline__ float fast_exp2(float x) {
     return y;
 }
 
-// fixed-order FP64 consensus of cluster c by the whole CTA
-__device__ void consensus_cluster(const SweepArgs& a, int c, double* s_acc) {
+// Fixed-order FP64 consensus of cluster c by one warp (the last to finish a
+// member of c).  Lane (g, i) sums the members p = p0 + g, p0 + g + G, ... of
+// column i; the G groups and then the m columns are combined in a fixed order,
+// so the result does not depend on which warp runs it.
+__device__ __noinline__ void warp_consensus(const SweepArgs& a, int c) {
+    const int lane = threadIdx.x & 31;
     const int m = a.m;
-    const int G = SWEEP_THREADS / m;  // position groups (m <= 256)
-    const int t = threadIdx.x;
-    const int i = t % m, g = t / m;
     const int64_t p0 = a.cofs[c], p1 = a.cofs[c + 1];
-    double acc = 0.0;
-    if (g < G) {
-        for (int64_t p = p0 + g; p < p1; p += G) acc += (double)__ldcg(a.pos_part + p * m + i);
-        s_acc[g * m + i] = acc;
+    const bool r2 = a.flags & SW_R2;
+    if (m <= 32) {
+        const int G = 32 / m;
+        const int g = lane / m, i = lane - g * m;
+        double acc = 0.0;
+        if (g < G)
+            for (int64_t p = p0 + g; p < p1; p += G) acc += (double)__ldcg(a.pos_part + p * m + i);
+        double s_i = acc;  // lanes of group 0 gather the other groups in order
+        for (int h = 1; h < G; ++h) {
+            double o = __shfl_sync(0xffffffffu, acc, (h * m + i) & 31);
+            if (g == 0) s_i += o;
+        }
+        double v = (g == 0) ? (r2 ? s_i * s_i : s_i) : 0.0;
+        double tot = group_sum_d<32>(v);
+        if (g == 0) {
+            const double wv = v / tot;
+            a.w_next64[(int64_t)c * m + i] = wv;
+            a.w_next[(int64_t)c * m + i] = (float)wv;
+        }
+    } else {
+        double vals[8];
+        double part = 0.0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int i = lane + 32 * t;
+            double acc = 0.0;
+            if (i < m)
+                for (int64_t p = p0; p < p1; ++p) acc += (double)__ldcg(a.pos_part + p * m + i);
+            vals[t] = r2 ? acc * acc : acc;
+            if (i < m) part += vals[t];
+        }
+        const double tot = group_sum_d<32>(part);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int i = lane + 32 * t;
+            if (i < m) {
+                const double wv = vals[t] / tot;
+                a.w_next64[(int64_t)c * m + i] = wv;
+                a.w_next[(int64_t)c * m + i] = (float)wv;
+            }
+        }
     }
-    __syncthreads();
-    if (t < m) {
-        double s = 0.0;
-        for (int h = 0; h < G; ++h) s += s_acc[h * m + t];
-        s_acc[SWEEP_THREADS + t] = (a.flags & SW_R2) ? s * s : s;
-    }
-    __syncthreads();
-    if (t == 0) {
-        double tot = 0.0;
-        for (int h = 0; h < m; ++h) tot += s_acc[SWEEP_THREADS + h];
-        s_acc[SWEEP_THREADS + 256] = tot;
-    }
-    __syncthreads();
-    if (t < m) {
-        double wv = s_acc[SWEEP_THREADS + t] / s_acc[SWEEP_THREADS + 256];
-        a.w_next64[(int64_t)c * m + t] = wv;
-        a.w_next[(int64_t)c * m + t] = (float)wv;
-    }
-    if (t == 0) a.counters[c] = 0;
-    __syncthreads();
+    if (lane == 0) a.counters[c] = 0;
 }
 
 template <int VEC, int LPR, int NV>
-__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
+__global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep(SweepArgs a) {
     constexpr int RPW = 32 / LPR;   // rows per warp step
     constexpr int NE = VEC * NV;    // floats per lane per row
-    __shared__ int s_list[SWEEP_WARPS];
-    __shared__ int s_nlist;
-    __shared__ double s_acc[SWEEP_THREADS + 257];
 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int sub = lane / LPR, cl = lane % LPR;
-    const int64_t p = (int64_t)blockIdx.x * SWEEP_WARPS + wib;
     const int m = a.m;
     const int fl = a.flags;
     const bool doA = fl & SW_A, doB = fl & SW_B;
+    const int64_t nwarps = (int64_t)gridDim.x * SWEEP_WARPS;
 
-    if (p < a.P) {
+    // persistent warps: member positions round-robin, no CTA-level barrier
+    for (int64_t p = (int64_t)blockIdx.x * SWEEP_WARPS + wib; p < a.P; p += nwarps) {
         const int64_t k = a.members[p];
         const int c = a.pos_cluster[p];
         const int64_t row0 = a.offsets[k];
@@ -306,40 +331,300 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
                 double ov = group_sum_d<32>((double)objacc);
                 if (lane == 0) a.pos_obj[p] = ov;
             }
-        }
-    }
-
-    // ---- weight consensus by the last CTA to finish each cluster
-    if (doA && a.w_next) {
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int nl = 0;
-            const int64_t p0 = (int64_t)blockIdx.x * SWEEP_WARPS;
-            const int64_t p1 = min(p0 + SWEEP_WARPS, a.P);
-            int64_t q = p0;
-            while (q < p1) {
-                const int c = a.pos_cluster[q];
-                int64_t e = q;
-                while (e < p1 && a.pos_cluster[e] == c) ++e;
-                const int cnt = (int)(e - q);
-                const int total = (int)(a.cofs[c + 1] - a.cofs[c]);
-                const int old = atomicAdd(&a.counters[c], cnt);
-                if (old + cnt == total) s_list[nl++] = c;
-                q = e;
+            // arrival of this member; the last member of the cluster to
+            // arrive makes its warp run the consensus
+            if (a.w_next) {
+                __threadfence();
+                __syncwarp();
+                int last = 0;
+                if (lane == 0) {
+                    const int total = (int)(a.cofs[c + 1] - a.cofs[c]);
+                    last = (atomicAdd(&a.counters[c], 1) + 1 == total);
+                }
+                last = __shfl_sync(0xffffffffu, last, 0);
+                if (last) {
+                    __threadfence();
+                    warp_consensus(a, c);
+                }
             }
-            s_nlist = nl;
-        }
-        __syncthreads();
-        const int nl = s_nlist;
-        for (int r = 0; r < nl; ++r) {
-            __threadfence();
-            consensus_cluster(a, s_list[r], s_acc);
         }
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Pipelined variant for m % 4 == 0, m <= 128 (one float4 per lane per row).
+// Each warp runs a PIPE_S-stage ring in shared memory: stage s holds one row
+// group (RPW rows) of the plan buffer, Lambda and C, the rows' weights and,
+// on the first row group of a member, that member's r_k and w slice.  Lanes
+// copy exactly the bytes they will consume (cp.async, 16 B), so a stage is
+// ready for a lane once its own copies have landed; PIPE_S - 1 row groups
+// are in flight per warp while one is computed, without holding them in
+// registers.  The issue side walks the same member sequence as the compute
+// side and leaves each stage's member metadata next to its data.
+// ---------------------------------------------------------------------------
+#define PIPE_S 4
+
+struct PipeMeta {
+    int64_t p;      // member position (-1: no more work)
+    int64_t row0;   // first support row of the member
+    int mk, base, c, flags;  // flags: 1 = first row group, 2 = plan was copied
+};
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
+
+template <int LPR>
+struct PipeWarp {
+    float4 data[PIPE_S][3][32];   // plan, lambda, cost
+    float4 hdr[PIPE_S][2][LPR];   // r_k and w columns of the member (first group)
+    float wk[PIPE_S][32 / LPR];   // row weights
+    PipeMeta meta[PIPE_S];
+    PipeMeta cur;                 // issue cursor: member being issued, next row group
+};
+
+template <int LPR>
+__global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep_pipe(SweepArgs a) {
+    constexpr int RPW = 32 / LPR;
+    extern __shared__ float4 pipe_dyn[];
+    PipeWarp<LPR>* pw = reinterpret_cast<PipeWarp<LPR>*>(pipe_dyn) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / LPR, cl = lane % LPR;
+    const int m = a.m;
+    const int fl = a.flags;
+    const bool doA = fl & SW_A, doB = fl & SW_B;
+    const bool ldL = !(fl & SW_LAM_ZERO);
+    const int col0 = cl * 4;
+    const bool okc = col0 < m;
+    const int64_t nw = (int64_t)gridDim.x * SWEEP_WARPS;
+
+    // ---- issue cursor (lives in shared memory; lane 0 advances it)
+    auto load_cursor = [&](int64_t ip) {
+        __syncwarp();
+        if (lane == 0) {
+            PipeMeta cu;
+            cu.p = ip < a.P ? ip : -1;
+            cu.row0 = 0;
+            cu.mk = 0;
+            cu.base = 0;
+            cu.c = 0;
+            cu.flags = 0;
+            if (ip < a.P) {
+                const int64_t k = a.members[ip];
+                cu.row0 = a.offsets[k];
+                cu.mk = (int)(a.offsets[k + 1] - cu.row0);
+                cu.c = a.pos_cluster[ip];
+                const bool cold = (fl & SW_COLD) && !(a.warm_mask && a.warm_mask[k]);
+                cu.flags = (doB || !cold) ? 2 : 0;
+            }
+            pw->cur = cu;
+        }
+        __syncwarp();
+    };
+    load_cursor((int64_t)blockIdx.x * SWEEP_WARPS + (threadIdx.x >> 5));
+    auto issue = [&](int slot) {
+        const PipeMeta cu = pw->cur;
+        if (cu.p >= 0) {
+            const int j = cu.base + sub;
+            if (j < cu.mk) {
+                const int64_t ro = (cu.row0 + j) * (int64_t)m + col0;
+                if (okc) {
+                    if (cu.flags & 2) cp_async16(&pw->data[slot][0][lane], a.plan + ro);
+                    if (ldL) cp_async16(&pw->data[slot][1][lane], a.lam + ro);
+                    if (doA) cp_async16(&pw->data[slot][2][lane], a.cost + ro);
+                }
+                if (cl == 0) cp_async4(&pw->wk[slot][sub], a.wt + cu.row0 + j);
+            }
+            if (cu.base == 0 && sub == 0 && okc) {
+                if (doB) cp_async16(&pw->hdr[slot][0][cl], a.pos_r + cu.p * m + col0);
+                cp_async16(&pw->hdr[slot][1][cl], a.w_cur + (int64_t)cu.c * m + col0);
+            }
+            if (lane == 0) {
+                PipeMeta mt = cu;
+                mt.flags = cu.flags | (cu.base == 0 ? 1 : 0);
+                pw->meta[slot] = mt;
+            }
+            if (cu.base + RPW >= cu.mk) {
+                load_cursor(cu.p + nw);
+            } else {
+                __syncwarp();
+                if (lane == 0) pw->cur.base = cu.base + RPW;
+                __syncwarp();
+            }
+        } else if (lane == 0) {
+            pw->meta[slot].p = -1;
+        }
+        cp_async_commit();
+    };
+
+#pragma unroll
+    for (int s0 = 0; s0 < PIPE_S - 1; ++s0) issue(s0);
+
+    // ---- compute cursor state (per member)
+    float coef[4], wcol[4], racc[4];
+    float beta = 0.f, rho = 0.f, objacc = 0.f;
+    bool ldP = false;
+    const float eps = a.eps;
+    int slot = 0;
+    for (;;) {
+        cp_async_wait<PIPE_S - 2>();
+        __syncwarp();
+        const PipeMeta mt = pw->meta[slot];
+        if (mt.p < 0) break;
+        const int64_t p = mt.p;
+        const int c = mt.c;
+        if (mt.flags & 1) {
+            beta = a.beta[c];
+            rho = a.rho[c];
+            ldP = mt.flags & 2;
+            const float4 wv = pw->hdr[slot][1][cl];
+            const float4 rv4 = pw->hdr[slot][0][cl];
+            wcol[0] = wv.x; wcol[1] = wv.y; wcol[2] = wv.z; wcol[3] = wv.w;
+            coef[0] = doB ? wv.x / rv4.x : 0.f;
+            coef[1] = doB ? wv.y / rv4.y : 0.f;
+            coef[2] = doB ? wv.z / rv4.z : 0.f;
+            coef[3] = doB ? wv.w / rv4.w : 0.f;
+#pragma unroll
+            for (int x = 0; x < 4; ++x) racc[x] = 0.f;
+            objacc = 0.f;
+        }
+        const int j = mt.base + sub;
+        const bool rv = j < mt.mk;
+        const bool act = rv && okc;
+        float pin[4] = {0.f, 0.f, 0.f, 0.f}, lin[4] = {0.f, 0.f, 0.f, 0.f}, cin[4] = {0.f, 0.f, 0.f, 0.f};
+        float wkj = 0.f;
+        if (rv) wkj = pw->wk[slot][sub];
+        if (act) {
+            if (ldP) {
+                const float4 t = pw->data[slot][0][lane];
+                pin[0] = t.x; pin[1] = t.y; pin[2] = t.z; pin[3] = t.w;
+            }
+            if (ldL) {
+                const float4 t = pw->data[slot][1][lane];
+                lin[0] = t.x; lin[1] = t.y; lin[2] = t.z; lin[3] = t.w;
+            }
+            if (doA) {
+                const float4 t = pw->data[slot][2][lane];
+                cin[0] = t.x; cin[1] = t.y; cin[2] = t.z; cin[3] = t.w;
+            }
+        }
+        const int64_t rowoff = (mt.row0 + (rv ? j : 0)) * (int64_t)m + col0;
+        float p2[4], l2[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            if (doB) {
+                const float pt = fmaf(pin[x], fast_exp2(lin[x] * beta), eps);
+                p2[x] = pt * coef[x];
+                l2[x] = fmaf(rho, pin[x] - p2[x], lin[x]);
+            } else {
+                p2[x] = ldP ? pin[x] : wcol[x] * wkj;
+                l2[x] = lin[x];
+            }
+        }
+        if (doA) {
+            float ex[4];
+            float smax = -INFINITY;
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                ex[x] = -(cin[x] + l2[x]) * beta;
+                if (okc) smax = fmaxf(smax, ex[x]);
+            }
+            smax = group_max<LPR>(smax);
+            const float epss = fast_exp2(fminf(a.log2eps - smax, 126.f));
+            float t1[4];
+            float rs = 0.f;
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                t1[x] = okc ? fmaf(p2[x], fast_exp2(ex[x] - smax), epss) : 0.f;
+                rs += t1[x];
+            }
+            rs = group_sum<LPR>(rs);
+            const float scale = rs > 0.f ? wkj / rs : 0.f;
+            float p1n[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                p1n[x] = t1[x] * scale;
+                if (act) {
+                    racc[x] += fmaf(p1n[x], fast_exp2(l2[x] * beta), eps);
+                    objacc = fmaf(cin[x], p1n[x], objacc);
+                }
+            }
+            if (act) {
+                VecIO<4>::st(a.plan + rowoff, p1n);
+                if (fl & SW_LAM_OUT) VecIO<4>::st(a.lam + rowoff, l2);
+            }
+        } else if (act) {
+            VecIO<4>::st(a.plan + rowoff, p2);
+            if (fl & SW_LAM_OUT) VecIO<4>::st(a.lam + rowoff, l2);
+        }
+        const bool last = mt.base + RPW >= mt.mk;
+        __syncwarp();
+        issue(slot);
+        slot = (slot + 1 == PIPE_S) ? 0 : slot + 1;
+
+        if (last && doA) {
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int o = LPR; o < 32; o <<= 1) racc[x] += __shfl_xor_sync(0xffffffffu, racc[x], o);
+            float tl = 0.f;
+            if (okc) tl = (racc[0] + racc[1]) + (racc[2] + racc[3]);
+            tl = group_sum<LPR>(tl);
+            const float inv_tl = 1.0f / tl;
+            if (sub == 0 && okc) {
+                *reinterpret_cast<float4*>(a.pos_r + p * m + col0) = make_float4(racc[0], racc[1], racc[2], racc[3]);
+                float q[4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const float wtl = racc[x] * inv_tl;
+                    q[x] = (fl & SW_R2) ? sqrtf(wtl) : wtl;
+                }
+                *reinterpret_cast<float4*>(a.pos_part + p * m + col0) = make_float4(q[0], q[1], q[2], q[3]);
+            }
+            if (fl & SW_OBJ) {
+                double ov = group_sum_d<32>((double)objacc);
+                if (lane == 0) a.pos_obj[p] = ov;
+            }
+            if (a.w_next) {
+                __threadfence();
+                __syncwarp();
+                int fin = 0;
+                if (lane == 0) {
+                    const int total = (int)(a.cofs[c + 1] - a.cofs[c]);
+                    fin = (atomicAdd(&a.counters[c], 1) + 1 == total);
+                }
+                fin = __shfl_sync(0xffffffffu, fin, 0);
+                if (fin) {
+                    __threadfence();
+                    warp_consensus(a, c);
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
 typedef void (*SweepFn)(SweepArgs);
+
+static SweepFn pick_sweep_pipe(int m, size_t* smem) {
+    if (m % 4 != 0 || m > 128) return nullptr;
+    if (m <= 4) { *smem = SWEEP_WARPS * sizeof(PipeWarp<1>); return k_sweep_pipe<1>; }
+    if (m <= 8) { *smem = SWEEP_WARPS * sizeof(PipeWarp<2>); return k_sweep_pipe<2>; }
+    if (m <= 16) { *smem = SWEEP_WARPS * sizeof(PipeWarp<4>); return k_sweep_pipe<4>; }
+    if (m <= 32) { *smem = SWEEP_WARPS * sizeof(PipeWarp<8>); return k_sweep_pipe<8>; }
+    if (m <= 64) { *smem = SWEEP_WARPS * sizeof(PipeWarp<16>); return k_sweep_pipe<16>; }
+    *smem = SWEEP_WARPS * sizeof(PipeWarp<32>);
+    return k_sweep_pipe<32>;
+}
 
 static SweepFn pick_sweep(int m) {
     if (m % 4 == 0) {
@@ -605,8 +890,22 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
     sa.log2eps = opts.eps > 0.0 ? (float)log2(opts.eps) : -INFINITY;
     sa.w_next64 = cw.w64;
     const int rflag = (opts.rule == D2_RULE_R2) ? SW_R2 : 0;
-    SweepFn sweep = pick_sweep(m);
-    const unsigned grid = (unsigned)d2_ceil_div(P, SWEEP_WARPS);
+    size_t sweep_smem = 0;
+    SweepFn sweep = nullptr;
+    if (!(opts.flags & D2_NO_PIPE)) sweep = pick_sweep_pipe(m, &sweep_smem);
+    if (sweep) {
+        if (sweep_smem > 48 * 1024)
+            D2_CK(ctx, cudaFuncSetAttribute(sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem));
+    } else {
+        sweep = pick_sweep(m);
+        sweep_smem = 0;
+    }
+    // persistent grid: as many CTAs as fit on the device at once
+    int dev_sms = 152, per_sm = 1;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep, SWEEP_THREADS, sweep_smem);
+    if (per_sm < 1) per_sm = 1;
+    const unsigned grid = (unsigned)std::min<int64_t>(d2_ceil_div(P, SWEEP_WARPS), (int64_t)dev_sms * per_sm);
     const int T = opts.iters, tau = opts.tau;
 
     auto launch = [&](int flags, const float* wcur, float* wnext) -> int {
@@ -615,7 +914,7 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
         s.w_cur = wcur;
         s.w_next = fix_w ? nullptr : wnext;
         d2_time_begin(ctx, ((flags & SW_A) && (flags & SW_B)) ? D2_KT_SWEEP_FUSED : D2_KT_SWEEP_HALF, st);
-        sweep<<<grid, SWEEP_THREADS, 0, st>>>(s);
+        sweep<<<grid, SWEEP_THREADS, sweep_smem, st>>>(s);
         d2_time_end(ctx, st);
         D2_LAUNCH_CK(ctx, "k_sweep");
         return D2_OK;

@@ -1,0 +1,130 @@
+"""GPU checks of the learned pruner against the FP64 oracle (oracle/mlp.py)
+and against the exact assignment.
+
+Forward/backward take FP16-rounded inputs with FP32 accumulation, so the
+embedding and the gradient blocks are compared in relative norm (2% / 5%).
+With a certified-only margin (delta = inf) or r = K the pruned assignment
+must equal the exact one label for label."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import mlp, w2_exact
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def d2():
+    import paper_1510_00012_gb300 as d2mod
+    from paper_1510_00012_gb300 import build
+    build.build()
+    return d2mod
+
+
+@pytest.fixture(scope="module")
+def ctx(d2):
+    return d2.Context(0)
+
+
+def small_problem(seed, N=40, d=6, K=5, m=4):
+    bags = synth.gaussian_class_bags(seed, N, d, K, mk=(2, 12), mu_sigma=2.0, alpha=1.0)
+    g = torch.Generator().manual_seed(seed + 1)
+    x = (torch.randn(K, m, d, generator=g) * 2.0).float()
+    w = torch.rand(K, m, generator=g) + 0.1
+    w = (w / w.sum(1, keepdim=True)).float()
+    return bags, x, w
+
+
+def relnorm(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-12))
+
+
+def test_embedding_matches_oracle(d2, ctx):
+    bags, x, w = small_problem(1)
+    db = d2.DeviceBags.from_synth(bags)
+    p = d2.Pruner(ctx, bags.d, hidden=32, embed=16, seed=3)
+    params = {k: v.double().numpy() for k, v in p.unpack(p.params()).items()}
+    ids = torch.arange(bags.N, dtype=torch.int64, device="cuda")
+    emb, mu = p.embed(db, ids)
+    emb, mu = emb.cpu().double().numpy(), mu.cpu().double().numpy()
+    for k in range(bags.N):
+        y, wy = bags.bag(k)
+        ref = mlp.embed(params, y, wy)
+        assert relnorm(emb[k], ref) < 2e-2, k
+        np.testing.assert_allclose(mu[k], wy @ y, atol=1e-5)
+
+
+def test_loss_and_gradient_match_oracle(d2, ctx):
+    bags, x, w = small_problem(2)
+    db = d2.DeviceBags.from_synth(bags)
+    p = d2.Pruner(ctx, bags.d, hidden=32, embed=16, seed=4)
+    params = {k: v.double().numpy() for k, v in p.unpack(p.params()).items()}
+    K = x.shape[0]
+    pairs = [(a, (a * 7 + 3) % K) for a in range(0, bags.N, 2)]
+    members = [bags.bag(k) for k in range(bags.N)]
+    cents = [(x[q].double().numpy(), w[q].double().numpy()) for q in range(K)]
+    targets = [w2_exact(cents[q][0], cents[q][1], *members[a]) for a, q in pairs]
+    L, g = mlp.pair_loss_and_grad(params, members, cents, pairs, targets)
+    pb = torch.tensor([a for a, _ in pairs], dtype=torch.int64, device="cuda")
+    pc = torch.tensor([q for _, q in pairs], dtype=torch.int32, device="cuda")
+    tg = torch.tensor(targets, dtype=torch.float32, device="cuda")
+    loss, grad = p.loss_grad(db, x.cuda(), w.cuda(), pb, pc, tg)
+    assert abs(float(loss) - L) <= 2e-2 * L
+    gg = {k: v.double().numpy() for k, v in p.unpack(grad.cpu()).items()}
+    for name in mlp.PARAM_NAMES:
+        assert relnorm(gg[name], g[name]) < 5e-2, (name, relnorm(gg[name], g[name]))
+
+
+def exact_labels(d2, ctx, db, x, w):
+    lab, dist = d2.d2_assign(ctx, db, x.cuda(), w.cuda())
+    return lab.cpu().numpy(), dist.cpu().numpy()
+
+
+def test_certified_margin_and_r_equal_K_are_exact(d2, ctx):
+    bags, x, w = small_problem(3, N=60, K=6)
+    db = d2.DeviceBags.from_synth(bags)
+    p = d2.Pruner(ctx, bags.d, hidden=32, embed=16, seed=5)
+    ref_lab, ref_dist = exact_labels(d2, ctx, db, x, w)
+    p.set_margin(2, 1e30)                 # only the exact mean-term bound prunes
+    lab, dist, st = d2.d2_assign(ctx, db, x.cuda(), w.cuda(), prune=p, want_stats=True)
+    np.testing.assert_array_equal(lab.cpu().numpy(), ref_lab)
+    np.testing.assert_allclose(dist.cpu().numpy(), ref_dist, rtol=1e-6)
+    assert st["exact_solves"] <= bags.N * 6 + bags.N * 2
+    p.set_margin(6, 0.0)                  # r = K: every centroid is a candidate
+    lab, dist, st = d2.d2_assign(ctx, db, x.cuda(), w.cuda(), prune=p, want_stats=True)
+    np.testing.assert_array_equal(lab.cpu().numpy(), ref_lab)
+    assert st["fallbacks"] == 0
+
+
+def test_train_then_prune(d2, ctx):
+    """Train on exact W^2 of every (bag, centroid) pair of a 16-class mixture,
+    then assign with r = 4: the loss must fall, the misassignment rate against
+    the exact assignment must stay small and fewer exact solves are needed."""
+    K, m, d = 16, 8, 8
+    bags = synth.gaussian_class_bags(7, 600, d, K, mk=(8, 24), mu_sigma=2.0, alpha=1.0)
+    db = d2.DeviceBags.from_synth(bags)
+    co = torch.zeros(K + 1, dtype=torch.int64)
+    lab = bags.labels
+    order = torch.sort(lab, stable=True).indices
+    co[1:] = torch.cumsum(torch.bincount(lab, minlength=K), 0)
+    x, w = synth.sample_initial_barycenters(8, bags, co, order, m)
+    x, w = x.cuda(), w.cuda()
+    N = bags.N
+    pb = torch.arange(N, device="cuda").repeat_interleave(K)
+    pc = torch.arange(K, device="cuda", dtype=torch.int32).repeat(N)
+    perm = torch.randperm(N * K, generator=torch.Generator().manual_seed(0)).cuda()
+    pb, pc = pb[perm].contiguous(), pc[perm].contiguous()
+    tg = d2.d2_w2_pairs(ctx, db, x, w, pb, pc)
+    p = d2.Pruner(ctx, d, hidden=64, embed=32, seed=9)
+    losses = p.train(db, x, w, pb, pc, tg, steps=400, batch=256, lr=2e-3, seed=1)
+    assert np.mean(losses[-20:]) < 0.3 * np.mean(losses[:20]), (losses[:5], losses[-5:])
+    r_default, delta = p.margin()
+    assert delta > 0
+    p.set_margin(4, delta)
+    ref_lab, _ = exact_labels(d2, ctx, db, x, w)
+    lab, _, st = d2.d2_assign(ctx, db, x, w, prune=p, want_stats=True)
+    mis = float(np.mean(lab.cpu().numpy() != ref_lab))
+    assert mis <= 0.02, mis
+    assert st["exact_solves"] < N * K
