@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libd2.so")
 
 D2_OK, D2_EINVAL, D2_ENOMEM, D2_ECUDA, D2_ETIMEOUT, D2_ENOTSUP, D2_ENOCONV = 0, -1, -2, -3, -4, -5, -6
 D2_RULE_R1, D2_RULE_R2 = 1, 2
-D2_FIX_X, D2_FIX_W, D2_VALIDATE, D2_NO_GRAPH = 0x1, 0x2, 0x4, 0x8
+D2_FIX_X, D2_FIX_W, D2_VALIDATE, D2_NO_GRAPH, D2_NO_PIPE = 0x1, 0x2, 0x4, 0x8, 0x10
 KT_NAMES = ("sweep_fused", "sweep_half", "cost", "support", "assign", "prune", "other")
 KT_COUNT = len(KT_NAMES)
 

@@ -25,13 +25,12 @@
 // arithmetic and keeps FP32 from underflowing on far-away points.
 //
 // Weight consensus (Eq. badmmw / badmmw2).  Each warp writes its member's
-// wtilde^(k) (FP32, normalised by one reciprocal) and counts its arrival on
-// the cluster; the warp that brings the count to N_c (no waiting anywhere)
-// sums the cluster's members in a fixed order in FP64, normalises, and
-// publishes w^{n+1} for the next launch.  The result does not depend on the
-// order in which warps finish.  Warps are persistent and take member
-// positions round-robin, so no warp idles at a CTA barrier while a sibling
-// finishes a longer member.
+// wtilde^(k) (FP32, normalised by one reciprocal); a small kernel then sums
+// every cluster's members in a fixed order in FP64 and publishes w^{n+1} for
+// the next pass, so the result does not depend on scheduling and the sweep
+// itself has no atomics, fences or barriers.  Warps are persistent and take
+// member positions round-robin, so no warp idles waiting for a sibling that
+// owns a longer member.
 #include <algorithm>
 
 #include "d2_internal.cuh"
@@ -106,57 +105,46 @@ __device__ __forceinline__ float fast_exp2(float x) {
     return y;
 }
 
-// Fixed-order FP64 consensus of cluster c by one warp (the last to finish a
-// member of c).  Lane (g, i) sums the members p = p0 + g, p0 + g + G, ... of
-// column i; the G groups and then the m columns are combined in a fixed order,
-// so the result does not depend on which warp runs it.
-__device__ __noinline__ void warp_consensus(const SweepArgs& a, int c) {
-    const int lane = threadIdx.x & 31;
-    const int m = a.m;
-    const int64_t p0 = a.cofs[c], p1 = a.cofs[c + 1];
-    const bool r2 = a.flags & SW_R2;
-    if (m <= 32) {
-        const int G = 32 / m;
-        const int g = lane / m, i = lane - g * m;
-        double acc = 0.0;
-        if (g < G)
-            for (int64_t p = p0 + g; p < p1; p += G) acc += (double)__ldcg(a.pos_part + p * m + i);
-        double s_i = acc;  // lanes of group 0 gather the other groups in order
-        for (int h = 1; h < G; ++h) {
-            double o = __shfl_sync(0xffffffffu, acc, (h * m + i) & 31);
-            if (g == 0) s_i += o;
+// Weight consensus (Eq. badmmw / badmmw2) of one cluster per CTA, in FP64 and
+// a fixed order: thread (g, i) sums the members p0 + g, p0 + g + G, ... of
+// column i, the G groups are then added in order, then the m columns.
+__global__ void __launch_bounds__(256) k_consensus(const int64_t* cofs, const float* pos_part, int m, bool r2,
+                                                   float* w_next, double* w_next64) {
+    __shared__ double s_acc[256 + 257];
+    const int c = blockIdx.x;
+    const int64_t p0 = cofs[c], p1 = cofs[c + 1];
+    if (p1 == p0) return;  // empty cluster: weights unchanged
+    const int G = 256 / m;
+    const int t = threadIdx.x;
+    const int i = t % m, g = t / m;
+    if (g < G) {
+        double acc0 = 0.0, acc1 = 0.0;
+        int64_t p = p0 + g;
+        for (; p + G < p1; p += 2 * G) {  // two independent chains, combined in order
+            acc0 += (double)pos_part[p * m + i];
+            acc1 += (double)pos_part[(p + G) * m + i];
         }
-        double v = (g == 0) ? (r2 ? s_i * s_i : s_i) : 0.0;
-        double tot = group_sum_d<32>(v);
-        if (g == 0) {
-            const double wv = v / tot;
-            a.w_next64[(int64_t)c * m + i] = wv;
-            a.w_next[(int64_t)c * m + i] = (float)wv;
-        }
-    } else {
-        double vals[8];
-        double part = 0.0;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int i = lane + 32 * t;
-            double acc = 0.0;
-            if (i < m)
-                for (int64_t p = p0; p < p1; ++p) acc += (double)__ldcg(a.pos_part + p * m + i);
-            vals[t] = r2 ? acc * acc : acc;
-            if (i < m) part += vals[t];
-        }
-        const double tot = group_sum_d<32>(part);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int i = lane + 32 * t;
-            if (i < m) {
-                const double wv = vals[t] / tot;
-                a.w_next64[(int64_t)c * m + i] = wv;
-                a.w_next[(int64_t)c * m + i] = (float)wv;
-            }
-        }
+        if (p < p1) acc0 += (double)pos_part[p * m + i];
+        s_acc[g * m + i] = acc0 + acc1;
     }
-    if (lane == 0) a.counters[c] = 0;
+    __syncthreads();
+    if (t < m) {
+        double sv = 0.0;
+        for (int h = 0; h < G; ++h) sv += s_acc[h * m + t];
+        s_acc[256 + t] = r2 ? sv * sv : sv;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double tot = 0.0;
+        for (int h = 0; h < m; ++h) tot += s_acc[256 + h];
+        s_acc[256 + 256] = tot;
+    }
+    __syncthreads();
+    if (t < m) {
+        const double wv = s_acc[256 + t] / s_acc[256 + 256];
+        w_next64[(int64_t)c * m + t] = wv;
+        w_next[(int64_t)c * m + t] = (float)wv;
+    }
 }
 
 template <int VEC, int LPR, int NV>
@@ -330,22 +318,6 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep(SweepArg
             if (fl & SW_OBJ) {
                 double ov = group_sum_d<32>((double)objacc);
                 if (lane == 0) a.pos_obj[p] = ov;
-            }
-            // arrival of this member; the last member of the cluster to
-            // arrive makes its warp run the consensus
-            if (a.w_next) {
-                __threadfence();
-                __syncwarp();
-                int last = 0;
-                if (lane == 0) {
-                    const int total = (int)(a.cofs[c + 1] - a.cofs[c]);
-                    last = (atomicAdd(&a.counters[c], 1) + 1 == total);
-                }
-                last = __shfl_sync(0xffffffffu, last, 0);
-                if (last) {
-                    __threadfence();
-                    warp_consensus(a, c);
-                }
             }
         }
     }
@@ -568,7 +540,9 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep_pipe(Swe
         }
         const bool last = mt.base + RPW >= mt.mk;
         __syncwarp();
-        issue(slot);
+        // refill the slot consumed one step earlier: stage n + PIPE_S - 1
+        // goes to slot (n + PIPE_S - 1) mod PIPE_S
+        issue(slot == 0 ? PIPE_S - 1 : slot - 1);
         slot = (slot + 1 == PIPE_S) ? 0 : slot + 1;
 
         if (last && doA) {
@@ -593,20 +567,6 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep_pipe(Swe
             if (fl & SW_OBJ) {
                 double ov = group_sum_d<32>((double)objacc);
                 if (lane == 0) a.pos_obj[p] = ov;
-            }
-            if (a.w_next) {
-                __threadfence();
-                __syncwarp();
-                int fin = 0;
-                if (lane == 0) {
-                    const int total = (int)(a.cofs[c + 1] - a.cofs[c]);
-                    fin = (atomicAdd(&a.counters[c], 1) + 1 == total);
-                }
-                fin = __shfl_sync(0xffffffffu, fin, 0);
-                if (fin) {
-                    __threadfence();
-                    warp_consensus(a, c);
-                }
             }
         }
     }
@@ -759,6 +719,125 @@ __global__ void __launch_bounds__(XU_THREADS) k_xpartial(const int64_t* members,
     }
 }
 
+
+// Pipelined support partials for m % 4 == 0 and d % 4 == 0: 128 threads own a
+// 32 (i) x 64 (d) output tile, 4 x 4 per thread; rows arrive in tiles of 64
+// through double-buffered cp.async copies of the matching Pi2 and y slices.
+#define XP_ROWS 32
+#define XP_PS (32 + 4)
+#define XP_YS (64 + 4)
+
+__device__ __forceinline__ void xp_cp16(void* sdst, const void* gsrc) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc));
+}
+
+__global__ void __launch_bounds__(128) k_xpartial_pipe(const int64_t* members, const int64_t* offsets,
+                                                       const float* supp, const int32_t* vidx, const float* vocab,
+                                                       int d, int m, const float* plan, const Chunk* chunks,
+                                                       const int64_t* nchunks, float* xpart) {
+    __shared__ __align__(16) float ps[2][XP_ROWS][XP_PS];
+    __shared__ __align__(16) float ys[2][XP_ROWS][XP_YS];
+    __shared__ int64_t s_rs[D2_CHUNK];
+    __shared__ int s_pre[D2_CHUNK + 1];
+    __shared__ int64_t s_row[2][XP_ROWS];
+    const int64_t q = blockIdx.x;
+    if (q >= *nchunks) return;
+    const int d0 = blockIdx.y * 64, i0 = blockIdx.z * 32;
+    if (d0 >= d || i0 >= m) return;
+    const Chunk ch = chunks[q];
+    const int nm = (int)(ch.p1 - ch.p0);
+    const int tid = threadIdx.x;
+    if (tid < nm) {
+        int64_t k = members[ch.p0 + tid];
+        s_rs[tid] = offsets[k];
+        s_pre[tid + 1] = (int)(offsets[k + 1] - offsets[k]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        s_pre[0] = 0;
+        for (int t = 0; t < nm; ++t) s_pre[t + 1] += s_pre[t];
+    }
+    __syncthreads();
+    const int R = s_pre[nm];
+    const int ntile = (R + XP_ROWS - 1) / XP_ROWS;
+    const int td = tid & 15, ti = tid >> 4;   // dd = td*4 .. +3, i = ti*4 .. +3
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+
+    auto rows_of = [&](int t, int b) {  // global rows of tile t into s_row[b]
+        if (tid < XP_ROWS) {
+            const int lr = t * XP_ROWS + tid;
+            int64_t g = -1;
+            if (lr < R) {
+                int lo = 0, hi = nm - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (s_pre[mid] <= lr) lo = mid; else hi = mid - 1;
+                }
+                g = s_rs[lo] + (lr - s_pre[lo]);
+            }
+            s_row[b][tid] = g;
+        }
+    };
+    auto issue = [&](int b) {
+        // Pi2 slices: 64 rows x 8 segments; y slices: 64 rows x 16 segments
+        for (int e = tid; e < XP_ROWS * 8; e += 128) {
+            const int r = e >> 3, sg = e & 7;
+            const int64_t g = s_row[b][r];
+            if (g >= 0 && i0 + sg * 4 < m) xp_cp16(&ps[b][r][sg * 4], plan + g * m + i0 + sg * 4);
+            else *reinterpret_cast<float4*>(&ps[b][r][sg * 4]) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int e = tid; e < XP_ROWS * 16; e += 128) {
+            const int r = e >> 4, sg = e & 15;
+            const int64_t g = s_row[b][r];
+            if (g >= 0 && d0 + sg * 4 < d) xp_cp16(&ys[b][r][sg * 4], d2_row_ptr(supp, vidx, vocab, d, g) + d0 + sg * 4);
+            else *reinterpret_cast<float4*>(&ys[b][r][sg * 4]) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        asm volatile("cp.async.commit_group;");
+    };
+    if (ntile > 0) {
+        rows_of(0, 0);
+        __syncthreads();
+        issue(0);
+    }
+    for (int t = 0; t < ntile; ++t) {
+        const int b = t & 1;
+        if (t + 1 < ntile) {
+            rows_of(t + 1, b ^ 1);
+            __syncthreads();
+            issue(b ^ 1);
+            asm volatile("cp.async.wait_group 1;");
+        } else {
+            asm volatile("cp.async.wait_group 0;");
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int r = 0; r < XP_ROWS; ++r) {
+            const float4 pv = *reinterpret_cast<const float4*>(&ps[b][r][ti * 4]);
+            const float4 yv = *reinterpret_cast<const float4*>(&ys[b][r][td * 4]);
+            const float pa[4] = {pv.x, pv.y, pv.z, pv.w};
+            const float ya[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(pa[u], ya[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+    float* out = xpart + q * (int64_t)m * d;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = i0 + ti * 4 + u;
+        const int dd = d0 + td * 4;
+        if (i < m && dd < d)
+            *reinterpret_cast<float4*>(out + (int64_t)i * d + dd) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+    }
+}
+
 __global__ void k_xfinal(int m, int d, const int64_t* cofs, const int64_t* chunk_first, const float* xpart,
                          const float* w, float* x) {
     const int c = blockIdx.x;
@@ -907,6 +986,9 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
     if (per_sm < 1) per_sm = 1;
     const unsigned grid = (unsigned)std::min<int64_t>(d2_ceil_div(P, SWEEP_WARPS), (int64_t)dev_sms * per_sm);
     const int T = opts.iters, tau = opts.tau;
+    // the d % 4 == 0 and m % 4 == 0 path copies 16-byte slices of plan and y rows
+    const bool xp_pipe = (d % 4 == 0) && (m % 4 == 0) &&
+        ((reinterpret_cast<uintptr_t>(bags->supp ? bags->supp : bags->vocab) & 15) == 0);
 
     auto launch = [&](int flags, const float* wcur, float* wnext) -> int {
         SweepArgs s = sa;
@@ -917,6 +999,12 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
         sweep<<<grid, SWEEP_THREADS, sweep_smem, st>>>(s);
         d2_time_end(ctx, st);
         D2_LAUNCH_CK(ctx, "k_sweep");
+        if ((flags & SW_A) && s.w_next) {
+            d2_time_begin(ctx, D2_KT_OTHER, st);
+            k_consensus<<<K, 256, 0, st>>>(cluster_offsets, sa.pos_part, m, rflag != 0, s.w_next, cw.w64);
+            d2_time_end(ctx, st);
+            D2_LAUNCH_CK(ctx, "k_consensus");
+        }
         return D2_OK;
     };
     auto wbuf = [&](int n) -> float* { return fix_w ? cw.wb[0] : cw.wb[n & 1]; };
@@ -934,9 +1022,15 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
             // Eq. (updatex) with Pi2^n and w^n, then the new cost
             dim3 g((unsigned)maxch, (unsigned)d2_ceil_div(d, XU_DT), (unsigned)d2_ceil_div(m, XU_MT));
             d2_time_begin(ctx, D2_KT_SUPPORT, st);
-            k_xpartial<<<g, XU_THREADS, 0, st>>>(members, bags->offsets, bags->supp, bags->vocab_idx,
-                                                  bags->vocab, d, m, plan, cw.chunks, cw.nchunks,
-                                                  static_cast<float*>(vxp));
+            if (xp_pipe) {
+                dim3 g2((unsigned)maxch, (unsigned)d2_ceil_div(d, 64), (unsigned)d2_ceil_div(m, 32));
+                k_xpartial_pipe<<<g2, 128, 0, st>>>(members, bags->offsets, bags->supp, bags->vocab_idx, bags->vocab,
+                                                    d, m, plan, cw.chunks, cw.nchunks, static_cast<float*>(vxp));
+            } else {
+                k_xpartial<<<g, XU_THREADS, 0, st>>>(members, bags->offsets, bags->supp, bags->vocab_idx,
+                                                      bags->vocab, d, m, plan, cw.chunks, cw.nchunks,
+                                                      static_cast<float*>(vxp));
+            }
             D2_LAUNCH_CK(ctx, "k_xpartial");
             k_xfinal<<<K, 256, 0, st>>>(m, d, cluster_offsets, cw.chunk_first, static_cast<float*>(vxp),
                                         wbuf(it), x);

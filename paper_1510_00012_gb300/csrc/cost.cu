@@ -170,6 +170,184 @@ __global__ void __launch_bounds__(COST_THREADS) k_cost(CostArgs a) {
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Pipelined variant for d % 4 == 0: member rows are staged in d-tiles of 32
+// floats with cp.async (a warp copies 4 rows of 128 B per instruction) into
+// a double-buffered tile [256 rows][36 floats] (row stride 144 B keeps 16-B
+// alignment and makes each thread's float4 reads of its own row
+// bank-conflict free); the copy of tile t+1 overlaps the FMAs of tile t.
+// ---------------------------------------------------------------------------
+#define CP_DT 32
+#define CP_STRIDE 36
+
+__device__ __forceinline__ void cost_cp16(void* sdst, const void* gsrc) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc));
+}
+__device__ __forceinline__ void cost_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cost_wait1() { asm volatile("cp.async.wait_group 1;"); }
+__device__ __forceinline__ void cost_wait0() { asm volatile("cp.async.wait_group 0;"); }
+
+template <int MT>
+__global__ void __launch_bounds__(COST_THREADS) k_cost_pipe(CostArgs a) {
+    extern __shared__ float4 dyn4[];
+    float* ys = reinterpret_cast<float*>(dyn4);                        // 2 x 256 x CP_STRIDE
+    float* xs = ys + 2 * COST_THREADS * CP_STRIDE;                      // d x MT
+    float* smu = xs + (size_t)a.d * MT;                                 // d
+    __shared__ int64_t s_rs[D2_CHUNK];
+    __shared__ int s_pre[D2_CHUNK + 1];
+    __shared__ int64_t s_row[COST_THREADS];
+    __shared__ double s_red[COST_THREADS / 32];
+
+    const int64_t q = blockIdx.x;
+    if (q >= *a.nchunks) return;
+    const Chunk ch = a.chunks[q];
+    const int c = ch.c;
+    const int nm = (int)(ch.p1 - ch.p0);
+    const int d = a.d, m = a.m;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < nm) {
+        int64_t k = a.members[ch.p0 + tid];
+        s_rs[tid] = a.offsets[k];
+        s_pre[tid + 1] = (int)(a.offsets[k + 1] - a.offsets[k]);
+    }
+    for (int t = tid; t < d; t += COST_THREADS) smu[t] = a.mu[(int64_t)c * d + t];
+    __syncthreads();
+    if (tid == 0) {
+        s_pre[0] = 0;
+        for (int t = 0; t < nm; ++t) s_pre[t + 1] += s_pre[t];
+    }
+    __syncthreads();
+    const int R = s_pre[nm];
+    const int ntile = (d + CP_DT - 1) / CP_DT;
+    double rowsum_acc = 0.0;
+
+    // copy d-tile `t` of the rows in s_row into buffer b (rows beyond R skipped)
+    auto issue = [&](int t, int b) {
+        const int d0 = t * CP_DT;
+        const int sub = lane >> 3, seg = lane & 7;      // 4 rows x 8 segments of 16 B
+        for (int r0 = warp * 4; r0 < COST_THREADS; r0 += 4 * (COST_THREADS / 32)) {
+            const int r = r0 + sub;
+            const int64_t g = s_row[r];
+            const int col = d0 + seg * 4;
+            if (g >= 0 && col < d) {
+                const float* src = d2_row_ptr(a.supp, a.vidx, a.vocab, d, g) + col;
+                cost_cp16(ys + ((size_t)b * COST_THREADS + r) * CP_STRIDE + seg * 4, src);
+            }
+        }
+        cost_commit();
+    };
+
+    for (int ct = 0; ct < m; ct += MT) {
+        __syncthreads();
+        for (int idx = tid; idx < d * MT; idx += COST_THREADS) {
+            int dd = idx / MT, i = idx - dd * MT;
+            xs[idx] = (ct + i < m) ? a.xt[((int64_t)c * m + ct + i) * d + dd] : 0.f;
+        }
+        for (int rbase = 0; rbase < R; rbase += COST_THREADS) {
+            __syncthreads();
+            {
+                const int lr = rbase + tid;
+                int64_t grow = -1;
+                if (lr < R) {
+                    int lo = 0, hi = nm - 1;
+                    while (lo < hi) {
+                        int mid = (lo + hi + 1) >> 1;
+                        if (s_pre[mid] <= lr) lo = mid; else hi = mid - 1;
+                    }
+                    grow = s_rs[lo] + (lr - s_pre[lo]);
+                }
+                s_row[tid] = grow;
+            }
+            __syncthreads();
+            const bool valid = rbase + tid < R;
+            float acc[MT];
+#pragma unroll
+            for (int i = 0; i < MT; ++i) acc[i] = 0.f;
+            float yn = 0.f;
+            issue(0, 0);
+            for (int t = 0; t < ntile; ++t) {
+                if (t + 1 < ntile) {
+                    issue(t + 1, (t + 1) & 1);
+                    cost_wait1();
+                } else {
+                    cost_wait0();
+                }
+                __syncthreads();
+                if (valid) {
+                    const float* yr = ys + ((size_t)(t & 1) * COST_THREADS + tid) * CP_STRIDE;
+                    const int d0 = t * CP_DT;
+                    const int dt = min(CP_DT, d - d0);
+                    for (int dd = 0; dd < dt; dd += 4) {
+                        const float4 y4 = *reinterpret_cast<const float4*>(yr + dd);
+                        const float yv[4] = {y4.x - smu[d0 + dd], y4.y - smu[d0 + dd + 1], y4.z - smu[d0 + dd + 2],
+                                             y4.w - smu[d0 + dd + 3]};
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            yn = fmaf(yv[u], yv[u], yn);
+                            const float* xr = xs + (size_t)(d0 + dd + u) * MT;
+#pragma unroll
+                            for (int i = 0; i < MT; i += 4) {
+                                const float4 xv = *reinterpret_cast<const float4*>(xr + i);
+                                acc[i] = fmaf(xv.x, yv[u], acc[i]);
+                                acc[i + 1] = fmaf(xv.y, yv[u], acc[i + 1]);
+                                acc[i + 2] = fmaf(xv.z, yv[u], acc[i + 2]);
+                                acc[i + 3] = fmaf(xv.w, yv[u], acc[i + 3]);
+                            }
+                        }
+                    }
+                }
+                __syncthreads();  // buffer t & 1 is refilled by the next issue
+            }
+            if (valid) {
+                const int64_t g = s_row[tid];
+                float* out = a.C + g * m + ct;
+                const float* xnr = a.xn + (int64_t)c * m + ct;
+                const int nv = min(MT, m - ct);
+                float rs = 0.f;
+#pragma unroll
+                for (int i = 0; i < MT; i += 4) {
+                    if (i < nv) {
+                        float4 v;
+                        v.x = fmaxf(fmaf(-2.f, acc[i], xnr[i] + yn), 0.f);
+                        v.y = fmaxf(fmaf(-2.f, acc[i + 1], xnr[i + 1] + yn), 0.f);
+                        v.z = fmaxf(fmaf(-2.f, acc[i + 2], xnr[i + 2] + yn), 0.f);
+                        v.w = fmaxf(fmaf(-2.f, acc[i + 3], xnr[i + 3] + yn), 0.f);
+                        __stcs(reinterpret_cast<float4*>(out + i), v);
+                        rs += (v.x + v.y) + (v.z + v.w);
+                    }
+                }
+                rowsum_acc += (double)rs;
+            }
+        }
+    }
+    if (a.chunk_sum) {
+        double v = group_sum_d<32>(rowsum_acc);
+        __syncthreads();
+        if (lane == 0) s_red[warp] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double sum = 0.0;
+            for (int w = 0; w < COST_THREADS / 32; ++w) sum += s_red[w];
+            a.chunk_sum[q] = sum;
+            a.chunk_rows[q] = R;
+        }
+    }
+}
+
+template <int MT>
+static int launch_cost_pipe(d2_ctx* ctx, const CostArgs& a, int64_t maxch, cudaStream_t st) {
+    size_t smem = ((size_t)2 * COST_THREADS * CP_STRIDE + (size_t)a.d * MT + a.d) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_cost_pipe<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return d2_cuda_fail(ctx, e, "k_cost_pipe smem attribute");
+    d2_time_begin(ctx, D2_KT_COST, st);
+    k_cost_pipe<MT><<<(unsigned)maxch, COST_THREADS, smem, st>>>(a);
+    d2_time_end(ctx, st);
+    D2_LAUNCH_CK(ctx, "k_cost_pipe");
+    return D2_OK;
+}
+
 template <int MT>
 static int launch_cost(d2_ctx* ctx, const CostArgs& a, int64_t maxch, cudaStream_t st) {
     size_t smem = ((size_t)a.d * MT + (size_t)COST_DT * COST_YPAD) * sizeof(float);
@@ -212,6 +390,14 @@ int d2_cost_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t 
     }
     if ((size_t)b->d * 64 * 4 + COST_DT * COST_YPAD * 4 > 200 * 1024)
         return d2_fail(ctx, D2_ENOTSUP, "d2_cost: support dimension %d too large for the cost tile", b->d);
+    const bool aligned16 = (b->d % 4 == 0) &&
+        ((reinterpret_cast<uintptr_t>(b->supp ? b->supp : b->vocab) & 15) == 0) && (m % 4 == 0);
+    if (aligned16 && ((size_t)2 * COST_THREADS * CP_STRIDE + (size_t)b->d * 64 + b->d) * 4 <= 200 * 1024) {
+        if (m <= 8) return launch_cost_pipe<8>(ctx, a, maxch, st);
+        if (m <= 16) return launch_cost_pipe<16>(ctx, a, maxch, st);
+        if (m <= 32) return launch_cost_pipe<32>(ctx, a, maxch, st);
+        return launch_cost_pipe<64>(ctx, a, maxch, st);
+    }
     if (m <= 8) return launch_cost<8>(ctx, a, maxch, st);
     if (m <= 16) return launch_cost<16>(ctx, a, maxch, st);
     if (m <= 32) return launch_cost<32>(ctx, a, maxch, st);

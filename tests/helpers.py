@@ -28,7 +28,7 @@ def split_clusters(labels, K):
     return co, order
 
 
-def run_gpu_badmm(d2, ctx, bags, cluster_offsets, members, x0, w0, plan0=None, warm=None, **kw):
+def run_gpu_badmm(d2, ctx, bags, cluster_offsets, members, x0, w0, plan0=None, warm=None, nopipe=False, **kw):
     db = d2.DeviceBags.from_synth(bags)
     x = x0.clone().cuda().contiguous()
     w = w0.clone().cuda().contiguous()
@@ -36,6 +36,8 @@ def run_gpu_badmm(d2, ctx, bags, cluster_offsets, members, x0, w0, plan0=None, w
             else torch.zeros(bags.n, x.shape[1], dtype=torch.float32, device="cuda"))
     wm = None if warm is None else warm.to(torch.uint8).cuda()
     opts = d2.badmm_opts(**kw)
+    if nopipe:
+        opts.flags |= d2.D2_NO_PIPE
     x, w, plan, obj = d2.badmm_barycenter(ctx, db, cluster_offsets.cuda(), members.cuda(), x, w, plan,
                                           wm, opts)
     torch.cuda.synchronize()

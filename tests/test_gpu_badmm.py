@@ -56,11 +56,12 @@ def ragged_case(seed, K, m, d=16, N=150, mk=(1, 24)):
     return bags, co, mem, x0, w0
 
 
-@pytest.mark.parametrize("m", [16, 12, 5, 32, 1])
-def test_batched_ragged_clusters(d2, ctx, m):
+@pytest.mark.parametrize("m,nopipe", [(16, False), (16, True), (12, False), (5, False), (32, False),
+                                      (32, True), (1, False), (64, False), (128, False)])
+def test_batched_ragged_clusters(d2, ctx, m, nopipe):
     K = 7
     bags, co, mem, x0, w0 = ragged_case(3, K, m)
-    gx, gw, gplan, gobj = run_gpu_badmm(d2, ctx, bags, co, mem, x0, w0, iters=31, tau=10)
+    gx, gw, gplan, gobj = run_gpu_badmm(d2, ctx, bags, co, mem, x0, w0, iters=31, tau=10, nopipe=nopipe)
     for c in range(K):
         ids, members = cluster_members(bags, co, mem, c)
         if not ids:
@@ -150,7 +151,7 @@ def test_deterministic(d2, ctx):
         assert torch.equal(u, v)
 
 
-@pytest.mark.parametrize("m,d", [(8, 2), (16, 16), (12, 7), (64, 300), (100, 3)])
+@pytest.mark.parametrize("m,d", [(8, 2), (16, 16), (12, 7), (64, 300), (100, 3), (100, 8), (32, 64)])
 def test_cost_matches_definition(d2, ctx, m, d):
     K = 3
     bags = synth.gaussian_class_bags(20 + m, 40, d, K, mk=(1, 30), mu_sigma=4.0)
