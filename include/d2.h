@@ -44,6 +44,7 @@ extern "C" {
 #define D2_ETIMEOUT (-4)  /* a bounded device-side wait expired                */
 #define D2_ENOTSUP  (-5)  /* valid request outside what this build implements  */
 #define D2_ENOCONV  (-6)  /* exact OT hit its pivot limit on some pair          */
+#define D2_ESCRATCH (-7)  /* problem larger than d2_assign_noalloc's fixed scratch */
 
 /* ---- options flags ---------------------------------------------------- */
 #define D2_RULE_R1   1    /* Eq. (badmmw):  w_i  prop. to (1/N) sum_k wtilde_i^(k)        */
@@ -242,6 +243,26 @@ int d2_assign(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,
 int d2_w2_pairs(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,
                 const float* x, const float* w, const int64_t* pair_bag,
                 const int32_t* pair_cent, int64_t npairs, float* out, void* stream);
+
+/* Exact assignment without any device allocation.  The paper has no
+ * counterpart: this is d2_assign with prune = NULL for callers that may not
+ * allocate device memory themselves or have a library do it (a process
+ * whose device memory is owned by another framework's fixed pool, or a
+ * service that must not allocate after start-up).  It takes no context.
+ * Scratch: one fixed file-scope device array holding up to
+ * D2_NOALLOC_MAX_PAIRS (2^20) pair distances, so it needs N * K <= 2^20 and
+ * returns D2_ESCRATCH beyond that.  Every GPU that loads the library keeps
+ * the array (about 4 MiB) until the process exits.  The first call on a
+ * device resolves the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (the
+ * counters are cleared by each call): calls that overlap on the GPU, on any
+ * streams, race.  Other arguments and results as for d2_assign.  Returns
+ * D2_OK, D2_EINVAL, D2_ESCRATCH, D2_ENOTSUP (m * max_mk too large) or
+ * D2_ECUDA. */
+#define D2_NOALLOC_MAX_PAIRS (1 << 20)
+int d2_assign_noalloc(const d2_bags* bags, int32_t K, int32_t m, const float* x, const float* w,
+                      int32_t* labels, float* dist, void* stream);
 
 /* Greedy merge of Eq. (merge) (Section 5): reduce bag ids[c] to m support
  * points for c = 0..cnt-1 -> x (device cnt x m x d), w (device cnt x m).

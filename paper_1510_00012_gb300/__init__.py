@@ -18,7 +18,8 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libd2.so")
 
-D2_OK, D2_EINVAL, D2_ENOMEM, D2_ECUDA, D2_ETIMEOUT, D2_ENOTSUP, D2_ENOCONV = 0, -1, -2, -3, -4, -5, -6
+D2_OK, D2_EINVAL, D2_ENOMEM, D2_ECUDA, D2_ETIMEOUT, D2_ENOTSUP, D2_ENOCONV, D2_ESCRATCH = 0, -1, -2, -3, -4, -5, -6, -7
+D2_NOALLOC_MAX_PAIRS = 1 << 20
 D2_RULE_R1, D2_RULE_R2 = 1, 2
 D2_FIX_X, D2_FIX_W, D2_VALIDATE, D2_NO_GRAPH, D2_NO_PIPE = 0x1, 0x2, 0x4, 0x8, 0x10
 KT_NAMES = ("sweep_fused", "sweep_half", "cost", "support", "assign", "prune", "other")
@@ -58,6 +59,7 @@ _SIGS = {
                                  c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "d2_assign": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
                           c_void_p, c_void_p, c_void_p, c_void_p]),
+    "d2_assign_noalloc": (c_int, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "d2_w2_pairs": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                             c_int64, c_void_p, c_void_p]),
     "d2_merge_init": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p,
@@ -391,3 +393,18 @@ class Pruner:
                                             _ptr(pair_bag), _ptr(pair_cent), _ptr(target), pair_bag.numel(),
                                             steps, batch, c_float(lr), c_uint64(seed), losses))
         return list(losses)
+
+
+def d2_assign_noalloc(bags, x, w):
+    """Exact assignment through the no-allocation entry point (no context):
+    labels (N int32), W^2 to the chosen centroid (N float32).  The output
+    tensors are allocated here by torch, not by the library."""
+    _need(x, torch.float32, "x")
+    _need(w, torch.float32, "w")
+    labels = torch.empty(bags.N, dtype=torch.int32, device=x.device)
+    dist = torch.empty(bags.N, dtype=torch.float32, device=x.device)
+    rc = lib().d2_assign_noalloc(bags.ref(), x.shape[0], x.shape[1], _ptr(x), _ptr(w), _ptr(labels), _ptr(dist),
+                                 _stream())
+    if rc != D2_OK:
+        raise D2Error(rc, "d2_assign_noalloc failed" + (": N * K exceeds the fixed scratch" if rc == D2_ESCRATCH else ""))
+    return labels, dist

@@ -457,3 +457,32 @@ extern "C" int d2_w2_pairs(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t 
     a.out = out;
     return d2_launch_pairs(ctx, a, npairs, st);
 }
+
+// All N x K pairs into D, then argmin per bag, with caller-provided scratch
+// (D: N*K floats, flags: 1 int, fail_count: 1 int64, both already zeroed).
+// No context, no allocation.
+cudaError_t d2_assign_exact_into(const d2_bags* b, int K, int m, const float* x, const float* w, int32_t* labels,
+                                 float* dist, float* D, int* flags, int64_t* fail_count, int device,
+                                 cudaStream_t st) {
+    AssignArgs a = d2_assign_args(b, K, m, x, w, flags, fail_count);
+    a.mode = 0;
+    a.npairs = b->N * (int64_t)K;
+    a.out = D;
+    a.warp_bytes = d2_assign_warp_bytes(m, b->max_mk);
+    if (a.warp_bytes > 200 * 1024) return cudaErrorInvalidValue;
+    const int wpb = (int)std::min<size_t>(4, std::max<size_t>(1, (200 * 1024) / a.warp_bytes));
+    const size_t smem = a.warp_bytes * wpb;
+    cudaError_t e = cudaFuncSetAttribute(k_w2_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int sms = 152, per_sm = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_w2_pairs, wpb * 32, smem);
+    per_sm = std::max(per_sm, 1);
+    const int64_t want = d2_ceil_div(std::max<int64_t>(a.npairs, 1), wpb);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min(want, (int64_t)sms * per_sm * 8));
+    a.max_phase = 8 * (a.m + a.nmax) + 64;
+    k_w2_pairs<<<grid, wpb * 32, smem, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_argmin_rows<<<(unsigned)d2_ceil_div(b->N, 256), 256, 0, st>>>(D, b->N, K, labels, dist);
+    return cudaGetLastError();
+}
