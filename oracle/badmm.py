@@ -9,7 +9,8 @@ Readings where the paper is silent or ambiguous (each listed in the design
 notes):
   * rho (Eq. rho): rho0 times the MEAN entry of all cost matrices of the
     cluster, computed once per call from the initial support, not recomputed
-    after the support moves.
+    after the support moves; if every cost is zero, rho = 1 (with C = 0 the
+    plans depend on Lambda / rho only, which does not depend on rho).
   * "Update x per tau loops": the support update (Eq. updatex) runs at the top
     of iterations n > 0 with n mod tau == 0 and uses the current Pi^(k,2) and
     w, whose row sums equal w_i, so N*w_i is the transported mass; a point
@@ -75,6 +76,8 @@ def badmm_barycenter(members, x0, w0, *, rho0=2.0, T=100, tau=10, eps=1e-16, rul
         total = sum(float(Ck.sum()) for Ck in C)
         count = m * sum(y.shape[0] for y in Y)
         rho = rho0 * total / count
+        if not rho > 0.0:
+            rho = 1.0  # all costs zero: every rho > 0 gives the same plans
     rho = float(rho)
 
     # Algorithm badmm, first line: Lambda := 0; Pi^(2),0 := Pi
