@@ -132,12 +132,138 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def rank_seed(seed, rank):
+    """Each rank solves its own independent problem of the same size."""
+    return seed + 7919 * rank
+
+
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """Slowest rank's time (the whole-job step time); identity on one rank."""
+    if dist is None:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(entries_per_rank, iters, world, ms_per_step):
+    """Whole-job plan-entry updates per second (weak scaling: every rank has
+    entries_per_rank entries)."""
+    return world * entries_per_rank * iters / (ms_per_step * 1e-3)
+
+
 def make_workload(name, seed, device):
     W = WORKLOADS[name]
     bags, co, mem = synth.ragged_cluster_bags(seed, W["clusters"], d=W["d"], nc=W["nc"], mk=W["mk"],
                                               mu_sigma=3.0, device=device)
     x0, w0 = synth.sample_initial_barycenters(seed + 1, bags, co, mem, W["m"])
     return bags, co, mem, x0, w0
+
+
+D2_WORKLOAD = dict(N=20000, d=16, K=10, mk=(8, 32), m=16, rounds=5, iters=100, tau=10,
+                   desc="D2-clustering: K=10, N=20,000 distributions, d=16, m_k~U{8..32}, 10 Gaussian "
+                        "classes (means N(0,4I), sigma=1), Dirichlet(0.5) weights, m=16, 5 rounds x 100 "
+                        "B-ADMM iterations")
+
+
+def d2_round_comparison(d2, ctx, dev, seed):
+    """Seconds per D2-clustering round: plain form vs batched vs batched + pruning.
+
+    plain   : every round = exact full-K assignment, then one badmm_barycenter
+              call per cluster with the register-prefetch sweep;
+    batched : d2_cluster (all clusters in one call, pipelined sweep), exact;
+    pruned  : d2_cluster with the learned pruner (trained on exact W^2 of
+              100k (bag, centroid) pairs against the batched run's centroids;
+              training time reported separately)."""
+    W = D2_WORKLOAD
+    bags = synth.gaussian_class_bags(seed, W["N"], W["d"], W["K"], mk=W["mk"], device=dev)
+    db = d2.DeviceBags(bags.offsets, bags.wt, bags.d, supp=bags.supp)
+    K, m, R = W["K"], W["m"], W["rounds"]
+    opts = d2.badmm_opts(iters=W["iters"], tau=W["tau"])
+    out = {"workload": W["desc"]}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    # batched (warm-up once, then timed)
+    d2.d2_cluster(ctx, db, K, m, 11, 1, opts)
+    (xb, wb, lb, ob), tb = timed(lambda: d2.d2_cluster(ctx, db, K, m, 11, R, opts))
+    # plain: the same rounds with one call per cluster
+    nop = d2.badmm_opts(iters=W["iters"], tau=W["tau"])
+    nop.flags |= d2.D2_NO_PIPE
+
+    def plain():
+        x, w = d2.d2_merge_init(ctx, db, torch.tensor(pick_ids(bags, K, m, 11), device=dev), m)
+        plan = torch.empty(bags.n, m, dtype=torch.float32, device=dev)
+        prev = None
+        objs = []
+        for _ in range(R):
+            lab, dist = d2.d2_assign(ctx, db, x, w)
+            objs.append(float(dist.double().mean()))
+            warm = (lab == prev).to(torch.uint8) if prev is not None else torch.zeros_like(lab, dtype=torch.uint8)
+            for c in range(K):
+                ids = torch.nonzero(lab == c).flatten().to(torch.int64)
+                if ids.numel() == 0:
+                    continue
+                co = torch.tensor([0, ids.numel()], dtype=torch.int64, device=dev)
+                xc, wc = x[c:c + 1].clone(), w[c:c + 1].clone()
+                d2.badmm_barycenter(ctx, db, co, ids, xc, wc, plan, warm, nop)
+                x[c:c + 1], w[c:c + 1] = xc, wc
+            prev = lab
+        return x, w, prev, objs
+
+    plain()
+    (xp, wp, lp, op), tp = timed(plain)
+    out["plain_s_per_round"] = tp / R
+    out["batched_s_per_round"] = tb / R
+    out["obj_plain"] = op
+    out["obj_batched"] = ob
+    out["max_rel_obj_diff_batched_vs_plain"] = max(abs(a - b) / b for a, b in zip(ob, op))
+    # learned pruning: train on exact W^2 against the batched centroids
+    g = torch.Generator(device=dev).manual_seed(seed + 5)
+    npairs = 100_000
+    pb = torch.randint(0, bags.N, (npairs,), generator=g, device=dev)
+    pc = torch.randint(0, K, (npairs,), generator=g, device=dev, dtype=torch.int32)
+    (tg), tt = timed(lambda: d2.d2_w2_pairs(ctx, db, xb, wb, pb, pc))
+    pr = d2.Pruner(ctx, bags.d, hidden=128, embed=64, seed=3)
+    _, ttrain = timed(lambda: pr.train(db, xb, wb, pb, pc, tg, steps=300, batch=1024, lr=2e-3, seed=4))
+    r, delta = pr.margin()
+    pr.set_margin(3, delta)
+    lab_exact, _ = d2.d2_assign(ctx, db, xb, wb)
+    (lab_pr, _, st), _ = timed(lambda: d2.d2_assign(ctx, db, xb, wb, prune=pr, want_stats=True))
+    d2.d2_cluster(ctx, db, K, m, 11, 1, opts, prune=pr)
+    (xq, wq, lq, oq), tq = timed(lambda: d2.d2_cluster(ctx, db, K, m, 11, R, opts, prune=pr))
+    out.update({"pruned_s_per_round": tq / R, "obj_pruned": oq,
+                "max_rel_obj_diff_pruned_vs_plain": max(abs(a - b) / b for a, b in zip(oq, op)),
+                "pruner": {"r": 3, "delta": delta, "train_pairs": npairs, "target_s": tt, "train_s": ttrain,
+                           "misassignment_vs_exact": float((lab_pr != lab_exact).float().mean()),
+                           "exact_solves": st["exact_solves"], "fallbacks": st["fallbacks"],
+                           "exact_solves_full": bags.N * K}})
+    out["speedup_batched_vs_plain"] = out["plain_s_per_round"] / out["batched_s_per_round"]
+    out["speedup_pruned_vs_plain"] = out["plain_s_per_round"] / out["pruned_s_per_round"]
+    return out
+
+
+def pick_ids(bags, K, m, seed):
+    """The K bags d2_cluster seeds its centroids from (SplitMix64 partial
+    Fisher-Yates over the ids with m_k >= m), for the plain-form replay."""
+    M = (1 << 64) - 1
+    sizes = (bags.offsets[1:] - bags.offsets[:-1]).cpu().tolist()
+    elig = [k for k, s_ in enumerate(sizes) if s_ >= m]
+    st = seed & M
+    for t in range(K):
+        st = (st + 0x9E3779B97F4A7C15) & M
+        z = st
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+        z ^= z >> 31
+        j = t + z % (len(elig) - t)
+        elig[t], elig[j] = elig[j], elig[t]
+    return elig[:K]
 
 
 def oracle_sample(name, seed, budget_s):
@@ -205,6 +331,7 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-d2", action="store_true", help="skip the D2-clustering s/round comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -225,7 +352,7 @@ def main():
     W = WORKLOADS[args.workload]
 
     t0 = time.time()
-    bags, co, mem, x0, w0 = make_workload(args.workload, args.seed + 7919 * rank, dev)
+    bags, co, mem, x0, w0 = make_workload(args.workload, rank_seed(args.seed, rank), dev)
     torch.cuda.synchronize()
     log("[bench] rank %d: generated %d distributions, %d support rows in %.1fs"
         % (rank, bags.N, bags.n, time.time() - t0))
@@ -270,13 +397,9 @@ def main():
     clocks = sampler.stop()
     kt = ctx.timing_read()
     ctx.timing(False)
-    ms_total = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     ms_step = ms_total / args.steps
-    value = world * entries * T / (ms_step * 1e-3)
+    value = job_rate(entries, T, world, ms_step)
 
     # roofline of the dominant kernel (the fused plan sweep)
     f_ms, f_n = kt["sweep_fused"]
@@ -329,14 +452,17 @@ def main():
             out_o.copy_(obj, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
-        e_ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
         e_step = e_ms / args.e2e_steps
-        e2e = {"value": world * entries * T / (e_step * 1e-3), "unit": UNIT, "ms_per_step": e_step,
+        e2e = {"value": job_rate(entries, T, world, e_step), "unit": UNIT, "ms_per_step": e_step,
                "steps": args.e2e_steps, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+
+    d2cmp = None
+    if rank == 0 and not args.no_d2:
+        try:
+            d2cmp = d2_round_comparison(d2, ctx, dev, args.seed + 17)
+        except Exception as exc:  # reported, never hides the main metric
+            d2cmp = {"error": repr(exc)}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -353,7 +479,7 @@ def main():
                            % (12 * entries / 1e9),
                            "parallelism": "independent problem per GPU" if world > 1 else "single GPU"},
                 "roofline": roof, "kernel_breakdown_ms_per_step": breakdown, "cpu_baseline": cpu,
-                "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+                "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "d2_round": d2cmp}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
