@@ -167,6 +167,14 @@ D2_WORKLOAD = dict(N=20000, d=16, K=10, mk=(8, 32), m=16, rounds=5, iters=100, t
 
 
 def d2_round_comparison(d2, ctx, dev, seed):
+    """Runs _d2_round_comparison on a side stream, so that every variant's
+    badmm_barycenter calls may replay their launch sequence as a CUDA graph."""
+    side = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(side):
+        return _d2_round_comparison(d2, ctx, dev, seed)
+
+
+def _d2_round_comparison(d2, ctx, dev, seed):
     """Seconds per D2-clustering round: plain form vs batched vs batched + pruning.
 
     plain   : every round = exact full-K assignment, then one badmm_barycenter
@@ -189,7 +197,7 @@ def d2_round_comparison(d2, ctx, dev, seed):
         torch.cuda.synchronize()
         return r, time.perf_counter() - t0
 
-    # batched (warm-up once, then timed)
+    # batched: warm-up once, then timed
     d2.d2_cluster(ctx, db, K, m, 11, 1, opts)
     (xb, wb, lb, ob), tb = timed(lambda: d2.d2_cluster(ctx, db, K, m, 11, R, opts))
     # plain: the same rounds with one call per cluster
@@ -245,6 +253,77 @@ def d2_round_comparison(d2, ctx, dev, seed):
                            "exact_solves_full": bags.N * K}})
     out["speedup_batched_vs_plain"] = out["plain_s_per_round"] / out["batched_s_per_round"]
     out["speedup_pruned_vs_plain"] = out["plain_s_per_round"] / out["pruned_s_per_round"]
+    return out
+
+
+PRUNE_WORKLOAD = dict(N=500_000, d=32, K=256, mk=(16, 64), m=32, r=8, train_pairs=100_000, eval_bags=50_000,
+                      desc="learned-pruning assignment: K=256 centroids (m=32, d=32) from one B-ADMM update "
+                           "on 256 Gaussian classes (means N(0,4I), sigma=1), N=500,000 distributions, "
+                           "m_k~U{16..64}, Dirichlet(1); MLP 32->128->128->64; r=8")
+
+
+def pruning_at_scale(d2, ctx, dev, seed, steps=1500):
+    """Misassignment rate and speedup of the learned pruner against the exact
+    full-K assignment (both on the same evaluation bags), plus the pruned
+    assignment time over all N bags."""
+    W = PRUNE_WORKLOAD
+    K, m, r = W["K"], W["m"], W["r"]
+    bags = synth.gaussian_class_bags(seed, W["N"], W["d"], K, mk=W["mk"], mu_sigma=2.0, alpha=1.0, device=dev)
+    db = d2.DeviceBags(bags.offsets, bags.wt, bags.d, supp=bags.supp)
+    lab = bags.labels
+    order = torch.sort(lab, stable=True).indices
+    co = torch.zeros(K + 1, dtype=torch.int64, device=dev)
+    co[1:] = torch.cumsum(torch.bincount(lab, minlength=K), 0)
+    x, w = synth.sample_initial_barycenters(seed + 1, bags, co, order, m)
+    d2.badmm_barycenter(ctx, db, co, order.contiguous(), x, w, None, None, d2.badmm_opts(iters=100, tau=10))
+    out = {"workload": W["desc"]}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = fn()
+        torch.cuda.synchronize()
+        return res, time.perf_counter() - t0
+
+    # training pairs: half the 8 nearest centroids by mean distance, half random
+    g = torch.Generator(device=dev).manual_seed(seed + 2)
+    npairs = W["train_pairs"]
+    half = npairs // 2
+    tb = torch.randint(0, bags.N, (npairs,), generator=g, device=dev)
+    owner = torch.repeat_interleave(torch.arange(bags.N, device=dev), bags.offsets[1:] - bags.offsets[:-1])
+    mu_b = torch.zeros(bags.N, W["d"], device=dev).index_add_(0, owner, bags.supp * bags.wt[:, None])
+    mu_c = (w[:, :, None] * x).sum(1)
+    near = torch.cdist(mu_b[tb[:half]], mu_c).topk(8, largest=False).indices
+    pick = torch.randint(0, 8, (half,), generator=g, device=dev)
+    pc = torch.empty(npairs, dtype=torch.int32, device=dev)
+    pc[:half] = near.gather(1, pick[:, None]).squeeze(1).to(torch.int32)
+    pc[half:] = torch.randint(0, K, (npairs - half,), generator=g, device=dev, dtype=torch.int32)
+    perm = torch.randperm(npairs, generator=g, device=dev)
+    tb, pc = tb[perm].contiguous(), pc[perm].contiguous()
+    tg, t_tg = timed(lambda: d2.d2_w2_pairs(ctx, db, x, w, tb, pc))
+    pr = d2.Pruner(ctx, W["d"], hidden=128, embed=64, seed=seed + 3)
+    losses, t_train = timed(lambda: pr.train(db, x, w, tb, pc, tg, steps=steps, batch=1024, lr=1e-3,
+                                             seed=seed + 4))
+    _, delta = pr.margin()
+    pr.set_margin(r, delta)
+    # evaluation bags: exact full K vs pruned on the same bags
+    ev = min(W["eval_bags"], bags.N)
+    sub = synth.subset_bags(bags, torch.arange(ev, device=dev))
+    dsub = d2.DeviceBags(sub.offsets, sub.wt, sub.d, supp=sub.supp)
+    d2.d2_assign(ctx, dsub, x, w)  # warm-up
+    (le, _), t_exact = timed(lambda: d2.d2_assign(ctx, dsub, x, w))
+    (lp, _, st), t_pruned = timed(lambda: d2.d2_assign(ctx, dsub, x, w, prune=pr, want_stats=True))
+    (la, _, st_all), t_all = timed(lambda: d2.d2_assign(ctx, db, x, w, prune=pr, want_stats=True))
+    mis = float((lp != le).float().mean())
+    out.update({"train_pairs": npairs, "target_w2_s": t_tg, "train_steps": steps, "train_s": t_train,
+                "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:])),
+                "r": r, "delta": delta, "eval_bags": ev,
+                "exact_full_K_s": t_exact, "exact_pairs_per_s": ev * K / t_exact,
+                "pruned_s": t_pruned, "speedup_vs_full_K": t_exact / t_pruned,
+                "misassignment_vs_exact": mis,
+                "pruned_exact_solves": st["exact_solves"], "pruned_fallbacks": st["fallbacks"],
+                "full_K_solves": ev * K,
+                "all_bags_pruned_s": t_all, "all_bags": bags.N, "all_bags_fallbacks": st_all["fallbacks"]})
     return out
 
 
@@ -332,6 +411,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-d2", action="store_true", help="skip the D2-clustering s/round comparison")
+    ap.add_argument("--pruning", action="store_true", help="also run the learned-pruning assignment at scale")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -464,6 +544,13 @@ def main():
         except Exception as exc:  # reported, never hides the main metric
             d2cmp = {"error": repr(exc)}
 
+    prune_res = None
+    if rank == 0 and args.pruning:
+        try:
+            prune_res = pruning_at_scale(d2, ctx, dev, args.seed + 31)
+        except Exception as exc:
+            prune_res = {"error": repr(exc)}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, desc, _ = oracle_sample(args.workload, args.seed, args.cpu_budget)
@@ -480,6 +567,8 @@ def main():
                            "parallelism": "independent problem per GPU" if world > 1 else "single GPU"},
                 "roofline": roof, "kernel_breakdown_ms_per_step": breakdown, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "d2_round": d2cmp}
+        if prune_res is not None:
+            line["pruning"] = prune_res
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

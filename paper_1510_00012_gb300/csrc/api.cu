@@ -57,6 +57,7 @@ extern "C" void d2_destroy(d2_ctx* ctx) {
         cudaEventDestroy(t.b);
     }
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     for (int s = 0; s < WS_NSLOTS; ++s)
         if (ctx->ws[s]) cudaFree(ctx->ws[s]);
     if (ctx->dev_flags) cudaFree(ctx->dev_flags);

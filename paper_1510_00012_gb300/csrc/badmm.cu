@@ -32,6 +32,7 @@
 // member positions round-robin, so no warp idles waiting for a sibling that
 // owns a longer member.
 #include <algorithm>
+#include <cstring>
 
 #include "d2_internal.cuh"
 
@@ -916,36 +917,19 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
     if (!fix_x) {
         if ((rc = d2_ws(ctx, WS_XPART, (size_t)maxch * m * d * 4, &vxp))) return rc;
     }
+    const bool need_sums = !(opts.rho > 0.0);
+    void *vpc = nullptr, *vcs = nullptr;
+    if ((rc = d2_ws(ctx, WS_POS_CLUSTER, (size_t)P * 4, &vpc))) return rc;
+    if (need_sums && (rc = d2_ws(ctx, WS_CHUNK_SUM, (size_t)maxch * 16, &vcs))) return rc;
     // the cluster workspace may have moved while growing the others
     rc = d2_cluster_ws(ctx, K, m, d, P, &cw);
     if (rc) return rc;
-
-    int32_t* pos_cluster = nullptr;
-    rc = d2_setup_clusters(ctx, cluster_offsets, P, K, &pos_cluster, &cw, st);
-    if (rc) return rc;
-    D2_CK(ctx, cudaMemsetAsync(cw.counters, 0, (size_t)K * 4, st));
-    D2_CK(ctx, cudaMemcpyAsync(cw.wb[0], w, (size_t)K * m * 4, cudaMemcpyDeviceToDevice, st));
-
+    if ((rc = d2_cost_prepare(ctx, bags, m))) return rc;
+    int32_t* pos_cluster = static_cast<int32_t*>(vpc);
+    double* chunk_sum = need_sums ? static_cast<double*>(vcs) : nullptr;
+    int64_t* chunk_rows = need_sums ? reinterpret_cast<int64_t*>(static_cast<char*>(vcs) + (size_t)maxch * 8) : nullptr;
     float* lam = static_cast<float*>(vlam);
     float* cost = static_cast<float*>(vcost);
-
-    // initial cost and rho (Eq. rho)
-    if ((rc = d2_prep_x(ctx, x, K, m, d, cw, st))) return rc;
-    const bool need_sums = !(opts.rho > 0.0);
-    if ((rc = d2_cost_rows(ctx, bags, members, P, K, m, cw, cost, need_sums, st))) return rc;
-    {
-        void* cs = nullptr;
-        double* chunk_sum = nullptr;
-        int64_t* chunk_rows = nullptr;
-        if (need_sums) {
-            if ((rc = d2_ws(ctx, WS_CHUNK_SUM, (size_t)maxch * 16, &cs))) return rc;
-            chunk_sum = static_cast<double*>(cs);
-            chunk_rows = reinterpret_cast<int64_t*>(static_cast<char*>(cs) + (size_t)maxch * 8);
-        }
-        k_rho<<<(unsigned)d2_ceil_div(K, 128), 128, 0, st>>>(K, m, cw.chunk_first, chunk_sum, chunk_rows,
-                                                            opts.rho0, opts.rho, cw.rho, cw.beta, cw.nrows);
-        D2_LAUNCH_CK(ctx, "k_rho");
-    }
 
     SweepArgs sa;
     sa.members = members;
@@ -989,6 +973,18 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
     // the d % 4 == 0 and m % 4 == 0 path copies 16-byte slices of plan and y rows
     const bool xp_pipe = (d % 4 == 0) && (m % 4 == 0) &&
         ((reinterpret_cast<uintptr_t>(bags->supp ? bags->supp : bags->vocab) & 15) == 0);
+
+  auto enqueue = [&]() -> int {
+    int rc = D2_OK;
+    if ((rc = d2_setup_clusters(ctx, cluster_offsets, P, K, &pos_cluster, &cw, st))) return rc;
+    D2_CK(ctx, cudaMemsetAsync(cw.counters, 0, (size_t)K * 4, st));
+    D2_CK(ctx, cudaMemcpyAsync(cw.wb[0], w, (size_t)K * m * 4, cudaMemcpyDeviceToDevice, st));
+    // initial cost and rho (Eq. rho)
+    if ((rc = d2_prep_x(ctx, x, K, m, d, cw, st))) return rc;
+    if ((rc = d2_cost_rows(ctx, bags, members, P, K, m, cw, cost, need_sums, st))) return rc;
+    k_rho<<<(unsigned)d2_ceil_div(K, 128), 128, 0, st>>>(K, m, cw.chunk_first, chunk_sum, chunk_rows,
+                                                        opts.rho0, opts.rho, cw.rho, cw.beta, cw.nrows);
+    D2_LAUNCH_CK(ctx, "k_rho");
 
     auto launch = [&](int flags, const float* wcur, float* wnext) -> int {
         SweepArgs s = sa;
@@ -1050,5 +1046,59 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
     k_finish<<<(unsigned)d2_ceil_div(K, 128), 128, 0, st>>>(K, m, cluster_offsets, sa.pos_obj, wbuf(T), w,
                                                             obj, true);
     D2_LAUNCH_CK(ctx, "k_finish");
+    return D2_OK;
+  };
+
+    // Replay the whole launch sequence as one CUDA graph when possible: on a
+    // non-default stream that is not itself being captured, with per-launch
+    // timing off.  The graph is rebuilt whenever anything it bakes in changes
+    // (pointers, sizes, options, workspace placement).
+    const bool want_graph = !(opts.flags & D2_NO_GRAPH) && !ctx->timing && st != nullptr;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (want_graph && cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return enqueue();
+    }
+    if (!want_graph || cap != cudaStreamCaptureStatusNone) return enqueue();
+    auto u = [](const void* p) { return (uint64_t)reinterpret_cast<uintptr_t>(p); };
+    uint64_t rho_bits, rho0_bits, eps_bits;
+    memcpy(&rho_bits, &opts.rho, 8);
+    memcpy(&rho0_bits, &opts.rho0, 8);
+    memcpy(&eps_bits, &opts.eps, 8);
+    const std::vector<uint64_t> key = {
+        (uint64_t)ctx->generation, (uint64_t)bags->N, (uint64_t)bags->n, (uint64_t)bags->d, (uint64_t)bags->max_mk,
+        u(bags->offsets), u(bags->supp), u(bags->vocab_idx), u(bags->vocab), (uint64_t)bags->V, u(bags->wt),
+        u(cluster_offsets), u(members), (uint64_t)P, (uint64_t)K, (uint64_t)m, u(x), u(w), u(plan),
+        u(warm_mask), u(obj), rho_bits, rho0_bits, eps_bits, (uint64_t)opts.iters, (uint64_t)opts.tau,
+        (uint64_t)opts.rule, (uint64_t)opts.flags};
+    if (ctx->graph_exec && ctx->graph_key == key) {
+        D2_CK(ctx, cudaGraphLaunch(ctx->graph_exec, st));
+        ctx->launches += ctx->graph_launches;
+        return D2_OK;
+    }
+    const int64_t l0 = ctx->launches;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return enqueue();
+    }
+    const int rc_cap = enqueue();
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (rc_cap == D2_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    const int64_t nl = ctx->launches - l0;
+    ctx->launches = l0;
+    if (rc_cap != D2_OK || e != cudaSuccess || !exec) {  // capture refused: launch directly
+        cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        return enqueue();
+    }
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = exec;
+    ctx->graph_key = key;
+    ctx->graph_launches = nl;
+    D2_CK(ctx, cudaGraphLaunch(exec, st));
+    ctx->launches += nl;
     return D2_OK;
 }

@@ -362,6 +362,28 @@ static int launch_cost(d2_ctx* ctx, const CostArgs& a, int64_t maxch, cudaStream
     return D2_OK;
 }
 
+int d2_cost_prepare(d2_ctx* ctx, const d2_bags* b, int m) {
+    const bool aligned16 = (b->d % 4 == 0) &&
+        ((reinterpret_cast<uintptr_t>(b->supp ? b->supp : b->vocab) & 15) == 0) && (m % 4 == 0);
+    const int MT = m <= 8 ? 8 : m <= 16 ? 16 : m <= 32 ? 32 : 64;
+    size_t smem;
+    const void* fn;
+    if (aligned16 && ((size_t)2 * COST_THREADS * CP_STRIDE + (size_t)b->d * 64 + b->d) * 4 <= 200 * 1024) {
+        smem = ((size_t)2 * COST_THREADS * CP_STRIDE + (size_t)b->d * MT + b->d) * sizeof(float);
+        fn = MT == 8 ? (const void*)k_cost_pipe<8> : MT == 16 ? (const void*)k_cost_pipe<16>
+           : MT == 32 ? (const void*)k_cost_pipe<32> : (const void*)k_cost_pipe<64>;
+    } else {
+        smem = ((size_t)b->d * MT + (size_t)COST_DT * COST_YPAD) * sizeof(float);
+        fn = MT == 8 ? (const void*)k_cost<8> : MT == 16 ? (const void*)k_cost<16>
+           : MT == 32 ? (const void*)k_cost<32> : (const void*)k_cost<64>;
+    }
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return d2_cuda_fail(ctx, e, "cost kernel smem attribute");
+    }
+    return D2_OK;
+}
+
 int d2_cost_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t P, int K, int m,
                  const ClusterWs& cw, float* C, bool want_sums, cudaStream_t st) {
     int64_t maxch = d2_ceil_div(P, D2_CHUNK) + K + 1;

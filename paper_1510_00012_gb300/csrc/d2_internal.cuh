@@ -50,6 +50,10 @@ struct d2_ctx {
     std::vector<cudaEvent_t> ev_pool;   // recycled events
     double t_ms[D2_KT_COUNT] = {};
     int64_t t_n[D2_KT_COUNT] = {};
+    // last captured badmm_barycenter launch sequence and what it was built for
+    std::vector<uint64_t> graph_key;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_launches = 0;
 };
 
 // Event bracket around one launch when timing is on (no-ops otherwise).
@@ -154,6 +158,9 @@ int d2_setup_clusters(d2_ctx* ctx, const int64_t* cofs, int64_t P, int K, int32_
 
 // Centre and norms of each barycenter (mu_c, x_c - mu_c, ||x_c,i - mu_c||^2).
 int d2_prep_x(d2_ctx* ctx, const float* x, int K, int m, int d, const ClusterWs& cw, cudaStream_t st);
+
+// Sets the launch attributes d2_cost_rows will need (done before a capture).
+int d2_cost_prepare(d2_ctx* ctx, const d2_bags* b, int m);
 
 // Cost rows of every member position; accumulates FP64 sums per cluster when csum.
 int d2_cost_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t P, int K, int m,

@@ -296,13 +296,14 @@ def sample_initial_barycenters(seed: int, bags: Bags, cluster_offsets: torch.Ten
 
 def subset_bags(bags: Bags, ids) -> Bags:
     """Bags restricted to the given bag ids (renumbered 0..len(ids)-1)."""
-    ids = torch.as_tensor(ids, dtype=torch.int64, device=bags.offsets.device)
+    dev = bags.offsets.device
+    ids = torch.as_tensor(ids, dtype=torch.int64, device=dev)
     lo = bags.offsets[ids]
     sz = bags.offsets[ids + 1] - lo
     offsets = _ragged(sz)
-    rows = torch.cat([torch.arange(int(a), int(a) + int(s), device=bags.offsets.device)
-                      for a, s in zip(lo.tolist(), sz.tolist())]) if ids.numel() else \
-        torch.zeros(0, dtype=torch.int64, device=bags.offsets.device)
+    n = int(offsets[-1])
+    owner = torch.repeat_interleave(torch.arange(ids.numel(), device=dev), sz)
+    rows = lo[owner] + (torch.arange(n, device=dev) - offsets[:-1][owner])
     return Bags(offsets, bags.wt[rows].clone(), bags.d,
                 supp=None if bags.supp is None else bags.supp[rows].clone(),
                 vocab_idx=None if bags.vocab_idx is None else bags.vocab_idx[rows].clone(),

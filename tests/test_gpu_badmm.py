@@ -223,3 +223,31 @@ def test_full_size_ragged_clusters(d2, ctx):
             a, b = int(host.offsets[k]), int(host.offsets[k + 1])
             got = plan[a:b].double().cpu().numpy().T
             np.testing.assert_allclose(got, ref["P2"][t], atol=1e-5, rtol=0)
+
+
+def test_graph_replay_matches_direct_launches(d2, ctx):
+    """On a non-default stream the launch sequence is captured once and
+    replayed; new data in the same buffers must give the direct results."""
+    K, m = 5, 16
+    bags, co, mem, x0, w0 = ragged_case(15, K, m)
+    db = d2.DeviceBags.from_synth(bags)
+    co_d, mem_d = co.cuda(), mem.cuda()
+    s = torch.cuda.Stream()
+    x = torch.empty(K, m, bags.d, device="cuda")
+    w = torch.empty(K, m, device="cuda")
+    plan = torch.zeros(bags.n, m, device="cuda")
+    obj = torch.empty(K, dtype=torch.float64, device="cuda")
+    results = []
+    for shift in (0.0, 0.5, 0.5):
+        for graph in (True, False):
+            with torch.cuda.stream(s):
+                x.copy_(x0.cuda() + shift)
+                w.copy_(w0.cuda())
+                d2.badmm_barycenter(ctx, db, co_d, mem_d, x, w, plan, None,
+                                    d2.badmm_opts(iters=23, tau=10, graph=graph), obj)
+            s.synchronize()
+            results.append((x.clone(), w.clone(), plan.clone(), obj.clone()))
+    for i in range(0, len(results), 2):
+        for a, b in zip(results[i], results[i + 1]):
+            assert torch.equal(a, b)
+    assert not torch.equal(results[0][0], results[2][0])
