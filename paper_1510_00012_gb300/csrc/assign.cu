@@ -48,6 +48,10 @@ struct AssignArgs {
     size_t warp_bytes;
 };
 
+// the cost-build staging (AS_DC x (m + n) floats) lives in the flow tableau,
+// which is only cleared after the cost is built, whenever it fits there
+__host__ __device__ static inline bool staging_in_flows(int m, int nmax) { return AS_DC * (m + nmax) <= m * nmax; }
+
 struct WarpMem {
     float* C;      // m x n
     float* F;      // m x n
@@ -277,9 +281,15 @@ __global__ void k_w2_pairs(AssignArgs a) {
     s.pot = s.F + m * n;
     s.dist = s.pot + V;
     s.exc = s.dist + V;
-    s.xs = s.exc + V;
-    s.ys = s.xs + AS_DC * m;
-    s.pred = reinterpret_cast<short*>(s.ys + AS_DC * n);
+    if (staging_in_flows(m, n)) {
+        s.xs = s.F;
+        s.ys = s.F + AS_DC * m;
+        s.pred = reinterpret_cast<short*>(s.exc + V);
+    } else {
+        s.xs = s.exc + V;
+        s.ys = s.xs + AS_DC * m;
+        s.pred = reinterpret_cast<short*>(s.ys + AS_DC * n);
+    }
     s.vis = reinterpret_cast<unsigned char*>(s.pred + V);
 
     int64_t total;
@@ -341,10 +351,27 @@ __global__ void k_argmin_rows(const float* D, int64_t N, int K, int32_t* labels,
     dist[k] = b;
 }
 
+
 size_t d2_assign_warp_bytes(int m, int nmax) {
     const int V = m + nmax;
-    size_t b = (size_t)(2 * m * nmax + 3 * V + AS_DC * (m + nmax)) * 4 + (size_t)V * 2 + V;
+    const int stage = staging_in_flows(m, nmax) ? 0 : AS_DC * (m + nmax);
+    size_t b = (size_t)(2 * m * nmax + 3 * V + stage) * 4 + (size_t)V * 2 + V;
     return (b + 15) & ~(size_t)15;
+}
+
+// warps per block that maximise resident warps per SM for this footprint
+static int pick_wpb(size_t warp_bytes) {
+    const size_t per_sm = 227 * 1024;
+    int best = 1, best_w = 0;
+    for (int w = 1; w <= 8; ++w) {
+        if (warp_bytes * w > 200 * 1024) break;
+        const int res = (int)(per_sm / (warp_bytes * w)) * w;
+        if (res >= best_w) {
+            best_w = res;
+            best = w;
+        }
+    }
+    return best;
 }
 
 // Launch the pair solver; grid is a bound (persistent stride loop).
@@ -352,7 +379,7 @@ int d2_launch_pairs(d2_ctx* ctx, AssignArgs a, int64_t max_units, cudaStream_t s
     a.warp_bytes = d2_assign_warp_bytes(a.m, a.nmax);
     if (a.warp_bytes > 200 * 1024)
         return d2_fail(ctx, D2_ENOTSUP, "d2_assign: m * max_mk too large for the per-warp tableau");
-    int wpb = (int)std::min<size_t>(4, std::max<size_t>(1, (200 * 1024) / a.warp_bytes));
+    const int wpb = pick_wpb(a.warp_bytes);
     size_t smem = a.warp_bytes * wpb;
     cudaError_t e = cudaFuncSetAttribute(k_w2_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return d2_cuda_fail(ctx, e, "k_w2_pairs smem attribute");
@@ -470,7 +497,7 @@ cudaError_t d2_assign_exact_into(const d2_bags* b, int K, int m, const float* x,
     a.out = D;
     a.warp_bytes = d2_assign_warp_bytes(m, b->max_mk);
     if (a.warp_bytes > 200 * 1024) return cudaErrorInvalidValue;
-    const int wpb = (int)std::min<size_t>(4, std::max<size_t>(1, (200 * 1024) / a.warp_bytes));
+    const int wpb = pick_wpb(a.warp_bytes);
     const size_t smem = a.warp_bytes * wpb;
     cudaError_t e = cudaFuncSetAttribute(k_w2_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

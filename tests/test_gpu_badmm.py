@@ -128,10 +128,11 @@ def test_warm_start_chain(d2, ctx):
         compare_cluster(bags, co, mem, c, gx2, gw2, gplan2, gobj2, r2, x_tol=x_tol(r2))
 
 
-def test_vocabulary_bags(d2, ctx):
-    """Supports stored as indices into a word table (d=48)."""
-    bags = synth.document_bags(5, 80, V=400, d=48, mk=(3, 20))
-    K, m = 3, 8
+@pytest.mark.parametrize("d,m,mk", [(48, 8, (3, 20)), (300, 64, (10, 60))])
+def test_vocabulary_bags(d2, ctx, d, m, mk):
+    """Supports stored as indices into a word table (document-like bags)."""
+    bags = synth.document_bags(5, 80, V=400, d=d, mk=mk)
+    K = 3
     lab = torch.arange(bags.N) % K
     co, mem = split_clusters(lab, K)
     x0, w0 = synth.sample_initial_barycenters(6, bags, co, mem, m)
