@@ -119,14 +119,18 @@ __global__ void __launch_bounds__(256) k_consensus(const int64_t* cofs, const fl
     const int t = threadIdx.x;
     const int i = t % m, g = t / m;
     if (g < G) {
-        double acc0 = 0.0, acc1 = 0.0;
+        // eight independent load/add chains, combined in a fixed order
+        double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         int64_t p = p0 + g;
-        for (; p + G < p1; p += 2 * G) {  // two independent chains, combined in order
-            acc0 += (double)pos_part[p * m + i];
-            acc1 += (double)pos_part[(p + G) * m + i];
+        for (; p + 7 * G < p1; p += 8 * G) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcg(pos_part + (p + u * G) * m + i);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] += (double)v[u];
         }
-        if (p < p1) acc0 += (double)pos_part[p * m + i];
-        s_acc[g * m + i] = acc0 + acc1;
+        for (int u = 0; p < p1; p += G, ++u) acc[u] += (double)pos_part[p * m + i];
+        s_acc[g * m + i] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
     }
     __syncthreads();
     if (t < m) {
@@ -336,7 +340,6 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep(SweepArg
 // registers.  The issue side walks the same member sequence as the compute
 // side and leaves each stage's member metadata next to its data.
 // ---------------------------------------------------------------------------
-#define PIPE_S 4
 
 struct PipeMeta {
     int64_t p;      // member position (-1: no more work)
@@ -356,28 +359,34 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
 
-template <int LPR>
+template <int LPR, int NV, int S>
 struct PipeWarp {
-    float4 data[PIPE_S][3][32];   // plan, lambda, cost
-    float4 hdr[PIPE_S][2][LPR];   // r_k and w columns of the member (first group)
-    float wk[PIPE_S][32 / LPR];   // row weights
-    PipeMeta meta[PIPE_S];
+    float4 data[S][3][NV][32];    // plan, lambda, cost
+    float4 hdr[S][2][NV][LPR];    // r_k and w columns of the member (first group)
+    float wk[S][32 / LPR];        // row weights
+    PipeMeta meta[S];
     PipeMeta cur;                 // issue cursor: member being issued, next row group
 };
 
-template <int LPR>
+template <int LPR, int NV, int S>
 __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep_pipe(SweepArgs a) {
     constexpr int RPW = 32 / LPR;
+    constexpr int NE = 4 * NV;
     extern __shared__ float4 pipe_dyn[];
-    PipeWarp<LPR>* pw = reinterpret_cast<PipeWarp<LPR>*>(pipe_dyn) + (threadIdx.x >> 5);
+    PipeWarp<LPR, NV, S>* pw = reinterpret_cast<PipeWarp<LPR, NV, S>*>(pipe_dyn) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int sub = lane / LPR, cl = lane % LPR;
     const int m = a.m;
     const int fl = a.flags;
     const bool doA = fl & SW_A, doB = fl & SW_B;
     const bool ldL = !(fl & SW_LAM_ZERO);
-    const int col0 = cl * 4;
-    const bool okc = col0 < m;
+    bool okv[NV];
+    int colv[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        colv[v] = (cl + LPR * v) * 4;
+        okv[v] = colv[v] < m;
+    }
     const int64_t nw = (int64_t)gridDim.x * SWEEP_WARPS;
 
     // ---- issue cursor (lives in shared memory; lane 0 advances it)
@@ -409,17 +418,25 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep_pipe(Swe
         if (cu.p >= 0) {
             const int j = cu.base + sub;
             if (j < cu.mk) {
-                const int64_t ro = (cu.row0 + j) * (int64_t)m + col0;
-                if (okc) {
-                    if (cu.flags & 2) cp_async16(&pw->data[slot][0][lane], a.plan + ro);
-                    if (ldL) cp_async16(&pw->data[slot][1][lane], a.lam + ro);
-                    if (doA) cp_async16(&pw->data[slot][2][lane], a.cost + ro);
+                const int64_t ro = (cu.row0 + j) * (int64_t)m;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    if (okv[v]) {
+                        if (cu.flags & 2) cp_async16(&pw->data[slot][0][v][lane], a.plan + ro + colv[v]);
+                        if (ldL) cp_async16(&pw->data[slot][1][v][lane], a.lam + ro + colv[v]);
+                        if (doA) cp_async16(&pw->data[slot][2][v][lane], a.cost + ro + colv[v]);
+                    }
                 }
                 if (cl == 0) cp_async4(&pw->wk[slot][sub], a.wt + cu.row0 + j);
             }
-            if (cu.base == 0 && sub == 0 && okc) {
-                if (doB) cp_async16(&pw->hdr[slot][0][cl], a.pos_r + cu.p * m + col0);
-                cp_async16(&pw->hdr[slot][1][cl], a.w_cur + (int64_t)cu.c * m + col0);
+            if (cu.base == 0 && sub == 0) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    if (okv[v]) {
+                        if (doB) cp_async16(&pw->hdr[slot][0][v][cl], a.pos_r + cu.p * m + colv[v]);
+                        cp_async16(&pw->hdr[slot][1][v][cl], a.w_cur + (int64_t)cu.c * m + colv[v]);
+                    }
+                }
             }
             if (lane == 0) {
                 PipeMeta mt = cu;
@@ -440,16 +457,16 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep_pipe(Swe
     };
 
 #pragma unroll
-    for (int s0 = 0; s0 < PIPE_S - 1; ++s0) issue(s0);
+    for (int s0 = 0; s0 < S - 1; ++s0) issue(s0);
 
     // ---- compute cursor state (per member)
-    float coef[4], wcol[4], racc[4];
+    float coef[NE], wcol[NE], racc[NE];
     float beta = 0.f, rho = 0.f, objacc = 0.f;
     bool ldP = false;
     const float eps = a.eps;
     int slot = 0;
     for (;;) {
-        cp_async_wait<PIPE_S - 2>();
+        cp_async_wait<S - 2>();
         __syncwarp();
         const PipeMeta mt = pw->meta[slot];
         if (mt.p < 0) break;
@@ -459,41 +476,43 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep_pipe(Swe
             beta = a.beta[c];
             rho = a.rho[c];
             ldP = mt.flags & 2;
-            const float4 wv = pw->hdr[slot][1][cl];
-            const float4 rv4 = pw->hdr[slot][0][cl];
-            wcol[0] = wv.x; wcol[1] = wv.y; wcol[2] = wv.z; wcol[3] = wv.w;
-            coef[0] = doB ? wv.x / rv4.x : 0.f;
-            coef[1] = doB ? wv.y / rv4.y : 0.f;
-            coef[2] = doB ? wv.z / rv4.z : 0.f;
-            coef[3] = doB ? wv.w / rv4.w : 0.f;
 #pragma unroll
-            for (int x = 0; x < 4; ++x) racc[x] = 0.f;
+            for (int v = 0; v < NV; ++v) {
+                const float4 wv = pw->hdr[slot][1][v][cl];
+                const float4 rv4 = pw->hdr[slot][0][v][cl];
+                const float wa[4] = {wv.x, wv.y, wv.z, wv.w};
+                const float ra[4] = {rv4.x, rv4.y, rv4.z, rv4.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    wcol[v * 4 + e] = okv[v] ? wa[e] : 0.f;
+                    coef[v * 4 + e] = (doB && okv[v]) ? wa[e] / ra[e] : 0.f;
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < NE; ++x) racc[x] = 0.f;
             objacc = 0.f;
         }
         const int j = mt.base + sub;
         const bool rv = j < mt.mk;
-        const bool act = rv && okc;
-        float pin[4] = {0.f, 0.f, 0.f, 0.f}, lin[4] = {0.f, 0.f, 0.f, 0.f}, cin[4] = {0.f, 0.f, 0.f, 0.f};
+        float pin[NE], lin[NE], cin[NE];
         float wkj = 0.f;
         if (rv) wkj = pw->wk[slot][sub];
-        if (act) {
-            if (ldP) {
-                const float4 t = pw->data[slot][0][lane];
-                pin[0] = t.x; pin[1] = t.y; pin[2] = t.z; pin[3] = t.w;
-            }
-            if (ldL) {
-                const float4 t = pw->data[slot][1][lane];
-                lin[0] = t.x; lin[1] = t.y; lin[2] = t.z; lin[3] = t.w;
-            }
-            if (doA) {
-                const float4 t = pw->data[slot][2][lane];
-                cin[0] = t.x; cin[1] = t.y; cin[2] = t.z; cin[3] = t.w;
-            }
-        }
-        const int64_t rowoff = (mt.row0 + (rv ? j : 0)) * (int64_t)m + col0;
-        float p2[4], l2[4];
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
+        for (int v = 0; v < NV; ++v) {
+            float4 tp = make_float4(0.f, 0.f, 0.f, 0.f), tl = tp, tc = tp;
+            if (rv && okv[v]) {
+                if (ldP) tp = pw->data[slot][0][v][lane];
+                if (ldL) tl = pw->data[slot][1][v][lane];
+                if (doA) tc = pw->data[slot][2][v][lane];
+            }
+            pin[v * 4] = tp.x; pin[v * 4 + 1] = tp.y; pin[v * 4 + 2] = tp.z; pin[v * 4 + 3] = tp.w;
+            lin[v * 4] = tl.x; lin[v * 4 + 1] = tl.y; lin[v * 4 + 2] = tl.z; lin[v * 4 + 3] = tl.w;
+            cin[v * 4] = tc.x; cin[v * 4 + 1] = tc.y; cin[v * 4 + 2] = tc.z; cin[v * 4 + 3] = tc.w;
+        }
+        const int64_t rowoff = (mt.row0 + (rv ? j : 0)) * (int64_t)m;
+        float p2[NE], l2[NE];
+#pragma unroll
+        for (int x = 0; x < NE; ++x) {
             if (doB) {
                 const float pt = fmaf(pin[x], fast_exp2(lin[x] * beta), eps);
                 p2[x] = pt * coef[x];
@@ -504,66 +523,81 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep_pipe(Swe
             }
         }
         if (doA) {
-            float ex[4];
+            float ex[NE];
             float smax = -INFINITY;
 #pragma unroll
-            for (int x = 0; x < 4; ++x) {
+            for (int x = 0; x < NE; ++x) {
                 ex[x] = -(cin[x] + l2[x]) * beta;
-                if (okc) smax = fmaxf(smax, ex[x]);
+                if (okv[x / 4]) smax = fmaxf(smax, ex[x]);
             }
             smax = group_max<LPR>(smax);
             const float epss = fast_exp2(fminf(a.log2eps - smax, 126.f));
-            float t1[4];
+            float t1[NE];
             float rs = 0.f;
 #pragma unroll
-            for (int x = 0; x < 4; ++x) {
-                t1[x] = okc ? fmaf(p2[x], fast_exp2(ex[x] - smax), epss) : 0.f;
+            for (int x = 0; x < NE; ++x) {
+                t1[x] = okv[x / 4] ? fmaf(p2[x], fast_exp2(ex[x] - smax), epss) : 0.f;
                 rs += t1[x];
             }
             rs = group_sum<LPR>(rs);
             const float scale = rs > 0.f ? wkj / rs : 0.f;
-            float p1n[4];
+            float p1n[NE];
 #pragma unroll
-            for (int x = 0; x < 4; ++x) {
+            for (int x = 0; x < NE; ++x) {
                 p1n[x] = t1[x] * scale;
-                if (act) {
+                if (rv && okv[x / 4]) {
                     racc[x] += fmaf(p1n[x], fast_exp2(l2[x] * beta), eps);
                     objacc = fmaf(cin[x], p1n[x], objacc);
                 }
             }
-            if (act) {
-                VecIO<4>::st(a.plan + rowoff, p1n);
-                if (fl & SW_LAM_OUT) VecIO<4>::st(a.lam + rowoff, l2);
+            if (rv) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+                    if (okv[v]) {
+                        VecIO<4>::st(a.plan + rowoff + colv[v], p1n + v * 4);
+                        if (fl & SW_LAM_OUT) VecIO<4>::st(a.lam + rowoff + colv[v], l2 + v * 4);
+                    }
             }
-        } else if (act) {
-            VecIO<4>::st(a.plan + rowoff, p2);
-            if (fl & SW_LAM_OUT) VecIO<4>::st(a.lam + rowoff, l2);
+        } else if (rv) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                if (okv[v]) {
+                    VecIO<4>::st(a.plan + rowoff + colv[v], p2 + v * 4);
+                    if (fl & SW_LAM_OUT) VecIO<4>::st(a.lam + rowoff + colv[v], l2 + v * 4);
+                }
         }
         const bool last = mt.base + RPW >= mt.mk;
         __syncwarp();
-        // refill the slot consumed one step earlier: stage n + PIPE_S - 1
-        // goes to slot (n + PIPE_S - 1) mod PIPE_S
-        issue(slot == 0 ? PIPE_S - 1 : slot - 1);
-        slot = (slot + 1 == PIPE_S) ? 0 : slot + 1;
+        // refill the slot consumed one step earlier: stage n + S - 1 goes to
+        // slot (n + S - 1) mod S
+        issue(slot == 0 ? S - 1 : slot - 1);
+        slot = (slot + 1 == S) ? 0 : slot + 1;
 
         if (last && doA) {
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
+            for (int x = 0; x < NE; ++x)
 #pragma unroll
                 for (int o = LPR; o < 32; o <<= 1) racc[x] += __shfl_xor_sync(0xffffffffu, racc[x], o);
             float tl = 0.f;
-            if (okc) tl = (racc[0] + racc[1]) + (racc[2] + racc[3]);
+#pragma unroll
+            for (int x = 0; x < NE; ++x)
+                if (okv[x / 4]) tl += racc[x];
             tl = group_sum<LPR>(tl);
             const float inv_tl = 1.0f / tl;
-            if (sub == 0 && okc) {
-                *reinterpret_cast<float4*>(a.pos_r + p * m + col0) = make_float4(racc[0], racc[1], racc[2], racc[3]);
-                float q[4];
+            if (sub == 0) {
 #pragma unroll
-                for (int x = 0; x < 4; ++x) {
-                    const float wtl = racc[x] * inv_tl;
-                    q[x] = (fl & SW_R2) ? sqrtf(wtl) : wtl;
+                for (int v = 0; v < NV; ++v) {
+                    if (!okv[v]) continue;
+                    const float* rr = racc + v * 4;
+                    *reinterpret_cast<float4*>(a.pos_r + p * m + colv[v]) = make_float4(rr[0], rr[1], rr[2], rr[3]);
+                    float q[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float wtl = rr[e] * inv_tl;
+                        q[e] = (fl & SW_R2) ? sqrtf(wtl) : wtl;
+                    }
+                    *reinterpret_cast<float4*>(a.pos_part + p * m + colv[v]) = make_float4(q[0], q[1], q[2], q[3]);
                 }
-                *reinterpret_cast<float4*>(a.pos_part + p * m + col0) = make_float4(q[0], q[1], q[2], q[3]);
             }
             if (fl & SW_OBJ) {
                 double ov = group_sum_d<32>((double)objacc);
@@ -576,15 +610,36 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep_pipe(Swe
 
 typedef void (*SweepFn)(SweepArgs);
 
+#ifndef D2_PIPE_NV
+#define D2_PIPE_NV 1     // float4s per lane per row in the pipelined sweep (2: m % 8 == 0)
+#endif
+#ifndef D2_PIPE_S
+#define D2_PIPE_S 4      // ring stages per warp
+#endif
+
+template <int LPR, int NV>
+static SweepFn pipe_variant(size_t* smem) {
+    *smem = SWEEP_WARPS * sizeof(PipeWarp<LPR, NV, D2_PIPE_S>);
+    return k_sweep_pipe<LPR, NV, D2_PIPE_S>;
+}
+
 static SweepFn pick_sweep_pipe(int m, size_t* smem) {
-    if (m % 4 != 0 || m > 128) return nullptr;
-    if (m <= 4) { *smem = SWEEP_WARPS * sizeof(PipeWarp<1>); return k_sweep_pipe<1>; }
-    if (m <= 8) { *smem = SWEEP_WARPS * sizeof(PipeWarp<2>); return k_sweep_pipe<2>; }
-    if (m <= 16) { *smem = SWEEP_WARPS * sizeof(PipeWarp<4>); return k_sweep_pipe<4>; }
-    if (m <= 32) { *smem = SWEEP_WARPS * sizeof(PipeWarp<8>); return k_sweep_pipe<8>; }
-    if (m <= 64) { *smem = SWEEP_WARPS * sizeof(PipeWarp<16>); return k_sweep_pipe<16>; }
-    *smem = SWEEP_WARPS * sizeof(PipeWarp<32>);
-    return k_sweep_pipe<32>;
+    if (m % 4 != 0 || m > 256) return nullptr;
+    if (D2_PIPE_NV == 2 && m >= 8 && m % 8 == 0) {
+        if (m <= 8) return pipe_variant<1, 2>(smem);
+        if (m <= 16) return pipe_variant<2, 2>(smem);
+        if (m <= 32) return pipe_variant<4, 2>(smem);
+        if (m <= 64) return pipe_variant<8, 2>(smem);
+        if (m <= 128) return pipe_variant<16, 2>(smem);
+        return pipe_variant<32, 2>(smem);
+    }
+    if (m > 128) return nullptr;
+    if (m <= 4) return pipe_variant<1, 1>(smem);
+    if (m <= 8) return pipe_variant<2, 1>(smem);
+    if (m <= 16) return pipe_variant<4, 1>(smem);
+    if (m <= 32) return pipe_variant<8, 1>(smem);
+    if (m <= 64) return pipe_variant<16, 1>(smem);
+    return pipe_variant<32, 1>(smem);
 }
 
 static SweepFn pick_sweep(int m) {

@@ -189,16 +189,21 @@ __device__ __forceinline__ void cost_commit() { asm volatile("cp.async.commit_gr
 __device__ __forceinline__ void cost_wait1() { asm volatile("cp.async.wait_group 1;"); }
 __device__ __forceinline__ void cost_wait0() { asm volatile("cp.async.wait_group 0;"); }
 
+// Two rows per thread (rows t and t + CP_THREADS of each 256-row pass): every
+// broadcast load of the barycenter tile feeds 2 x 4 FMAs.
+#define CP_THREADS 128
+#define CP_ROWS 256
+
 template <int MT>
-__global__ void __launch_bounds__(COST_THREADS) k_cost_pipe(CostArgs a) {
+__global__ void __launch_bounds__(CP_THREADS) k_cost_pipe(CostArgs a) {
     extern __shared__ float4 dyn4[];
-    float* ys = reinterpret_cast<float*>(dyn4);                        // 2 x 256 x CP_STRIDE
-    float* xs = ys + 2 * COST_THREADS * CP_STRIDE;                      // d x MT
-    float* smu = xs + (size_t)a.d * MT;                                 // d
+    float* ys = reinterpret_cast<float*>(dyn4);                         // 2 x CP_ROWS x CP_STRIDE
+    float* xs = ys + 2 * CP_ROWS * CP_STRIDE;                            // d x MT
+    float* smu = xs + (size_t)a.d * MT;                                  // d
     __shared__ int64_t s_rs[D2_CHUNK];
     __shared__ int s_pre[D2_CHUNK + 1];
-    __shared__ int64_t s_row[COST_THREADS];
-    __shared__ double s_red[COST_THREADS / 32];
+    __shared__ int64_t s_row[CP_ROWS];
+    __shared__ double s_red[CP_THREADS / 32];
 
     const int64_t q = blockIdx.x;
     if (q >= *a.nchunks) return;
@@ -212,7 +217,7 @@ __global__ void __launch_bounds__(COST_THREADS) k_cost_pipe(CostArgs a) {
         s_rs[tid] = a.offsets[k];
         s_pre[tid + 1] = (int)(a.offsets[k + 1] - a.offsets[k]);
     }
-    for (int t = tid; t < d; t += COST_THREADS) smu[t] = a.mu[(int64_t)c * d + t];
+    for (int t = tid; t < d; t += CP_THREADS) smu[t] = a.mu[(int64_t)c * d + t];
     __syncthreads();
     if (tid == 0) {
         s_pre[0] = 0;
@@ -223,17 +228,18 @@ __global__ void __launch_bounds__(COST_THREADS) k_cost_pipe(CostArgs a) {
     const int ntile = (d + CP_DT - 1) / CP_DT;
     double rowsum_acc = 0.0;
 
-    // copy d-tile `t` of the rows in s_row into buffer b (rows beyond R skipped)
+    // copy d-tile `t` of the pass's rows into buffer b (a warp copies 4 rows
+    // of 128 B per instruction; rows beyond R are skipped)
     auto issue = [&](int t, int b) {
         const int d0 = t * CP_DT;
-        const int sub = lane >> 3, seg = lane & 7;      // 4 rows x 8 segments of 16 B
-        for (int r0 = warp * 4; r0 < COST_THREADS; r0 += 4 * (COST_THREADS / 32)) {
+        const int sub = lane >> 3, seg = lane & 7;
+        for (int r0 = warp * 4; r0 < CP_ROWS; r0 += 4 * (CP_THREADS / 32)) {
             const int r = r0 + sub;
             const int64_t g = s_row[r];
             const int col = d0 + seg * 4;
             if (g >= 0 && col < d) {
                 const float* src = d2_row_ptr(a.supp, a.vidx, a.vocab, d, g) + col;
-                cost_cp16(ys + ((size_t)b * COST_THREADS + r) * CP_STRIDE + seg * 4, src);
+                cost_cp16(ys + ((size_t)b * CP_ROWS + r) * CP_STRIDE + seg * 4, src);
             }
         }
         cost_commit();
@@ -241,14 +247,14 @@ __global__ void __launch_bounds__(COST_THREADS) k_cost_pipe(CostArgs a) {
 
     for (int ct = 0; ct < m; ct += MT) {
         __syncthreads();
-        for (int idx = tid; idx < d * MT; idx += COST_THREADS) {
+        for (int idx = tid; idx < d * MT; idx += CP_THREADS) {
             int dd = idx / MT, i = idx - dd * MT;
             xs[idx] = (ct + i < m) ? a.xt[((int64_t)c * m + ct + i) * d + dd] : 0.f;
         }
-        for (int rbase = 0; rbase < R; rbase += COST_THREADS) {
+        for (int rbase = 0; rbase < R; rbase += CP_ROWS) {
             __syncthreads();
-            {
-                const int lr = rbase + tid;
+            for (int rr = tid; rr < CP_ROWS; rr += CP_THREADS) {
+                const int lr = rbase + rr;
                 int64_t grow = -1;
                 if (lr < R) {
                     int lo = 0, hi = nm - 1;
@@ -258,14 +264,17 @@ __global__ void __launch_bounds__(COST_THREADS) k_cost_pipe(CostArgs a) {
                     }
                     grow = s_rs[lo] + (lr - s_pre[lo]);
                 }
-                s_row[tid] = grow;
+                s_row[rr] = grow;
             }
             __syncthreads();
-            const bool valid = rbase + tid < R;
-            float acc[MT];
+            const bool va = rbase + tid < R, vb = rbase + tid + CP_THREADS < R;
+            float acc_a[MT], acc_b[MT];
 #pragma unroll
-            for (int i = 0; i < MT; ++i) acc[i] = 0.f;
-            float yn = 0.f;
+            for (int i = 0; i < MT; ++i) {
+                acc_a[i] = 0.f;
+                acc_b[i] = 0.f;
+            }
+            float yna = 0.f, ynb = 0.f;
             issue(0, 0);
             for (int t = 0; t < ntile; ++t) {
                 if (t + 1 < ntile) {
@@ -275,47 +284,60 @@ __global__ void __launch_bounds__(COST_THREADS) k_cost_pipe(CostArgs a) {
                     cost_wait0();
                 }
                 __syncthreads();
-                if (valid) {
-                    const float* yr = ys + ((size_t)(t & 1) * COST_THREADS + tid) * CP_STRIDE;
+                if (va) {
+                    const float* yra = ys + ((size_t)(t & 1) * CP_ROWS + tid) * CP_STRIDE;
+                    const float* yrb = yra + (size_t)CP_THREADS * CP_STRIDE;
                     const int d0 = t * CP_DT;
                     const int dt = min(CP_DT, d - d0);
                     for (int dd = 0; dd < dt; dd += 4) {
-                        const float4 y4 = *reinterpret_cast<const float4*>(yr + dd);
-                        const float yv[4] = {y4.x - smu[d0 + dd], y4.y - smu[d0 + dd + 1], y4.z - smu[d0 + dd + 2],
-                                             y4.w - smu[d0 + dd + 3]};
+                        const float4 a4 = *reinterpret_cast<const float4*>(yra + dd);
+                        const float4 b4 = *reinterpret_cast<const float4*>(yrb + dd);
+                        const float4 m4 = *reinterpret_cast<const float4*>(smu + d0 + dd);
+                        const float ya[4] = {a4.x - m4.x, a4.y - m4.y, a4.z - m4.z, a4.w - m4.w};
+                        const float yb[4] = {b4.x - m4.x, b4.y - m4.y, b4.z - m4.z, b4.w - m4.w};
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
-                            yn = fmaf(yv[u], yv[u], yn);
+                            yna = fmaf(ya[u], ya[u], yna);
+                            ynb = fmaf(yb[u], yb[u], ynb);
                             const float* xr = xs + (size_t)(d0 + dd + u) * MT;
 #pragma unroll
                             for (int i = 0; i < MT; i += 4) {
                                 const float4 xv = *reinterpret_cast<const float4*>(xr + i);
-                                acc[i] = fmaf(xv.x, yv[u], acc[i]);
-                                acc[i + 1] = fmaf(xv.y, yv[u], acc[i + 1]);
-                                acc[i + 2] = fmaf(xv.z, yv[u], acc[i + 2]);
-                                acc[i + 3] = fmaf(xv.w, yv[u], acc[i + 3]);
+                                acc_a[i] = fmaf(xv.x, ya[u], acc_a[i]);
+                                acc_a[i + 1] = fmaf(xv.y, ya[u], acc_a[i + 1]);
+                                acc_a[i + 2] = fmaf(xv.z, ya[u], acc_a[i + 2]);
+                                acc_a[i + 3] = fmaf(xv.w, ya[u], acc_a[i + 3]);
+                                acc_b[i] = fmaf(xv.x, yb[u], acc_b[i]);
+                                acc_b[i + 1] = fmaf(xv.y, yb[u], acc_b[i + 1]);
+                                acc_b[i + 2] = fmaf(xv.z, yb[u], acc_b[i + 2]);
+                                acc_b[i + 3] = fmaf(xv.w, yb[u], acc_b[i + 3]);
                             }
                         }
                     }
                 }
                 __syncthreads();  // buffer t & 1 is refilled by the next issue
             }
-            if (valid) {
-                const int64_t g = s_row[tid];
+            const float* xnr = a.xn + (int64_t)c * m + ct;
+            const int nv = min(MT, m - ct);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const bool v = h == 0 ? va : vb;
+                if (!v) continue;
+                const float* acc = h == 0 ? acc_a : acc_b;
+                const float yn = h == 0 ? yna : ynb;
+                const int64_t g = s_row[tid + h * CP_THREADS];
                 float* out = a.C + g * m + ct;
-                const float* xnr = a.xn + (int64_t)c * m + ct;
-                const int nv = min(MT, m - ct);
                 float rs = 0.f;
 #pragma unroll
                 for (int i = 0; i < MT; i += 4) {
                     if (i < nv) {
-                        float4 v;
-                        v.x = fmaxf(fmaf(-2.f, acc[i], xnr[i] + yn), 0.f);
-                        v.y = fmaxf(fmaf(-2.f, acc[i + 1], xnr[i + 1] + yn), 0.f);
-                        v.z = fmaxf(fmaf(-2.f, acc[i + 2], xnr[i + 2] + yn), 0.f);
-                        v.w = fmaxf(fmaf(-2.f, acc[i + 3], xnr[i + 3] + yn), 0.f);
-                        __stcs(reinterpret_cast<float4*>(out + i), v);
-                        rs += (v.x + v.y) + (v.z + v.w);
+                        float4 o;
+                        o.x = fmaxf(fmaf(-2.f, acc[i], xnr[i] + yn), 0.f);
+                        o.y = fmaxf(fmaf(-2.f, acc[i + 1], xnr[i + 1] + yn), 0.f);
+                        o.z = fmaxf(fmaf(-2.f, acc[i + 2], xnr[i + 2] + yn), 0.f);
+                        o.w = fmaxf(fmaf(-2.f, acc[i + 3], xnr[i + 3] + yn), 0.f);
+                        __stcs(reinterpret_cast<float4*>(out + i), o);
+                        rs += (o.x + o.y) + (o.z + o.w);
                     }
                 }
                 rowsum_acc += (double)rs;
@@ -329,7 +351,7 @@ __global__ void __launch_bounds__(COST_THREADS) k_cost_pipe(CostArgs a) {
         __syncthreads();
         if (tid == 0) {
             double sum = 0.0;
-            for (int w = 0; w < COST_THREADS / 32; ++w) sum += s_red[w];
+            for (int w = 0; w < CP_THREADS / 32; ++w) sum += s_red[w];
             a.chunk_sum[q] = sum;
             a.chunk_rows[q] = R;
         }
@@ -338,11 +360,11 @@ __global__ void __launch_bounds__(COST_THREADS) k_cost_pipe(CostArgs a) {
 
 template <int MT>
 static int launch_cost_pipe(d2_ctx* ctx, const CostArgs& a, int64_t maxch, cudaStream_t st) {
-    size_t smem = ((size_t)2 * COST_THREADS * CP_STRIDE + (size_t)a.d * MT + a.d) * sizeof(float);
+    size_t smem = ((size_t)2 * CP_ROWS * CP_STRIDE + (size_t)a.d * MT + a.d) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_cost_pipe<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return d2_cuda_fail(ctx, e, "k_cost_pipe smem attribute");
     d2_time_begin(ctx, D2_KT_COST, st);
-    k_cost_pipe<MT><<<(unsigned)maxch, COST_THREADS, smem, st>>>(a);
+    k_cost_pipe<MT><<<(unsigned)maxch, CP_THREADS, smem, st>>>(a);
     d2_time_end(ctx, st);
     D2_LAUNCH_CK(ctx, "k_cost_pipe");
     return D2_OK;
@@ -368,8 +390,8 @@ int d2_cost_prepare(d2_ctx* ctx, const d2_bags* b, int m) {
     const int MT = m <= 8 ? 8 : m <= 16 ? 16 : m <= 32 ? 32 : 64;
     size_t smem;
     const void* fn;
-    if (aligned16 && ((size_t)2 * COST_THREADS * CP_STRIDE + (size_t)b->d * 64 + b->d) * 4 <= 200 * 1024) {
-        smem = ((size_t)2 * COST_THREADS * CP_STRIDE + (size_t)b->d * MT + b->d) * sizeof(float);
+    if (aligned16 && ((size_t)2 * CP_ROWS * CP_STRIDE + (size_t)b->d * 64 + b->d) * 4 <= 200 * 1024) {
+        smem = ((size_t)2 * CP_ROWS * CP_STRIDE + (size_t)b->d * MT + b->d) * sizeof(float);
         fn = MT == 8 ? (const void*)k_cost_pipe<8> : MT == 16 ? (const void*)k_cost_pipe<16>
            : MT == 32 ? (const void*)k_cost_pipe<32> : (const void*)k_cost_pipe<64>;
     } else {
@@ -414,7 +436,7 @@ int d2_cost_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t 
         return d2_fail(ctx, D2_ENOTSUP, "d2_cost: support dimension %d too large for the cost tile", b->d);
     const bool aligned16 = (b->d % 4 == 0) &&
         ((reinterpret_cast<uintptr_t>(b->supp ? b->supp : b->vocab) & 15) == 0) && (m % 4 == 0);
-    if (aligned16 && ((size_t)2 * COST_THREADS * CP_STRIDE + (size_t)b->d * 64 + b->d) * 4 <= 200 * 1024) {
+    if (aligned16 && ((size_t)2 * CP_ROWS * CP_STRIDE + (size_t)b->d * 64 + b->d) * 4 <= 200 * 1024) {
         if (m <= 8) return launch_cost_pipe<8>(ctx, a, maxch, st);
         if (m <= 16) return launch_cost_pipe<16>(ctx, a, maxch, st);
         if (m <= 32) return launch_cost_pipe<32>(ctx, a, maxch, st);
