@@ -56,6 +56,8 @@ extern "C" {
 #define D2_NO_GRAPH  0x8  /* launch kernels directly instead of replaying a CUDA graph    */
 #define D2_NO_PIPE   0x10 /* use the register-prefetch plan sweep instead of the
                              shared-memory pipelined one (both compute the same)  */
+#define D2_ELKAN     0x20 /* d2_cluster: skip assignment pairs by the triangle
+                             inequality of W (Section 5), when no pruner is given */
 
 typedef struct d2_ctx d2_ctx;
 
@@ -171,6 +173,10 @@ int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_of
                      float* x, float* w, float* plan, const uint8_t* warm_mask,
                      const d2_badmm_opts* opts, double* obj, void* stream);
 
+/* Exact W^2 solves (stats[0]) and pruner fall-backs (stats[1]) of the last
+ * d2_cluster call on this context (host, 2 int64). */
+int d2_cluster_stats(const d2_ctx* ctx, int64_t* stats);
+
 /* ---- learned candidate pruning (no counterpart in the paper) --------------
  * An MLP embedding f of a distribution (per-point d -> H -> H with ReLU,
  * weight-pooled, then H -> E), used to rank centroids by
@@ -274,8 +280,13 @@ int d2_merge_init(d2_ctx* ctx, const d2_bags* bags, const int64_t* ids, int64_t 
 /* D2-clustering (Algorithm 1 with the Section 5 choices), all on the device:
  * K distinct bags with m_k >= m chosen by a partial Fisher-Yates shuffle
  * driven by SplitMix64(seed) and reduced by Eq. (merge); then `rounds` rounds
- * of { d2_assign (with `prune` if non-NULL); badmm_barycenter over all K
- * clusters, warm-starting Pi^(k,2) of every bag whose label is unchanged }.
+ * of { d2_assign (with `prune` if non-NULL; else, with D2_ELKAN in
+ * opts->flags, Elkan's triangle-inequality skipping of Section 5 with the
+ * metric W = sqrt(W^2): lower bounds per (bag, centroid) carried across
+ * rounds and lowered by the centroid shifts, centroid-centroid distances,
+ * and an exact distance to each bag's current centroid every round);
+ * badmm_barycenter over all K clusters, warm-starting Pi^(k,2) of every bag
+ * whose label is unchanged }.
  *   x_out, w_out, labels_out : device, K x m x d, K x m, N
  *   obj_per_round : host, rounds doubles: (1/N) sum_k W^2(Q_{l_k}, P^(k)) at
  *                   each round's assignment

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libd2.so")
 D2_OK, D2_EINVAL, D2_ENOMEM, D2_ECUDA, D2_ETIMEOUT, D2_ENOTSUP, D2_ENOCONV, D2_ESCRATCH = 0, -1, -2, -3, -4, -5, -6, -7
 D2_NOALLOC_MAX_PAIRS = 1 << 20
 D2_RULE_R1, D2_RULE_R2 = 1, 2
-D2_FIX_X, D2_FIX_W, D2_VALIDATE, D2_NO_GRAPH, D2_NO_PIPE = 0x1, 0x2, 0x4, 0x8, 0x10
+D2_FIX_X, D2_FIX_W, D2_VALIDATE, D2_NO_GRAPH, D2_NO_PIPE, D2_ELKAN = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
 KT_NAMES = ("sweep_fused", "sweep_half", "cost", "support", "assign", "prune", "other")
 KT_COUNT = len(KT_NAMES)
 
@@ -53,6 +53,7 @@ _SIGS = {
     "d2_timing_enable": (c_int, [c_void_p, c_int]),
     "d2_timing_read": (c_int, [c_void_p, c_void_p, c_void_p]),
     "d2_launch_count": (c_int64, [c_void_p]),
+    "d2_cluster_stats": (c_int, [c_void_p, c_void_p]),
     "d2_cost": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32,
                         c_void_p, c_void_p, c_void_p]),
     "badmm_barycenter": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32,
@@ -166,6 +167,12 @@ class Context:
     def launch_count(self):
         return int(lib().d2_launch_count(self.h))
 
+    def cluster_stats(self):
+        """Exact W^2 solves and pruner fall-backs of the last d2_cluster call."""
+        st = (c_int64 * 2)()
+        self.check(lib().d2_cluster_stats(self.h, st))
+        return dict(exact_solves=st[0], fallbacks=st[1])
+
 
 class DeviceBags:
     """Device-resident bag set in the layout of d2_bags (see include/d2.h)."""
@@ -198,13 +205,13 @@ class DeviceBags:
 
 
 def badmm_opts(rho0=2.0, iters=100, tau=10, eps=1e-16, rule="R1", fix_x=False, fix_w=False,
-               validate=False, rho=0.0, graph=True):
+               validate=False, rho=0.0, graph=True, elkan=False):
     o = _Opts()
     lib().d2_badmm_opts_default(ctypes.byref(o))
     o.rho0, o.iters, o.tau, o.eps, o.rho = float(rho0), int(iters), int(tau), float(eps), float(rho)
     o.rule = D2_RULE_R2 if rule == "R2" else D2_RULE_R1
     o.flags = ((D2_FIX_X if fix_x else 0) | (D2_FIX_W if fix_w else 0) | (D2_VALIDATE if validate else 0)
-               | (0 if graph else D2_NO_GRAPH))
+               | (0 if graph else D2_NO_GRAPH) | (D2_ELKAN if elkan else 0))
     return o
 
 

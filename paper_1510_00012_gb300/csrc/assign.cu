@@ -513,3 +513,27 @@ cudaError_t d2_assign_exact_into(const d2_bags* b, int K, int m, const float* x,
     k_argmin_rows<<<(unsigned)d2_ceil_div(b->N, 256), 256, 0, st>>>(D, b->N, K, labels, dist);
     return cudaGetLastError();
 }
+
+// explicit pair list whose length is read on the device (<= max_pairs)
+int d2_solve_pair_list(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w,
+                       const int64_t* pair_bag, const int32_t* pair_cent, int64_t max_pairs,
+                       const int64_t* npairs_dev, float* out, int64_t* fail_count, cudaStream_t st) {
+    AssignArgs a = d2_assign_args(b, K, m, x, w, ctx->dev_flags, fail_count);
+    a.mode = 1;
+    a.npairs = max_pairs;
+    a.npairs_dev = npairs_dev;
+    a.pair_bag = pair_bag;
+    a.pair_cent = pair_cent;
+    a.out = out;
+    return d2_launch_pairs(ctx, a, max_pairs, st);
+}
+
+// all N x K pairs into out (N x K), no argmin
+int d2_launch_pairs_all(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w, float* out,
+                        int64_t* fail_count, cudaStream_t st) {
+    AssignArgs a = d2_assign_args(b, K, m, x, w, ctx->dev_flags, fail_count);
+    a.mode = 0;
+    a.npairs = b->N * (int64_t)K;
+    a.out = out;
+    return d2_launch_pairs(ctx, a, a.npairs, st);
+}

@@ -119,18 +119,19 @@ __global__ void __launch_bounds__(256) k_consensus(const int64_t* cofs, const fl
     const int t = threadIdx.x;
     const int i = t % m, g = t / m;
     if (g < G) {
-        // eight independent load/add chains, combined in a fixed order
-        double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        // blocks of 8 members are summed in FP32, the blocks in FP64 (FP64
+        // throughput is scarce on this part); eight loads are in flight
+        double acc = 0.0;
         int64_t p = p0 + g;
         for (; p + 7 * G < p1; p += 8 * G) {
             float v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) v[u] = __ldcg(pos_part + (p + u * G) * m + i);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) acc[u] += (double)v[u];
+            acc += (double)(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
         }
-        for (int u = 0; p < p1; p += G, ++u) acc[u] += (double)pos_part[p * m + i];
-        s_acc[g * m + i] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+        float tail = 0.f;
+        for (; p < p1; p += G) tail += pos_part[p * m + i];
+        s_acc[g * m + i] = acc + (double)tail;
     }
     __syncthreads();
     if (t < m) {
@@ -368,8 +369,12 @@ struct PipeWarp {
     PipeMeta cur;                 // issue cursor: member being issued, next row group
 };
 
+#ifndef D2_PIPE_MINB
+#define D2_PIPE_MINB 2    // the ring's shared memory allows 2 CTAs/SM at NV = 2
+#endif
+
 template <int LPR, int NV, int S>
-__global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep_pipe(SweepArgs a) {
+__global__ void __launch_bounds__(SWEEP_THREADS, D2_PIPE_MINB) k_sweep_pipe(SweepArgs a) {
     constexpr int RPW = 32 / LPR;
     constexpr int NE = 4 * NV;
     extern __shared__ float4 pipe_dyn[];
@@ -611,7 +616,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep_pipe(Swe
 typedef void (*SweepFn)(SweepArgs);
 
 #ifndef D2_PIPE_NV
-#define D2_PIPE_NV 1     // float4s per lane per row in the pipelined sweep (2: m % 8 == 0)
+#define D2_PIPE_NV 2     // float4s per lane per row in the pipelined sweep (2: m % 8 == 0)
 #endif
 #ifndef D2_PIPE_S
 #define D2_PIPE_S 4      // ring stages per warp

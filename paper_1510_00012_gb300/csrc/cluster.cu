@@ -15,6 +15,9 @@ int d2_assign_exact(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x,
 int d2_assign_pruned(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w,
                      const d2_prune* prune, int32_t* labels, float* dist, int64_t* counters,
                      cudaStream_t st);
+int d2_assign_elkan(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w,
+                    const float* x_prev, const float* w_prev, int32_t* labels, float* dist, int64_t* counters,
+                    cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Eq. (merge): one CTA per picked bag, FP64 like the definition
@@ -190,6 +193,11 @@ __global__ void k_stable_scatter(const int32_t* labels, int64_t N, int K, const 
     }
 }
 
+__global__ void k_acc_counts(int64_t* total, const int64_t* call) {
+    total[0] += call[0];
+    total[1] += call[1];
+}
+
 __global__ void k_warm_mask(const int32_t* labels, const int32_t* prev, int64_t N, uint8_t* mask) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k < N) mask[k] = (prev[k] >= 0 && prev[k] == labels[k]) ? 1 : 0;
@@ -288,7 +296,10 @@ extern "C" int d2_cluster(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m
     const size_t o_ids = o_cur + ((K * 8 + 255) & ~255ull);
     const size_t o_obj = o_ids + ((K * 8 + 255) & ~255ull);
     const size_t o_bobj = o_obj + 256;
-    const size_t o_plan = o_bobj + ((K * 8 + 255) & ~255ull);
+    const size_t o_xp = o_bobj + ((K * 8 + 255) & ~255ull);
+    const size_t o_wp = o_xp + (((size_t)K * m * bags->d * 4 + 255) & ~255ull);
+    const size_t o_cnt2 = o_wp + (((size_t)K * m * 4 + 255) & ~255ull);
+    const size_t o_plan = o_cnt2 + 256;
     const size_t total = o_plan + (size_t)n * m * 4;
     void* base = nullptr;
     if ((rc = d2_ws(ctx, WS_CLUSTER_LOOP, total, &base))) return rc;
@@ -305,6 +316,9 @@ extern "C" int d2_cluster(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m
     double* dobj = reinterpret_cast<double*>(b + o_obj);
     double* bobj = reinterpret_cast<double*>(b + o_bobj);
     float* plan = reinterpret_cast<float*>(b + o_plan);
+    float* x_prev = reinterpret_cast<float*>(b + o_xp);
+    float* w_prev = reinterpret_cast<float*>(b + o_wp);
+    int64_t* solves = reinterpret_cast<int64_t*>(b + o_cnt2);  // [0] exact solves, [1] fall-backs, [2] limit
 
     D2_CK(ctx, cudaMemcpyAsync(ids, elig.data(), K * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     if ((rc = d2_merge_init(ctx, bags, ids, K, m, x_out, w_out, stream))) return rc;
@@ -313,9 +327,24 @@ extern "C" int d2_cluster(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m
     d2_badmm_opts o;
     if (opts) o = *opts; else d2_badmm_opts_default(&o);
     o.flags &= ~D2_VALIDATE;
+    const bool elkan = (o.flags & D2_ELKAN) && !prune;
     const unsigned gN = (unsigned)d2_ceil_div(N, 256);
+    D2_CK(ctx, cudaMemsetAsync(solves, 0, 3 * sizeof(int64_t), st));
+    void* scnt = nullptr;
+    if ((rc = d2_ws(ctx, WS_SCAN, 64, &scnt))) return rc;
+    int64_t* acounters = static_cast<int64_t*>(scnt);
     for (int r = 0; r < rounds; ++r) {
-        if ((rc = d2_assign(ctx, bags, K, m, x_out, w_out, prune, lab, dist, nullptr, stream))) return rc;
+        if (elkan) {
+            if ((rc = d2_assign_elkan(ctx, bags, K, m, x_out, w_out, r == 0 ? nullptr : x_prev,
+                                      r == 0 ? nullptr : w_prev, lab, dist, solves, st)))
+                return rc;
+            D2_CK(ctx, cudaMemcpyAsync(x_prev, x_out, (size_t)K * m * bags->d * 4, cudaMemcpyDeviceToDevice, st));
+            D2_CK(ctx, cudaMemcpyAsync(w_prev, w_out, (size_t)K * m * 4, cudaMemcpyDeviceToDevice, st));
+        } else {
+            if ((rc = d2_assign(ctx, bags, K, m, x_out, w_out, prune, lab, dist, nullptr, stream))) return rc;
+            k_acc_counts<<<1, 1, 0, st>>>(solves, acounters);
+            D2_LAUNCH_CK(ctx, "k_acc_counts");
+        }
         k_mean_dist<<<1, 1024, 0, st>>>(dist, N, dobj);
         D2_LAUNCH_CK(ctx, "k_mean_dist");
         if (obj_per_round) {
@@ -335,6 +364,17 @@ extern "C" int d2_cluster(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m
         D2_CK(ctx, cudaMemcpyAsync(prev, lab, N * 4, cudaMemcpyDeviceToDevice, st));
     }
     D2_CK(ctx, cudaMemcpyAsync(labels_out, lab, N * 4, cudaMemcpyDeviceToDevice, st));
+    int64_t hs[3] = {0, 0, 0};
+    D2_CK(ctx, cudaMemcpyAsync(hs, solves, sizeof(hs), cudaMemcpyDeviceToHost, st));
     D2_CK(ctx, cudaStreamSynchronize(st));
+    ctx->cluster_solves = hs[0];
+    ctx->cluster_fallbacks = hs[1];
+    return D2_OK;
+}
+
+extern "C" int d2_cluster_stats(const d2_ctx* ctx, int64_t* stats) {
+    if (!ctx || !stats) return D2_EINVAL;
+    stats[0] = ctx->cluster_solves;
+    stats[1] = ctx->cluster_fallbacks;
     return D2_OK;
 }

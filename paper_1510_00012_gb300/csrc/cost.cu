@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_cost_pipe(CostArgs a) {
     float* smu = xs + (size_t)a.d * MT;                                  // d
     __shared__ int64_t s_rs[D2_CHUNK];
     __shared__ int s_pre[D2_CHUNK + 1];
-    __shared__ int64_t s_row[CP_ROWS];
+    __shared__ int64_t s_row[2][CP_ROWS];
     __shared__ double s_red[CP_THREADS / 32];
 
     const int64_t q = blockIdx.x;
@@ -226,16 +226,34 @@ __global__ void __launch_bounds__(CP_THREADS) k_cost_pipe(CostArgs a) {
     __syncthreads();
     const int R = s_pre[nm];
     const int ntile = (d + CP_DT - 1) / CP_DT;
+    const int npass = (R + CP_ROWS - 1) / CP_ROWS;
+    const int nsteps = npass * ntile;   // (pass, d-tile) steps of one column tile
     double rowsum_acc = 0.0;
 
-    // copy d-tile `t` of the pass's rows into buffer b (a warp copies 4 rows
-    // of 128 B per instruction; rows beyond R are skipped)
-    auto issue = [&](int t, int b) {
+    // global rows of pass `ps` into s_row[ps & 1]
+    auto rows_of = [&](int ps) {
+        for (int rr = tid; rr < CP_ROWS; rr += CP_THREADS) {
+            const int lr = ps * CP_ROWS + rr;
+            int64_t grow = -1;
+            if (lr < R) {
+                int lo = 0, hi = nm - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (s_pre[mid] <= lr) lo = mid; else hi = mid - 1;
+                }
+                grow = s_rs[lo] + (lr - s_pre[lo]);
+            }
+            s_row[ps & 1][rr] = grow;
+        }
+    };
+    // copy step `st` (pass st / ntile, d-tile st % ntile) into buffer st & 1
+    auto issue = [&](int st) {
+        const int ps = st / ntile, t = st - ps * ntile, b = st & 1;
         const int d0 = t * CP_DT;
         const int sub = lane >> 3, seg = lane & 7;
         for (int r0 = warp * 4; r0 < CP_ROWS; r0 += 4 * (CP_THREADS / 32)) {
             const int r = r0 + sub;
-            const int64_t g = s_row[r];
+            const int64_t g = s_row[ps & 1][r];
             const int col = d0 + seg * 4;
             if (g >= 0 && col < d) {
                 const float* src = d2_row_ptr(a.supp, a.vidx, a.vocab, d, g) + col;
@@ -251,97 +269,98 @@ __global__ void __launch_bounds__(CP_THREADS) k_cost_pipe(CostArgs a) {
             int dd = idx / MT, i = idx - dd * MT;
             xs[idx] = (ct + i < m) ? a.xt[((int64_t)c * m + ct + i) * d + dd] : 0.f;
         }
-        for (int rbase = 0; rbase < R; rbase += CP_ROWS) {
-            __syncthreads();
-            for (int rr = tid; rr < CP_ROWS; rr += CP_THREADS) {
-                const int lr = rbase + rr;
-                int64_t grow = -1;
-                if (lr < R) {
-                    int lo = 0, hi = nm - 1;
-                    while (lo < hi) {
-                        int mid = (lo + hi + 1) >> 1;
-                        if (s_pre[mid] <= lr) lo = mid; else hi = mid - 1;
-                    }
-                    grow = s_rs[lo] + (lr - s_pre[lo]);
+        rows_of(0);
+        __syncthreads();
+        issue(0);
+        float acc_a[MT], acc_b[MT];
+        float yna = 0.f, ynb = 0.f;
+#pragma unroll
+        for (int i = 0; i < MT; ++i) {
+            acc_a[i] = 0.f;
+            acc_b[i] = 0.f;
+        }
+        for (int stp = 0; stp < nsteps; ++stp) {
+            const int ps = stp / ntile, t = stp - ps * ntile;
+            if (stp + 1 < nsteps) {
+                if (t == ntile - 1) {  // next step starts a new pass: its rows first
+                    rows_of(ps + 1);
+                    __syncthreads();
                 }
-                s_row[rr] = grow;
+                issue(stp + 1);
+                cost_wait1();
+            } else {
+                cost_wait0();
             }
             __syncthreads();
+            const int rbase = ps * CP_ROWS;
             const bool va = rbase + tid < R, vb = rbase + tid + CP_THREADS < R;
-            float acc_a[MT], acc_b[MT];
+            if (va) {
+                const float* yra = ys + ((size_t)(stp & 1) * CP_ROWS + tid) * CP_STRIDE;
+                const float* yrb = yra + (size_t)CP_THREADS * CP_STRIDE;
+                const int d0 = t * CP_DT;
+                const int dt = min(CP_DT, d - d0);
+                for (int dd = 0; dd < dt; dd += 4) {
+                    const float4 a4 = *reinterpret_cast<const float4*>(yra + dd);
+                    const float4 b4 = *reinterpret_cast<const float4*>(yrb + dd);
+                    const float4 m4 = *reinterpret_cast<const float4*>(smu + d0 + dd);
+                    const float ya[4] = {a4.x - m4.x, a4.y - m4.y, a4.z - m4.z, a4.w - m4.w};
+                    const float yb[4] = {b4.x - m4.x, b4.y - m4.y, b4.z - m4.z, b4.w - m4.w};
 #pragma unroll
-            for (int i = 0; i < MT; ++i) {
-                acc_a[i] = 0.f;
-                acc_b[i] = 0.f;
-            }
-            float yna = 0.f, ynb = 0.f;
-            issue(0, 0);
-            for (int t = 0; t < ntile; ++t) {
-                if (t + 1 < ntile) {
-                    issue(t + 1, (t + 1) & 1);
-                    cost_wait1();
-                } else {
-                    cost_wait0();
-                }
-                __syncthreads();
-                if (va) {
-                    const float* yra = ys + ((size_t)(t & 1) * CP_ROWS + tid) * CP_STRIDE;
-                    const float* yrb = yra + (size_t)CP_THREADS * CP_STRIDE;
-                    const int d0 = t * CP_DT;
-                    const int dt = min(CP_DT, d - d0);
-                    for (int dd = 0; dd < dt; dd += 4) {
-                        const float4 a4 = *reinterpret_cast<const float4*>(yra + dd);
-                        const float4 b4 = *reinterpret_cast<const float4*>(yrb + dd);
-                        const float4 m4 = *reinterpret_cast<const float4*>(smu + d0 + dd);
-                        const float ya[4] = {a4.x - m4.x, a4.y - m4.y, a4.z - m4.z, a4.w - m4.w};
-                        const float yb[4] = {b4.x - m4.x, b4.y - m4.y, b4.z - m4.z, b4.w - m4.w};
+                    for (int u = 0; u < 4; ++u) {
+                        yna = fmaf(ya[u], ya[u], yna);
+                        ynb = fmaf(yb[u], yb[u], ynb);
+                        const float* xr = xs + (size_t)(d0 + dd + u) * MT;
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            yna = fmaf(ya[u], ya[u], yna);
-                            ynb = fmaf(yb[u], yb[u], ynb);
-                            const float* xr = xs + (size_t)(d0 + dd + u) * MT;
-#pragma unroll
-                            for (int i = 0; i < MT; i += 4) {
-                                const float4 xv = *reinterpret_cast<const float4*>(xr + i);
-                                acc_a[i] = fmaf(xv.x, ya[u], acc_a[i]);
-                                acc_a[i + 1] = fmaf(xv.y, ya[u], acc_a[i + 1]);
-                                acc_a[i + 2] = fmaf(xv.z, ya[u], acc_a[i + 2]);
-                                acc_a[i + 3] = fmaf(xv.w, ya[u], acc_a[i + 3]);
-                                acc_b[i] = fmaf(xv.x, yb[u], acc_b[i]);
-                                acc_b[i + 1] = fmaf(xv.y, yb[u], acc_b[i + 1]);
-                                acc_b[i + 2] = fmaf(xv.z, yb[u], acc_b[i + 2]);
-                                acc_b[i + 3] = fmaf(xv.w, yb[u], acc_b[i + 3]);
-                            }
+                        for (int i = 0; i < MT; i += 4) {
+                            const float4 xv = *reinterpret_cast<const float4*>(xr + i);
+                            acc_a[i] = fmaf(xv.x, ya[u], acc_a[i]);
+                            acc_a[i + 1] = fmaf(xv.y, ya[u], acc_a[i + 1]);
+                            acc_a[i + 2] = fmaf(xv.z, ya[u], acc_a[i + 2]);
+                            acc_a[i + 3] = fmaf(xv.w, ya[u], acc_a[i + 3]);
+                            acc_b[i] = fmaf(xv.x, yb[u], acc_b[i]);
+                            acc_b[i + 1] = fmaf(xv.y, yb[u], acc_b[i + 1]);
+                            acc_b[i + 2] = fmaf(xv.z, yb[u], acc_b[i + 2]);
+                            acc_b[i + 3] = fmaf(xv.w, yb[u], acc_b[i + 3]);
                         }
                     }
                 }
-                __syncthreads();  // buffer t & 1 is refilled by the next issue
             }
-            const float* xnr = a.xn + (int64_t)c * m + ct;
-            const int nv = min(MT, m - ct);
+            if (t == ntile - 1) {  // the pass is complete: emit its rows
+                const float* xnr = a.xn + (int64_t)c * m + ct;
+                const int nv = min(MT, m - ct);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const bool v = h == 0 ? va : vb;
-                if (!v) continue;
-                const float* acc = h == 0 ? acc_a : acc_b;
-                const float yn = h == 0 ? yna : ynb;
-                const int64_t g = s_row[tid + h * CP_THREADS];
-                float* out = a.C + g * m + ct;
-                float rs = 0.f;
+                for (int h = 0; h < 2; ++h) {
+                    const bool v = h == 0 ? va : vb;
+                    if (v) {
+                        const float* acc = h == 0 ? acc_a : acc_b;
+                        const float yn = h == 0 ? yna : ynb;
+                        const int64_t g = s_row[ps & 1][tid + h * CP_THREADS];
+                        float* out = a.C + g * m + ct;
+                        float rs = 0.f;
 #pragma unroll
-                for (int i = 0; i < MT; i += 4) {
-                    if (i < nv) {
-                        float4 o;
-                        o.x = fmaxf(fmaf(-2.f, acc[i], xnr[i] + yn), 0.f);
-                        o.y = fmaxf(fmaf(-2.f, acc[i + 1], xnr[i + 1] + yn), 0.f);
-                        o.z = fmaxf(fmaf(-2.f, acc[i + 2], xnr[i + 2] + yn), 0.f);
-                        o.w = fmaxf(fmaf(-2.f, acc[i + 3], xnr[i + 3] + yn), 0.f);
-                        __stcs(reinterpret_cast<float4*>(out + i), o);
-                        rs += (o.x + o.y) + (o.z + o.w);
+                        for (int i = 0; i < MT; i += 4) {
+                            if (i < nv) {
+                                float4 o;
+                                o.x = fmaxf(fmaf(-2.f, acc[i], xnr[i] + yn), 0.f);
+                                o.y = fmaxf(fmaf(-2.f, acc[i + 1], xnr[i + 1] + yn), 0.f);
+                                o.z = fmaxf(fmaf(-2.f, acc[i + 2], xnr[i + 2] + yn), 0.f);
+                                o.w = fmaxf(fmaf(-2.f, acc[i + 3], xnr[i + 3] + yn), 0.f);
+                                __stcs(reinterpret_cast<float4*>(out + i), o);
+                                rs += (o.x + o.y) + (o.z + o.w);
+                            }
+                        }
+                        rowsum_acc += (double)rs;
                     }
                 }
-                rowsum_acc += (double)rs;
+#pragma unroll
+                for (int i = 0; i < MT; ++i) {
+                    acc_a[i] = 0.f;
+                    acc_b[i] = 0.f;
+                }
+                yna = 0.f;
+                ynb = 0.f;
             }
+            __syncthreads();  // buffer stp & 1 is refilled two steps later
         }
     }
     if (a.chunk_sum) {

@@ -29,6 +29,7 @@ enum WsSlot {
     WS_ASSIGN,       // assignment scratch
     WS_CLUSTER_LOOP, // d2_cluster state (labels, plan cache, ...)
     WS_PRUNE,        // pruning scratch
+    WS_ELKAN,        // triangle-inequality bounds carried across rounds
     WS_NSLOTS
 };
 
@@ -54,6 +55,8 @@ struct d2_ctx {
     std::vector<uint64_t> graph_key;
     cudaGraphExec_t graph_exec = nullptr;
     int64_t graph_launches = 0;
+    // exact W^2 solves and pruner fall-backs of the last d2_cluster call
+    int64_t cluster_solves = 0, cluster_fallbacks = 0;
 };
 
 // Event bracket around one launch when timing is on (no-ops otherwise).

@@ -126,3 +126,20 @@ def test_d2_cluster_m1_is_kmeans_on_means(d2, ctx):
     np.testing.assert_array_equal(labels.cpu().numpy(), labels_ref[-1])
     np.testing.assert_allclose(x.cpu().double().numpy()[:, 0, :], cent, atol=1e-4)
     assert np.allclose(w.cpu().numpy(), 1.0)
+
+
+def test_elkan_skipping_matches_exact_clustering(d2, ctx):
+    """Triangle-inequality skipping (Section 5) changes which pairs are solved,
+    never the labels or the per-round objective."""
+    bags = synth.gaussian_class_bags(41, 400, 4, 6, mk=(4, 16), mu_sigma=3.0, alpha=1.0)
+    db = d2.DeviceBags.from_synth(bags)
+    K, m, rounds = 6, 5, 5
+    x1, w1, l1, o1 = d2.d2_cluster(ctx, db, K, m, seed=3, rounds=rounds, opts=d2.badmm_opts(iters=30))
+    full = ctx.cluster_stats()
+    x2, w2, l2, o2 = d2.d2_cluster(ctx, db, K, m, seed=3, rounds=rounds, opts=d2.badmm_opts(iters=30, elkan=True))
+    skip = ctx.cluster_stats()
+    np.testing.assert_array_equal(l1.cpu().numpy(), l2.cpu().numpy())
+    np.testing.assert_allclose(o2, o1, rtol=1e-6)
+    assert torch.equal(x1, x2) and torch.equal(w1, w2)
+    assert full["exact_solves"] == bags.N * K * rounds
+    assert skip["exact_solves"] < full["exact_solves"]
