@@ -412,6 +412,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-d2", action="store_true", help="skip the D2-clustering s/round comparison")
     ap.add_argument("--pruning", action="store_true", help="also run the learned-pruning assignment at scale")
+    ap.add_argument("--cost", default="bf16x3", choices=["fp32", "bf16", "bf16x3", "bf16x6"],
+                    help="cost-build precision (bf16*: tensor cores)")
+    ap.add_argument("--no-cost-variants", action="store_true",
+                    help="skip the timing of the other cost-build precisions")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -443,7 +447,7 @@ def main():
     w = w0.clone()
     plan = torch.empty(bags.n, m, dtype=torch.float32, device=dev)
     obj = torch.empty(K, dtype=torch.float64, device=dev)
-    opts = d2.badmm_opts(iters=T, tau=W["tau"])
+    opts = d2.badmm_opts(iters=T, tau=W["tau"], cost=args.cost)
     ctx = d2.Context(local)
 
     def step():
@@ -497,6 +501,45 @@ def main():
                 "share_of_step": f_ms / max(ms_total, 1e-9)}
     breakdown = {k: {"ms": v[0] / args.steps, "launches": v[1] // max(args.steps, 1)} for k, v in kt.items()
                  if v[1]}
+    # the cost build (tensor cores for d >= 32): HBM roofline of its launches
+    c_ms, c_n = kt["cost"]
+    cost_roof = None
+    if c_n:
+        cbytes = bags.n * 4 * (W["d"] + m)  # read the support rows, write the cost rows (FP32)
+        c_ach = cbytes / (c_ms / c_n * 1e-3) / 1e9
+        cost_roof = {"bound": "hbm", "kernel": "k_cost_tc<%d>" % {"bf16": 1, "bf16x3": 2, "bf16x6": 3}[args.cost]
+                     if args.cost != "fp32" else "k_cost_pipe<32>", "precision": args.cost,
+                     "achieved": c_ach, "peak": peak, "unit": "GB/s", "frac": c_ach / peak,
+                     "algorithmic_bytes_per_launch": cbytes, "avg_launch_ms": c_ms / c_n}
+
+    # the same step with the other cost-build precisions (fewer steps)
+    variants = None
+    if not args.no_cost_variants:
+        variants = {}
+        for prec in ("fp32", "bf16", "bf16x3", "bf16x6"):
+            if prec == args.cost:
+                continue
+            vopts = d2.badmm_opts(iters=T, tau=W["tau"], cost=prec)
+            for _ in range(1):
+                x.copy_(x0)
+                w.copy_(w0)
+                d2.badmm_barycenter(ctx, db, co, mem, x, w, plan, None, vopts, obj)
+            ctx.timing(True)
+            torch.cuda.synchronize()
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            for _ in range(2):
+                x.copy_(x0)
+                w.copy_(w0)
+                d2.badmm_barycenter(ctx, db, co, mem, x, w, plan, None, vopts, obj)
+            v1.record(stream)
+            torch.cuda.synchronize()
+            vkt = ctx.timing_read()
+            ctx.timing(False)
+            vms = max_over_ranks(v0.elapsed_time(v1), dist, dev) / 2
+            variants[prec] = {"value": job_rate(entries, T, world, vms), "ms_per_step": vms,
+                              "cost_ms_per_launch": vkt["cost"][0] / max(vkt["cost"][1], 1)}
+        ctx.device_errors()
 
     # end to end through the public API from pinned host buffers
     e2e = None
@@ -516,8 +559,10 @@ def main():
         if dist:
             dist.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.e2e_steps):
+        for it in range(1 + args.e2e_steps):  # one untimed step first (graph capture on new buffers)
+            if it == 1:
+                torch.cuda.synchronize()
+                e0.record(stream)
             d_off.copy_(h["offsets"], non_blocking=True)
             d_wt.copy_(h["wt"], non_blocking=True)
             d_supp.copy_(h["supp"], non_blocking=True)
@@ -562,10 +607,11 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": W["desc"], "clusters": K, "distributions_per_gpu": int(mem.numel()),
                            "support_rows_per_gpu": int(entries // m), "plan_entries_per_gpu": int(entries),
-                           "iters": T, "l2": "inputs larger than L2 (Pi, Lambda, C: %.1f GB per GPU)"
+                           "iters": T, "cost_precision": args.cost, "l2": "inputs larger than L2 (Pi, Lambda, C: %.1f GB per GPU)"
                            % (12 * entries / 1e9),
                            "parallelism": "independent problem per GPU" if world > 1 else "single GPU"},
-                "roofline": roof, "kernel_breakdown_ms_per_step": breakdown, "cpu_baseline": cpu,
+                "roofline": roof, "cost_roofline": cost_roof, "cost_variants": variants,
+                "kernel_breakdown_ms_per_step": breakdown, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "d2_round": d2cmp}
         if prune_res is not None:
             line["pruning"] = prune_res

@@ -58,6 +58,19 @@ extern "C" {
                              shared-memory pipelined one (both compute the same)  */
 #define D2_ELKAN     0x20 /* d2_cluster: skip assignment pairs by the triangle
                              inequality of W (Section 5), when no pruner is given */
+/* Precision of the cost build c(x_i, y_j) = ||x_i - y_j||^2 (Section 2).  Default
+ * (neither flag): FP32 on CUDA cores.  With one of these flags, and when the
+ * support dimension makes the build a dense contraction (d >= 32, d % 4 == 0,
+ * m % 4 == 0, a 16-byte-aligned support or vocabulary table), the cross term
+ * <x_i, y_j> runs on the tensor cores (tcgen05) with an FP32 accumulator, and
+ * the norms ||x_i||^2, ||y_j||^2 stay FP32 (all on coordinates centred at the
+ * mean of the cluster's barycenter points).  Outside those conditions the
+ * FP32 build is used.                                                      */
+#define D2_COST_BF16   0x40 /* BF16 operands: about 8 mantissa bits per factor   */
+#define D2_COST_BF16X3 0x80 /* each factor split hi + lo (BF16), three products:
+                               about 16 mantissa bits                           */
+#define D2_COST_BF16X6 0xC0 /* each factor split hi + mid + lo (BF16, exact for
+                               FP32 inputs), six products: FP32-level error     */
 
 typedef struct d2_ctx d2_ctx;
 
@@ -85,7 +98,8 @@ typedef struct {
     int32_t iters;     /* T, B-ADMM iterations per call, default 100 (Section 3.3)      */
     int32_t tau;       /* support update every tau iterations, default 10               */
     int32_t rule;      /* D2_RULE_R1 (default) or D2_RULE_R2                            */
-    int32_t flags;     /* D2_FIX_X | D2_FIX_W | D2_VALIDATE | D2_NO_GRAPH | D2_NO_PIPE  */
+    int32_t flags;     /* D2_FIX_X | D2_FIX_W | D2_VALIDATE | D2_NO_GRAPH | D2_NO_PIPE |
+                          D2_ELKAN | one of D2_COST_BF16, _BF16X3, _BF16X6             */
 } d2_badmm_opts;
 
 /* Fill `o` with the defaults above. */
@@ -126,6 +140,14 @@ int d2_timing_read(d2_ctx* ctx, double* ms, int64_t* launches);
 /* Number of kernels this context has launched since it was created. */
 int64_t d2_launch_count(const d2_ctx* ctx);
 
+/* Sticky device-side error bits raised by this context's kernels since the
+ * last call (synchronous; the bits are cleared).  Kernels never trap: a
+ * bounded wait on the device that expires (about 2 s; the tensor-core cost
+ * build waits on its MMAs) sets bit 0x40 and the kernel returns early.
+ * Returns D2_ETIMEOUT when that bit was set, else D2_OK; *bits (host,
+ * optional) receives the raw bits. */
+int d2_device_errors(d2_ctx* ctx, int32_t* bits);
+
 /* Validate a bag set on the device (synchronous): offsets non-decreasing with
  * offsets[N] == n and every m_k in [1, max_mk]; weights finite, >= 0 and each
  * bag's sum within 1e-5 of 1 (Section 2: w in the simplex); vocabulary indices
@@ -142,10 +164,13 @@ int d2_check_bags(d2_ctx* ctx, const d2_bags* bags, void* stream);
  *   x               : device, K x m x d, barycenter supports (row-major)
  *   C_out           : device, n x m; the j-major rows of every listed member
  *                     are written, other rows are left untouched
- * Requires 1 <= m <= 256.  FP32 arithmetic on centred coordinates. */
+ *   flags           : 0 (FP32) or D2_COST_BF16 / _BF16X3 / _BF16X6 (tensor
+ *                     cores, see those flags)
+ * Requires 1 <= m <= 256.  Arithmetic on coordinates centred at the mean of
+ * each cluster's barycenter points; entries are clamped at 0. */
 int d2_cost(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_offsets,
             const int64_t* members, int64_t P, int32_t K, int32_t m,
-            const float* x, float* C_out, void* stream);
+            const float* x, float* C_out, int32_t flags, void* stream);
 
 /* Centroid update with B-ADMM (Algorithm badmm, Section 3.3) for K clusters
  * at once, every cluster advancing through the same T iterations:

@@ -22,6 +22,8 @@ D2_OK, D2_EINVAL, D2_ENOMEM, D2_ECUDA, D2_ETIMEOUT, D2_ENOTSUP, D2_ENOCONV, D2_E
 D2_NOALLOC_MAX_PAIRS = 1 << 20
 D2_RULE_R1, D2_RULE_R2 = 1, 2
 D2_FIX_X, D2_FIX_W, D2_VALIDATE, D2_NO_GRAPH, D2_NO_PIPE, D2_ELKAN = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
+D2_COST_BF16, D2_COST_BF16X3, D2_COST_BF16X6 = 0x40, 0x80, 0xC0
+COST_PRECISION = {"fp32": 0, "bf16": D2_COST_BF16, "bf16x3": D2_COST_BF16X3, "bf16x6": D2_COST_BF16X6}
 KT_NAMES = ("sweep_fused", "sweep_half", "cost", "support", "assign", "prune", "other")
 KT_COUNT = len(KT_NAMES)
 
@@ -53,9 +55,10 @@ _SIGS = {
     "d2_timing_enable": (c_int, [c_void_p, c_int]),
     "d2_timing_read": (c_int, [c_void_p, c_void_p, c_void_p]),
     "d2_launch_count": (c_int64, [c_void_p]),
+    "d2_device_errors": (c_int, [c_void_p, c_void_p]),
     "d2_cluster_stats": (c_int, [c_void_p, c_void_p]),
     "d2_cost": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32,
-                        c_void_p, c_void_p, c_void_p]),
+                        c_void_p, c_void_p, c_int32, c_void_p]),
     "badmm_barycenter": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32,
                                  c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "d2_assign": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
@@ -167,6 +170,13 @@ class Context:
     def launch_count(self):
         return int(lib().d2_launch_count(self.h))
 
+    def device_errors(self):
+        """Sticky device-side error bits since the last call (cleared); raises
+        D2Error(D2_ETIMEOUT) if a bounded device wait expired."""
+        bits = c_int32(0)
+        self.check(lib().d2_device_errors(self.h, ctypes.byref(bits)))
+        return int(bits.value)
+
     def cluster_stats(self):
         """Exact W^2 solves and pruner fall-backs of the last d2_cluster call."""
         st = (c_int64 * 2)()
@@ -204,14 +214,21 @@ class DeviceBags:
         return ctypes.byref(self.c)
 
 
+def _cost_flag(precision):
+    if precision not in COST_PRECISION:
+        raise ValueError("cost precision must be one of %s" % sorted(COST_PRECISION))
+    return COST_PRECISION[precision]
+
+
 def badmm_opts(rho0=2.0, iters=100, tau=10, eps=1e-16, rule="R1", fix_x=False, fix_w=False,
-               validate=False, rho=0.0, graph=True, elkan=False):
+               validate=False, rho=0.0, graph=True, elkan=False, cost="fp32"):
+    """d2_badmm_opts; cost = "fp32" | "bf16" | "bf16x3" | "bf16x6" selects the cost build."""
     o = _Opts()
     lib().d2_badmm_opts_default(ctypes.byref(o))
     o.rho0, o.iters, o.tau, o.eps, o.rho = float(rho0), int(iters), int(tau), float(eps), float(rho)
     o.rule = D2_RULE_R2 if rule == "R2" else D2_RULE_R1
     o.flags = ((D2_FIX_X if fix_x else 0) | (D2_FIX_W if fix_w else 0) | (D2_VALIDATE if validate else 0)
-               | (0 if graph else D2_NO_GRAPH) | (D2_ELKAN if elkan else 0))
+               | (0 if graph else D2_NO_GRAPH) | (D2_ELKAN if elkan else 0) | _cost_flag(cost))
     return o
 
 
@@ -219,8 +236,9 @@ def d2_check_bags(ctx, bags):
     return ctx.check(lib().d2_check_bags(ctx.h, bags.ref(), _stream()))
 
 
-def d2_cost(ctx, bags, cluster_offsets, members, x, C_out=None):
-    """C (n x m, j-major rows) between each cluster's support x[c] and its members."""
+def d2_cost(ctx, bags, cluster_offsets, members, x, C_out=None, precision="fp32"):
+    """C (n x m, j-major rows) between each cluster's support x[c] and its members;
+    precision = "fp32" | "bf16" | "bf16x3" | "bf16x6" (tensor cores where d >= 32)."""
     _need(cluster_offsets, torch.int64, "cluster_offsets")
     _need(members, torch.int64, "members")
     _need(x, torch.float32, "x")
@@ -229,7 +247,7 @@ def d2_cost(ctx, bags, cluster_offsets, members, x, C_out=None):
         C_out = torch.zeros(bags.n, m, dtype=torch.float32, device=x.device)
     _need(C_out, torch.float32, "C_out")
     ctx.check(lib().d2_cost(ctx.h, bags.ref(), _ptr(cluster_offsets), _ptr(members), members.numel(),
-                            K, m, _ptr(x), _ptr(C_out), _stream()))
+                            K, m, _ptr(x), _ptr(C_out), _cost_flag(precision), _stream()))
     return C_out
 
 

@@ -141,6 +141,19 @@ extern "C" int d2_timing_read(d2_ctx* ctx, double* ms, int64_t* launches) {
 
 extern "C" int64_t d2_launch_count(const d2_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+extern "C" int d2_device_errors(d2_ctx* ctx, int32_t* bits) {
+    if (!ctx) return D2_EINVAL;
+    D2_CK(ctx, cudaSetDevice(ctx->device));
+    int v = 0;
+    int* word = ctx->dev_flags + D2_DEV_ERR_WORD;
+    D2_CK(ctx, cudaDeviceSynchronize());
+    D2_CK(ctx, cudaMemcpy(&v, word, sizeof(int), cudaMemcpyDeviceToHost));
+    D2_CK(ctx, cudaMemset(word, 0, sizeof(int)));
+    if (bits) *bits = v;
+    if (v & D2F_DEV_TIMEOUT) return d2_fail(ctx, D2_ETIMEOUT, "a bounded device-side wait expired");
+    return D2_OK;
+}
+
 int d2_ws(d2_ctx* ctx, int slot, size_t bytes, void** out) {
     if (bytes == 0) bytes = 256;
     if (ctx->ws_bytes[slot] < bytes) {

@@ -403,7 +403,12 @@ static int launch_cost(d2_ctx* ctx, const CostArgs& a, int64_t maxch, cudaStream
     return D2_OK;
 }
 
-int d2_cost_prepare(d2_ctx* ctx, const d2_bags* b, int m) {
+int d2_cost_prepare(d2_ctx* ctx, const d2_bags* b, int m, int prec) {
+    if (prec) {
+        bool used = false;
+        int rc = d2_cost_tc_prepare(ctx, b, m, prec, &used);
+        if (rc || used) return rc;
+    }
     const bool aligned16 = (b->d % 4 == 0) &&
         ((reinterpret_cast<uintptr_t>(b->supp ? b->supp : b->vocab) & 15) == 0) && (m % 4 == 0);
     const int MT = m <= 8 ? 8 : m <= 16 ? 16 : m <= 32 ? 32 : 64;
@@ -426,7 +431,7 @@ int d2_cost_prepare(d2_ctx* ctx, const d2_bags* b, int m) {
 }
 
 int d2_cost_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t P, int K, int m,
-                 const ClusterWs& cw, float* C, bool want_sums, cudaStream_t st) {
+                 const ClusterWs& cw, float* C, bool want_sums, int prec, cudaStream_t st) {
     int64_t maxch = d2_ceil_div(P, D2_CHUNK) + K + 1;
     CostArgs a;
     a.members = members;
@@ -451,6 +456,11 @@ int d2_cost_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t 
         a.chunk_sum = static_cast<double*>(p);
         a.chunk_rows = reinterpret_cast<int64_t*>(static_cast<char*>(p) + (size_t)maxch * 8);
     }
+    if (prec) {  // tensor cores where (d, m) make the build a dense contraction
+        bool used = false;
+        int rc = d2_cost_tc_rows(ctx, b, members, maxch, m, prec, cw, C, a.chunk_sum, a.chunk_rows, st, &used);
+        if (rc || used) return rc;
+    }
     if ((size_t)b->d * 64 * 4 + COST_DT * COST_YPAD * 4 > 200 * 1024)
         return d2_fail(ctx, D2_ENOTSUP, "d2_cost: support dimension %d too large for the cost tile", b->d);
     const bool aligned16 = (b->d % 4 == 0) &&
@@ -469,7 +479,7 @@ int d2_cost_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t 
 
 extern "C" int d2_cost(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_offsets,
                        const int64_t* members, int64_t P, int32_t K, int32_t m, const float* x,
-                       float* C_out, void* stream) {
+                       float* C_out, int32_t flags, void* stream) {
     if (!ctx) return D2_EINVAL;
     int rc = d2_check_bags_host(ctx, bags);
     if (rc) return rc;
@@ -486,5 +496,7 @@ extern "C" int d2_cost(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_
     if (rc) return rc;
     rc = d2_prep_x(ctx, x, K, m, bags->d, cw, st);
     if (rc) return rc;
-    return d2_cost_rows(ctx, bags, members, P, K, m, cw, C_out, false, st);
+    const int prec = d2_cost_prec(flags);
+    if ((rc = d2_cost_prepare(ctx, bags, m, prec))) return rc;
+    return d2_cost_rows(ctx, bags, members, P, K, m, cw, C_out, false, prec, st);
 }

@@ -70,6 +70,10 @@ void d2_time_end(d2_ctx* ctx, cudaStream_t st);
 #define D2F_BAD_MEMBER    0x08
 #define D2F_PIVOT_LIMIT   0x10
 #define D2F_BAD_SIZE      0x20
+#define D2F_DEV_TIMEOUT   0x40   // a bounded device-side wait expired
+// Word of dev_flags that accumulates sticky device errors (read and cleared
+// by d2_device_errors); word 0 is per-call validation scratch.
+#define D2_DEV_ERR_WORD   1
 
 int d2_fail(d2_ctx* ctx, int code, const char* fmt, ...);
 int d2_cuda_fail(d2_ctx* ctx, cudaError_t e, const char* what);
@@ -162,9 +166,23 @@ int d2_setup_clusters(d2_ctx* ctx, const int64_t* cofs, int64_t P, int K, int32_
 // Centre and norms of each barycenter (mu_c, x_c - mu_c, ||x_c,i - mu_c||^2).
 int d2_prep_x(d2_ctx* ctx, const float* x, int K, int m, int d, const ClusterWs& cw, cudaStream_t st);
 
+// Cost precision requested by a flags word: 0 (FP32 CUDA cores),
+// D2_COST_BF16, D2_COST_BF16X3 or D2_COST_BF16X6 (tensor cores, where they apply).
+static inline int d2_cost_prec(int flags) {
+    if ((flags & D2_COST_BF16X6) == D2_COST_BF16X6) return D2_COST_BF16X6;
+    return (flags & D2_COST_BF16X3) ? D2_COST_BF16X3 : (flags & D2_COST_BF16) ? D2_COST_BF16 : 0;
+}
+
 // Sets the launch attributes d2_cost_rows will need (done before a capture).
-int d2_cost_prepare(d2_ctx* ctx, const d2_bags* b, int m);
+int d2_cost_prepare(d2_ctx* ctx, const d2_bags* b, int m, int prec);
+
+// Tensor-core build (cost_tc.cu); *used = false when (d, m, prec) is outside
+// what it covers, and then nothing is launched.
+int d2_cost_tc_prepare(d2_ctx* ctx, const d2_bags* b, int m, int prec, bool* used);
+int d2_cost_tc_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t maxch, int m, int prec,
+                    const ClusterWs& cw, float* C, double* chunk_sum, int64_t* chunk_rows, cudaStream_t st,
+                    bool* used);
 
 // Cost rows of every member position; accumulates FP64 sums per cluster when csum.
 int d2_cost_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t P, int K, int m,
-                 const ClusterWs& cw, float* C, bool want_sums, cudaStream_t st);
+                 const ClusterWs& cw, float* C, bool want_sums, int prec, cudaStream_t st);

@@ -54,3 +54,18 @@ def compare_cluster(bags, cluster_offsets, members, c, gx, gw, gplan, gobj, ref,
     assert abs(float(gobj[c]) - ref["obj"]) <= obj_rtol * abs(ref["obj"]), (float(gobj[c]), ref["obj"])
     if x_tol is not None:
         np.testing.assert_allclose(gx[c].double().numpy(), ref["x"], rtol=0, atol=x_tol)
+
+
+def oracle_cluster_job(args):
+    """One oracle barycenter (a process-pool job): (members, x0, w0, T, tau)."""
+    from oracle import badmm_barycenter
+    members, x0, w0, T, tau = args
+    return badmm_barycenter(members, x0, w0, T=T, tau=tau)
+
+
+def oracle_clusters(jobs, procs=8):
+    """Oracle barycenters of several clusters in spawned worker processes
+    (spawn: the parent has already initialised CUDA)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(procs, max(1, len(jobs)))) as pool:
+        return pool.map(oracle_cluster_job, jobs)

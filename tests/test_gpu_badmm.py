@@ -11,7 +11,7 @@ import torch
 
 import synth
 from oracle import badmm_barycenter as oracle_badmm, cost_matrix
-from tests.helpers import (cluster_members, compare_cluster, member_plan, run_gpu_badmm,
+from tests.helpers import (cluster_members, compare_cluster, member_plan, oracle_clusters, run_gpu_badmm,
                            split_clusters)
 
 pytestmark = pytest.mark.gpu
@@ -188,20 +188,42 @@ def test_invalid_arguments(d2, ctx):
     d2.d2_check_bags(ctx, db)
 
 
-def test_full_size_ragged_clusters(d2, ctx):
-    """4,096 clusters with log-uniform member counts in [16, 4096] (~3M
-    distributions), d=64, m_k ~ U{16..64}, m=32, T=100: the launch
-    configuration the benchmark times.  Checks plan marginals on every cluster
-    and full parity on three sampled clusters against the oracle."""
+@pytest.fixture(scope="module")
+def full_size():
+    """The benchmark's workload: 4,096 clusters with log-uniform member counts
+    in [16, 4096] (~3M distributions), d=64, m_k ~ U{16..64}, m=32, T=100, and
+    the FP64 oracle on a 32-cluster subset (clusters at evenly spaced ranks of
+    size up to the 75th percentile, plus the largest-but-one quartile's first)."""
     bags, co, mem = synth.ragged_cluster_bags(7, 4096, device="cuda")
     m = 32
     x0, w0 = synth.sample_initial_barycenters(8, bags, co, mem, m)
+    sizes = (co[1:] - co[:-1]).cpu()
+    order = torch.argsort(sizes)
+    picks = [int(order[i]) for i in np.linspace(0, 3072, 32).astype(int)]
+    host = bags.to("cpu")
+    jobs = []
+    for c in picks:
+        _, members = cluster_members(host, co, mem, c)
+        jobs.append((members, x0[c].double().cpu().numpy(), w0[c].double().cpu().numpy(), 100, 10))
+    refs = oracle_clusters(jobs)
+    return bags, host, co, mem, x0, w0, picks, refs
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_full_size_ragged_clusters(d2, ctx, full_size, precision):
+    """The launch configuration the benchmark times (FP32 cost build, and the
+    split-BF16 tensor-core build the benchmark uses).  Checks plan marginals on
+    every cluster and full parity against the oracle on the 32-cluster subset."""
+    bags, host, co, mem, x0, w0, picks, refs = full_size
+    m = 32
     db = d2.DeviceBags.from_synth(bags)
     x, w = x0.clone(), w0.clone()
     plan = torch.empty(bags.n, m, dtype=torch.float32, device="cuda")
-    d2.badmm_barycenter(ctx, db, co, mem, x, w, plan, None, d2.badmm_opts(iters=100, tau=10),
-                        obj := torch.empty(4096, dtype=torch.float64, device="cuda"))
+    obj = torch.empty(4096, dtype=torch.float64, device="cuda")
+    d2.badmm_barycenter(ctx, db, co, mem, x, w, plan, None, d2.badmm_opts(iters=100, tau=10, cost=precision),
+                        obj)
     torch.cuda.synchronize()
+    assert ctx.device_errors() == 0
     # Pi^(k,2) row sums equal w_i for every member (Eq. badmmc1), w in the simplex
     owner = torch.repeat_interleave(torch.arange(bags.N, device="cuda"), bags.offsets[1:] - bags.offsets[:-1])
     rows = torch.zeros(bags.N, m, dtype=torch.float64, device="cuda").index_add_(0, owner, plan.double())
@@ -209,21 +231,21 @@ def test_full_size_ragged_clusters(d2, ctx):
     assert torch.allclose(rows, w[clus].double(), atol=1e-6, rtol=0)
     assert torch.allclose(w.double().sum(1), torch.ones(4096, dtype=torch.float64, device="cuda"), atol=1e-6)
     assert torch.isfinite(obj).all() and (obj > 0).all()
-    sizes = (co[1:] - co[:-1]).cpu()
-    order = torch.argsort(sizes)
-    picks = [int(order[0]), int(order[2048]), int(order[3000])]
-    host = bags.to("cpu")
-    gx, gw, gplan, gobj = x.cpu(), w.cpu(), None, obj.cpu()
-    for c in picks:
-        ids, members = cluster_members(host, co, mem, c)
-        ref = oracle_badmm(members, x0[c].double().cpu().numpy(), w0[c].double().cpu().numpy(),
-                           T=100, tau=10)
-        np.testing.assert_allclose(gw[c].double().numpy(), ref["w"], atol=1e-5, rtol=0)
-        assert abs(float(gobj[c]) - ref["obj"]) <= 1e-4 * ref["obj"]
+    gw, gobj, gx = w.cpu(), obj.cpu(), x.cpu()
+    worst = np.zeros(4)
+    for c, ref in zip(picks, refs):
+        ids, _ = cluster_members(host, co, mem, c)
+        ew = float(np.abs(gw[c].double().numpy() - ref["w"]).max())
+        eo = abs(float(gobj[c]) - ref["obj"]) / ref["obj"]
+        ex = float(np.abs(gx[c].double().numpy() - ref["x"]).max())
+        ep = 0.0
         for t, k in enumerate(ids):
             a, b = int(host.offsets[k]), int(host.offsets[k + 1])
-            got = plan[a:b].double().cpu().numpy().T
-            np.testing.assert_allclose(got, ref["P2"][t], atol=1e-5, rtol=0)
+            ep = max(ep, float(np.abs(plan[a:b].double().cpu().numpy().T - ref["P2"][t]).max()))
+        worst = np.maximum(worst, [ew, ep, eo, ex / (1 + float(np.abs(ref["x"]).max()))])
+    print("full size, %s cost, 32 clusters: max |w| err %.2e, max |plan| err %.2e, max rel obj err %.2e, "
+          "max x err / (1 + max|x|) %.2e" % (precision, *worst))
+    assert worst[0] <= 1e-5 and worst[1] <= 1e-5 and worst[2] <= 1e-4 and worst[3] <= 2e-4
 
 
 def test_graph_replay_matches_direct_launches(d2, ctx):
