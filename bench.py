@@ -327,6 +327,75 @@ def pruning_at_scale(d2, ctx, dev, seed, steps=1500):
     return out
 
 
+DOCS_WORKLOAD = dict(N=200_000, V=50_000, d=300, mk=(10, 60), K=64, m=64, rounds=5, iters=100, tau=10,
+                     desc="document-like sparse bags: N=200,000 distributions in d=300 (unit-norm Gaussian "
+                          "word vectors from a 50,000-entry seeded vocabulary, stored as indices), "
+                          "m_k~U{10..60} distinct words sampled Zipf(1.1), weights = normalised counts; "
+                          "K=64, m=64; D2-clustering, 5 rounds x 100 B-ADMM iterations; split-BF16 "
+                          "tensor-core cost build")
+
+
+def docs_clustering(d2, ctx, dev, seed):
+    """D2-clustering of the document-like workload with the tensor-core cost
+    build: seconds per round with the learned pruner (trained on 100k exact
+    W^2 pairs against the merge-initialised centroids) and the B-ADMM share of
+    a round; the exact full-K assignment of the plain form is timed on a
+    sample of bags and scaled to all N (its full run takes minutes)."""
+    W = DOCS_WORKLOAD
+    K, m, R = W["K"], W["m"], W["rounds"]
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = fn()
+        torch.cuda.synchronize()
+        return res, time.perf_counter() - t0
+
+    bags, t_gen = timed(lambda: synth.document_bags(seed, W["N"], V=W["V"], d=W["d"], mk=W["mk"], device=dev))
+    db = d2.DeviceBags(bags.offsets, bags.wt, bags.d, vocab_idx=bags.vocab_idx, vocab=bags.vocab)
+    opts = d2.badmm_opts(iters=W["iters"], tau=W["tau"], cost="bf16x3")
+    out = {"workload": W["desc"], "N": bags.N, "support_rows": bags.n, "generate_s": t_gen}
+    # centroids of Algorithm 1's initialisation, for the pruner's training pairs
+    x0, w0 = d2.d2_merge_init(ctx, db, torch.tensor(pick_ids(bags, K, m, 11), device=dev), m)
+    g = torch.Generator(device=dev).manual_seed(seed + 5)
+    npairs = 100_000
+    pb = torch.randint(0, bags.N, (npairs,), generator=g, device=dev)
+    pc = torch.randint(0, K, (npairs,), generator=g, device=dev, dtype=torch.int32)
+    tg, t_tg = timed(lambda: d2.d2_w2_pairs(ctx, db, x0, w0, pb, pc))
+    pr = d2.Pruner(ctx, bags.d, hidden=128, embed=64, seed=3)
+    _, t_train = timed(lambda: pr.train(db, x0, w0, pb, pc, tg, steps=600, batch=1024, lr=2e-3, seed=4))
+    _, delta = pr.margin()
+    pr.set_margin(8, delta)
+    # exact full-K rate on a sample (the plain form's assignment)
+    ns = 2000
+    sub = synth.subset_bags(bags, torch.arange(ns, device=dev))
+    dsub = d2.DeviceBags(sub.offsets, sub.wt, sub.d, vocab_idx=sub.vocab_idx, vocab=sub.vocab)
+    d2.d2_assign(ctx, dsub, x0, w0)
+    (le, _), t_ex = timed(lambda: d2.d2_assign(ctx, dsub, x0, w0))
+    (lp, _, st), t_pr = timed(lambda: d2.d2_assign(ctx, dsub, x0, w0, prune=pr, want_stats=True))
+    # pruned D2-clustering, all rounds, timed as one call
+    (xq, wq, lq, oq), t_cl = timed(lambda: d2.d2_cluster(ctx, db, K, m, 11, R, opts, prune=pr))
+    cs = ctx.cluster_stats()
+    # one B-ADMM update of all clusters at the final labels (the update step of a round)
+    order = torch.sort(lq.long(), stable=True).indices
+    co = torch.zeros(K + 1, dtype=torch.int64, device=dev)
+    co[1:] = torch.cumsum(torch.bincount(lq.long(), minlength=K), 0)
+    xb, wb = xq.clone(), wq.clone()
+    d2.badmm_barycenter(ctx, db, co, order.contiguous(), xb, wb, None, None, opts)
+    xb, wb = xq.clone(), wq.clone()
+    _, t_b = timed(lambda: d2.badmm_barycenter(ctx, db, co, order.contiguous(), xb, wb, None, None, opts))
+    out.update({"pruned_s_per_round": t_cl / R, "obj_per_round": oq,
+                "badmm_update_s": t_b, "badmm_updates_per_s": m * bags.n * W["iters"] / t_b,
+                "exact_solves": cs["exact_solves"], "fallbacks": cs["fallbacks"],
+                "full_K_solves_per_round": bags.N * K,
+                "pruner": {"r": 8, "delta": delta, "train_pairs": npairs, "target_s": t_tg, "train_s": t_train,
+                           "sample_bags": ns, "misassignment_vs_exact_on_sample": float((lp != le).float().mean()),
+                           "sample_exact_solves": st["exact_solves"], "sample_fallbacks": st["fallbacks"]},
+                "exact_pairs_per_s": ns * K / t_ex,
+                "plain_assign_s_per_round_est": bags.N * K / (ns * K / t_ex)})
+    return out
+
+
 def pick_ids(bags, K, m, seed):
     """The K bags d2_cluster seeds its centroids from (SplitMix64 partial
     Fisher-Yates over the ids with m_k >= m), for the plain-form replay."""
@@ -412,8 +481,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-d2", action="store_true", help="skip the D2-clustering s/round comparison")
     ap.add_argument("--pruning", action="store_true", help="also run the learned-pruning assignment at scale")
+    ap.add_argument("--docs", action="store_true",
+                    help="also run D2-clustering of the 200k document-like bags (d=300, K=64, m=64)")
     ap.add_argument("--cost", default="bf16x3", choices=["fp32", "bf16", "bf16x3", "bf16x6"],
                     help="cost-build precision (bf16*: tensor cores)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default sweep launch shape")
     ap.add_argument("--no-cost-variants", action="store_true",
                     help="skip the timing of the other cost-build precisions")
     args = ap.parse_args()
@@ -450,13 +522,15 @@ def main():
     opts = d2.badmm_opts(iters=T, tau=W["tau"], cost=args.cost)
     ctx = d2.Context(local)
 
-    def step():
+    def step(o=opts):
         x.copy_(x0)
         w.copy_(w0)
-        d2.badmm_barycenter(ctx, db, co, mem, x, w, plan, None, opts, obj)
+        d2.badmm_barycenter(ctx, db, co, mem, x, w, plan, None, o, obj)
 
-    for _ in range(args.warmup):
-        step()
+    # the first warm-up step lets the autotuner pick the sweep's launch shape
+    for i in range(args.warmup):
+        step(d2.badmm_opts(iters=T, tau=W["tau"], cost=args.cost, autotune=not args.no_autotune)
+             if i == 0 else opts)
     torch.cuda.synchronize()
     assert torch.isfinite(obj).all(), "non-finite objective"
 
@@ -493,7 +567,14 @@ def main():
         avg_s = f_ms / f_n * 1e-3
         achieved = BYTES_PER_ENTRY * entries / avg_s / 1e9
         tpe = sweep_traffic_per_entry()
-        roof = {"bound": "hbm", "kernel": "k_sweep (fused B+A pass)", "achieved": achieved,
+        tun = ctx.sweep_tuning(m)
+        kname = "k_sweep_pipe<4, 2, 4> (fused B+A pass)"
+        if tun is not None:
+            cd = tun["candidates"][tun["chosen"]]
+            kname = "%s (fused B+A pass; %d lanes/row, %d float4/lane, %d CTAs/SM, autotuned)" % (
+                "k_sweep_pipe" if cd["kind"] == "pipelined" else "k_sweep", cd["lanes_per_row"],
+                cd["float4_per_lane"], cd["ctas_per_sm"])
+        roof = {"bound": "hbm", "kernel": kname, "achieved": achieved,
                 "peak": peak, "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None if tpe is None else tpe * entries,
                 "algorithmic_bytes_per_launch": BYTES_PER_ENTRY * entries,
@@ -596,6 +677,13 @@ def main():
         except Exception as exc:
             prune_res = {"error": repr(exc)}
 
+    docs_res = None
+    if rank == 0 and args.docs:
+        try:
+            docs_res = docs_clustering(d2, ctx, dev, args.seed + 41)
+        except Exception as exc:
+            docs_res = {"error": repr(exc)}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, desc, _ = oracle_sample(args.workload, args.seed, args.cpu_budget)
@@ -611,10 +699,13 @@ def main():
                            % (12 * entries / 1e9),
                            "parallelism": "independent problem per GPU" if world > 1 else "single GPU"},
                 "roofline": roof, "cost_roofline": cost_roof, "cost_variants": variants,
+                "sweep_autotune": ctx.sweep_tuning(m),
                 "kernel_breakdown_ms_per_step": breakdown, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "d2_round": d2cmp}
         if prune_res is not None:
             line["pruning"] = prune_res
+        if docs_res is not None:
+            line["docs_clustering"] = docs_res
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

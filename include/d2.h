@@ -58,6 +58,9 @@ extern "C" {
                              shared-memory pipelined one (both compute the same)  */
 #define D2_ELKAN     0x20 /* d2_cluster: skip assignment pairs by the triangle
                              inequality of W (Section 5), when no pruner is given */
+#define D2_AUTOTUNE  0x100 /* badmm_barycenter: choose the plan sweep's launch shape
+                             for this plan width m by timing candidates (see
+                             d2_sweep_tuning); kept in the context for later calls */
 /* Precision of the cost build c(x_i, y_j) = ||x_i - y_j||^2 (Section 2).  Default
  * (neither flag): FP32 on CUDA cores.  With one of these flags, and when the
  * support dimension makes the build a dense contraction (d >= 32, d % 4 == 0,
@@ -71,6 +74,11 @@ extern "C" {
                                about 16 mantissa bits                           */
 #define D2_COST_BF16X6 0xC0 /* each factor split hi + mid + lo (BF16, exact for
                                FP32 inputs), six products: FP32-level error     */
+/* Testing only (d2_cost): the tensor-core build issues no MMA for each CTA's
+ * first tile, so that CTA's bounded wait expires (about 2 s); the CTA then
+ * stops, the call's output is undefined and d2_device_errors reports
+ * D2_ETIMEOUT.  Exercises the expiry path without a fault or a hang. */
+#define D2_TEST_EXPIRE_WAIT 0x8000
 
 typedef struct d2_ctx d2_ctx;
 
@@ -99,7 +107,8 @@ typedef struct {
     int32_t tau;       /* support update every tau iterations, default 10               */
     int32_t rule;      /* D2_RULE_R1 (default) or D2_RULE_R2                            */
     int32_t flags;     /* D2_FIX_X | D2_FIX_W | D2_VALIDATE | D2_NO_GRAPH | D2_NO_PIPE |
-                          D2_ELKAN | one of D2_COST_BF16, _BF16X3, _BF16X6             */
+                          D2_ELKAN | D2_AUTOTUNE |
+                          one of D2_COST_BF16, _BF16X3, _BF16X6                        */
 } d2_badmm_opts;
 
 /* Fill `o` with the defaults above. */
@@ -197,6 +206,26 @@ int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_of
                      const int64_t* members, int64_t P, int32_t K, int32_t m,
                      float* x, float* w, float* plan, const uint8_t* warm_mask,
                      const d2_badmm_opts* opts, double* obj, void* stream);
+
+/* Plan-sweep autotuner (no counterpart in the paper; Algorithm badmm fixes
+ * what is computed, not how it is laid out on a GPU).  The first
+ * badmm_barycenter call on a context with D2_AUTOTUNE in opts->flags and plan
+ * width m runs its fused passes (iterations that carry both halves of
+ * Eqs. badmmc1/badmm2 and badmmc0b/badmmc0) with each candidate launch shape
+ * in turn, `reps` passes per candidate, timing each with CUDA events; every
+ * candidate computes the same iteration, so the call's results are valid (up
+ * to FP32 rounding order).  The fastest shape is kept in the context and used
+ * by later calls with that m (with or without the flag).  Candidates: the
+ * shared-memory pipelined sweep with 2 or 1 float4s per lane (m/8 or m/4
+ * lanes per plan row), the register-prefetch sweep, each with 1..max
+ * persistent CTAs per SM (members per warp follow from the grid).
+ *   ncand, chosen : host, out (chosen = -1 and ncand = 0 when m is untuned)
+ *   ms            : host, D2_TUNE_MAX floats: mean fused-pass milliseconds
+ *   shape         : host, D2_TUNE_MAX x 4 int32: kind (0 pipelined,
+ *                   1 prefetch), lanes per row, float4s per lane, CTAs/SM */
+#define D2_TUNE_MAX 16
+int d2_sweep_tuning(const d2_ctx* ctx, int32_t m, int32_t* ncand, int32_t* chosen,
+                    float* ms, int32_t* shape);
 
 /* Exact W^2 solves (stats[0]) and pruner fall-backs (stats[1]) of the last
  * d2_cluster call on this context (host, 2 int64). */

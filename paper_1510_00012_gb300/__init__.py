@@ -23,6 +23,9 @@ D2_NOALLOC_MAX_PAIRS = 1 << 20
 D2_RULE_R1, D2_RULE_R2 = 1, 2
 D2_FIX_X, D2_FIX_W, D2_VALIDATE, D2_NO_GRAPH, D2_NO_PIPE, D2_ELKAN = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
 D2_COST_BF16, D2_COST_BF16X3, D2_COST_BF16X6 = 0x40, 0x80, 0xC0
+D2_AUTOTUNE = 0x100
+D2_TEST_EXPIRE_WAIT = 0x8000
+D2_TUNE_MAX = 16
 COST_PRECISION = {"fp32": 0, "bf16": D2_COST_BF16, "bf16x3": D2_COST_BF16X3, "bf16x6": D2_COST_BF16X6}
 KT_NAMES = ("sweep_fused", "sweep_half", "cost", "support", "assign", "prune", "other")
 KT_COUNT = len(KT_NAMES)
@@ -56,6 +59,7 @@ _SIGS = {
     "d2_timing_read": (c_int, [c_void_p, c_void_p, c_void_p]),
     "d2_launch_count": (c_int64, [c_void_p]),
     "d2_device_errors": (c_int, [c_void_p, c_void_p]),
+    "d2_sweep_tuning": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "d2_cluster_stats": (c_int, [c_void_p, c_void_p]),
     "d2_cost": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32,
                         c_void_p, c_void_p, c_int32, c_void_p]),
@@ -177,6 +181,21 @@ class Context:
         self.check(lib().d2_device_errors(self.h, ctypes.byref(bits)))
         return int(bits.value)
 
+    def sweep_tuning(self, m):
+        """The plan-sweep autotuner's record for plan width m: None when untuned,
+        else {"chosen": i, "candidates": [{"kind", "lanes_per_row",
+        "float4_per_lane", "ctas_per_sm", "ms"}, ...]}."""
+        n, ch = c_int32(0), c_int32(-1)
+        ms = (c_float * D2_TUNE_MAX)()
+        shape = (c_int32 * (4 * D2_TUNE_MAX))()
+        self.check(lib().d2_sweep_tuning(self.h, int(m), ctypes.byref(n), ctypes.byref(ch), ms, shape))
+        if n.value == 0:
+            return None
+        cands = [{"kind": ("pipelined", "prefetch")[shape[4 * i]], "lanes_per_row": shape[4 * i + 1],
+                  "float4_per_lane": shape[4 * i + 2], "ctas_per_sm": shape[4 * i + 3], "ms": ms[i]}
+                 for i in range(n.value)]
+        return {"chosen": ch.value, "candidates": cands}
+
     def cluster_stats(self):
         """Exact W^2 solves and pruner fall-backs of the last d2_cluster call."""
         st = (c_int64 * 2)()
@@ -221,14 +240,15 @@ def _cost_flag(precision):
 
 
 def badmm_opts(rho0=2.0, iters=100, tau=10, eps=1e-16, rule="R1", fix_x=False, fix_w=False,
-               validate=False, rho=0.0, graph=True, elkan=False, cost="fp32"):
+               validate=False, rho=0.0, graph=True, elkan=False, cost="fp32", autotune=False):
     """d2_badmm_opts; cost = "fp32" | "bf16" | "bf16x3" | "bf16x6" selects the cost build."""
     o = _Opts()
     lib().d2_badmm_opts_default(ctypes.byref(o))
     o.rho0, o.iters, o.tau, o.eps, o.rho = float(rho0), int(iters), int(tau), float(eps), float(rho)
     o.rule = D2_RULE_R2 if rule == "R2" else D2_RULE_R1
     o.flags = ((D2_FIX_X if fix_x else 0) | (D2_FIX_W if fix_w else 0) | (D2_VALIDATE if validate else 0)
-               | (0 if graph else D2_NO_GRAPH) | (D2_ELKAN if elkan else 0) | _cost_flag(cost))
+               | (0 if graph else D2_NO_GRAPH) | (D2_ELKAN if elkan else 0) | _cost_flag(cost)
+               | (D2_AUTOTUNE if autotune else 0))
     return o
 
 
@@ -236,7 +256,7 @@ def d2_check_bags(ctx, bags):
     return ctx.check(lib().d2_check_bags(ctx.h, bags.ref(), _stream()))
 
 
-def d2_cost(ctx, bags, cluster_offsets, members, x, C_out=None, precision="fp32"):
+def d2_cost(ctx, bags, cluster_offsets, members, x, C_out=None, precision="fp32", extra_flags=0):
     """C (n x m, j-major rows) between each cluster's support x[c] and its members;
     precision = "fp32" | "bf16" | "bf16x3" | "bf16x6" (tensor cores where d >= 32)."""
     _need(cluster_offsets, torch.int64, "cluster_offsets")
@@ -247,7 +267,8 @@ def d2_cost(ctx, bags, cluster_offsets, members, x, C_out=None, precision="fp32"
         C_out = torch.zeros(bags.n, m, dtype=torch.float32, device=x.device)
     _need(C_out, torch.float32, "C_out")
     ctx.check(lib().d2_cost(ctx.h, bags.ref(), _ptr(cluster_offsets), _ptr(members), members.numel(),
-                            K, m, _ptr(x), _ptr(C_out), _cost_flag(precision), _stream()))
+                            K, m, _ptr(x), _ptr(C_out), _cost_flag(precision) | int(extra_flags),
+                            _stream()))
     return C_out
 
 

@@ -623,49 +623,127 @@ typedef void (*SweepFn)(SweepArgs);
 #endif
 
 template <int LPR, int NV>
-static SweepFn pipe_variant(size_t* smem) {
+static SweepFn pipe_variant(size_t* smem, int* lpr) {
     *smem = SWEEP_WARPS * sizeof(PipeWarp<LPR, NV, D2_PIPE_S>);
+    *lpr = LPR;
     return k_sweep_pipe<LPR, NV, D2_PIPE_S>;
 }
 
-static SweepFn pick_sweep_pipe(int m, size_t* smem) {
+// Pipelined sweep with NV float4s per lane (2 needs m % 8 == 0; 1 needs m <= 128).
+static SweepFn pipe_with(int m, int nv, size_t* smem, int* lpr) {
     if (m % 4 != 0 || m > 256) return nullptr;
-    if (D2_PIPE_NV == 2 && m >= 8 && m % 8 == 0) {
-        if (m <= 8) return pipe_variant<1, 2>(smem);
-        if (m <= 16) return pipe_variant<2, 2>(smem);
-        if (m <= 32) return pipe_variant<4, 2>(smem);
-        if (m <= 64) return pipe_variant<8, 2>(smem);
-        if (m <= 128) return pipe_variant<16, 2>(smem);
-        return pipe_variant<32, 2>(smem);
+    if (nv == 2) {
+        if (m < 8 || m % 8 != 0) return nullptr;
+        if (m <= 8) return pipe_variant<1, 2>(smem, lpr);
+        if (m <= 16) return pipe_variant<2, 2>(smem, lpr);
+        if (m <= 32) return pipe_variant<4, 2>(smem, lpr);
+        if (m <= 64) return pipe_variant<8, 2>(smem, lpr);
+        if (m <= 128) return pipe_variant<16, 2>(smem, lpr);
+        return pipe_variant<32, 2>(smem, lpr);
     }
     if (m > 128) return nullptr;
-    if (m <= 4) return pipe_variant<1, 1>(smem);
-    if (m <= 8) return pipe_variant<2, 1>(smem);
-    if (m <= 16) return pipe_variant<4, 1>(smem);
-    if (m <= 32) return pipe_variant<8, 1>(smem);
-    if (m <= 64) return pipe_variant<16, 1>(smem);
-    return pipe_variant<32, 1>(smem);
+    if (m <= 4) return pipe_variant<1, 1>(smem, lpr);
+    if (m <= 8) return pipe_variant<2, 1>(smem, lpr);
+    if (m <= 16) return pipe_variant<4, 1>(smem, lpr);
+    if (m <= 32) return pipe_variant<8, 1>(smem, lpr);
+    if (m <= 64) return pipe_variant<16, 1>(smem, lpr);
+    return pipe_variant<32, 1>(smem, lpr);
 }
 
-static SweepFn pick_sweep(int m) {
-    if (m % 4 == 0) {
-        if (m <= 4) return k_sweep<4, 1, 1>;
-        if (m <= 8) return k_sweep<4, 2, 1>;
-        if (m <= 16) return k_sweep<4, 4, 1>;
-        if (m <= 32) return k_sweep<4, 8, 1>;
-        if (m <= 64) return k_sweep<4, 16, 1>;
-        if (m <= 128) return k_sweep<4, 32, 1>;
-        return k_sweep<4, 32, 2>;
+static SweepFn pick_sweep_pipe(int m, size_t* smem) {
+    int lpr = 0;
+    if (D2_PIPE_NV == 2) {
+        SweepFn f = pipe_with(m, 2, smem, &lpr);
+        if (f) return f;
     }
-    if (m <= 1) return k_sweep<1, 1, 1>;
-    if (m <= 2) return k_sweep<1, 2, 1>;
-    if (m <= 4) return k_sweep<1, 4, 1>;
-    if (m <= 8) return k_sweep<1, 8, 1>;
-    if (m <= 16) return k_sweep<1, 16, 1>;
-    if (m <= 32) return k_sweep<1, 32, 1>;
-    if (m <= 64) return k_sweep<1, 32, 2>;
-    if (m <= 128) return k_sweep<1, 32, 4>;
-    return k_sweep<1, 32, 8>;
+    return pipe_with(m, 1, smem, &lpr);
+}
+
+static SweepFn pick_sweep(int m, int* lpr = nullptr, int* nv = nullptr) {
+    int l = 32, v = 1;
+    SweepFn f;
+    if (m % 4 == 0) {
+        if (m <= 4) { f = k_sweep<4, 1, 1>; l = 1; }
+        else if (m <= 8) { f = k_sweep<4, 2, 1>; l = 2; }
+        else if (m <= 16) { f = k_sweep<4, 4, 1>; l = 4; }
+        else if (m <= 32) { f = k_sweep<4, 8, 1>; l = 8; }
+        else if (m <= 64) { f = k_sweep<4, 16, 1>; l = 16; }
+        else if (m <= 128) { f = k_sweep<4, 32, 1>; l = 32; }
+        else { f = k_sweep<4, 32, 2>; l = 32; v = 2; }
+    } else {
+        v = 0;  // scalar lanes
+        if (m <= 1) { f = k_sweep<1, 1, 1>; l = 1; }
+        else if (m <= 2) { f = k_sweep<1, 2, 1>; l = 2; }
+        else if (m <= 4) { f = k_sweep<1, 4, 1>; l = 4; }
+        else if (m <= 8) { f = k_sweep<1, 8, 1>; l = 8; }
+        else if (m <= 16) { f = k_sweep<1, 16, 1>; l = 16; }
+        else if (m <= 32) { f = k_sweep<1, 32, 1>; l = 32; }
+        else if (m <= 64) f = k_sweep<1, 32, 2>;
+        else if (m <= 128) f = k_sweep<1, 32, 4>;
+        else f = k_sweep<1, 32, 8>;
+    }
+    if (lpr) *lpr = l;
+    if (nv) *nv = v;
+    return f;
+}
+
+// One candidate launch shape of the plan sweep for the autotuner.
+struct SweepCand {
+    SweepFn fn;
+    size_t smem;
+    int kind, lpr, nv, per_sm;
+};
+
+// Candidates for plan width m: pipelined with 2 or 1 float4s per lane and the
+// register-prefetch sweep, each with 1 .. (max resident) persistent CTAs per SM.
+static int sweep_candidates(d2_ctx* ctx, int m, std::vector<SweepCand>* out) {
+    struct Base { SweepFn fn; size_t smem; int kind, lpr, nv; };
+    std::vector<Base> bases;
+    for (int nv = 2; nv >= 1; --nv) {
+        size_t sm = 0;
+        int lpr = 0;
+        SweepFn f = pipe_with(m, nv, &sm, &lpr);
+        if (f) bases.push_back({f, sm, 0, lpr, nv});
+    }
+    {
+        int lpr = 0, nv = 0;
+        SweepFn f = pick_sweep(m, &lpr, &nv);
+        bases.push_back({f, 0, 1, lpr, nv});
+    }
+    for (const Base& b : bases) {
+        if (b.smem > 48 * 1024)
+            D2_CK(ctx, cudaFuncSetAttribute(b.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem));
+        int occ = 1;
+        D2_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, b.fn, SWEEP_THREADS, b.smem));
+        occ = std::max(1, std::min(occ, 4));
+        for (int k = 1; k <= occ && (int)out->size() < D2_TUNE_MAX; ++k)
+            out->push_back({b.fn, b.smem, b.kind, b.lpr, b.nv, k});
+    }
+    return D2_OK;
+}
+
+static SweepTune* find_tune(d2_ctx* ctx, int m) {
+    for (auto& t : ctx->tuned)
+        if (t.m == m) return &t;
+    return nullptr;
+}
+
+extern "C" int d2_sweep_tuning(const d2_ctx* ctx, int32_t m, int32_t* ncand, int32_t* chosen, float* ms,
+                               int32_t* shape) {
+    if (!ctx) return D2_EINVAL;
+    if (ncand) *ncand = 0;
+    if (chosen) *chosen = -1;
+    for (const auto& t : ctx->tuned) {
+        if (t.m != m) continue;
+        if (ncand) *ncand = t.ncand;
+        if (chosen) *chosen = t.chosen;
+        for (int i = 0; i < t.ncand; ++i) {
+            if (ms) ms[i] = t.ms[i];
+            if (shape)
+                for (int q = 0; q < 4; ++q) shape[i * 4 + q] = t.shape[i][q];
+        }
+    }
+    return D2_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -933,6 +1011,44 @@ __global__ void k_finish(int K, int m, const int64_t* cofs, const double* pos_ob
         for (int i = 0; i < m; ++i) w_out[(int64_t)c * m + i] = wfin[(int64_t)c * m + i];
 }
 
+// Reads the autotuner's event pairs (synchronises the stream), averages them
+// per candidate and keeps the fastest launch shape in the context.
+static int d2_tune_finish(d2_ctx* ctx, int m, const std::vector<SweepCand>& cands,
+                          const std::vector<cudaEvent_t>& tev, const std::vector<int>& tev_cand,
+                          cudaStream_t st) {
+    if (cands.empty() || tev_cand.empty()) return D2_OK;
+    D2_CK(ctx, cudaStreamSynchronize(st));
+    SweepTune t;
+    t.m = m;
+    t.ncand = (int)cands.size();
+    std::vector<double> sum(cands.size(), 0.0);
+    std::vector<int> cnt(cands.size(), 0);
+    for (size_t i = 0; i < tev_cand.size(); ++i) {
+        float ms = 0.f;
+        D2_CK(ctx, cudaEventElapsedTime(&ms, tev[2 * i], tev[2 * i + 1]));
+        sum[tev_cand[i]] += ms;
+        cnt[tev_cand[i]]++;
+    }
+    double best = 1e300;
+    for (int i = 0; i < t.ncand; ++i) {
+        t.ms[i] = cnt[i] ? (float)(sum[i] / cnt[i]) : 0.f;
+        t.shape[i][0] = cands[i].kind;
+        t.shape[i][1] = cands[i].lpr;
+        t.shape[i][2] = cands[i].nv;
+        t.shape[i][3] = cands[i].per_sm;
+        if (cnt[i] && sum[i] / cnt[i] < best) {
+            best = sum[i] / cnt[i];
+            t.chosen = i;
+        }
+    }
+    if (t.chosen < 0) return D2_OK;
+    t.fn = reinterpret_cast<const void*>(cands[t.chosen].fn);
+    t.smem = cands[t.chosen].smem;
+    t.per_sm = cands[t.chosen].per_sm;
+    ctx->tuned.push_back(t);
+    return D2_OK;
+}
+
 // ---------------------------------------------------------------------------
 // entry point
 // ---------------------------------------------------------------------------
@@ -1016,20 +1132,40 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
     const int rflag = (opts.rule == D2_RULE_R2) ? SW_R2 : 0;
     size_t sweep_smem = 0;
     SweepFn sweep = nullptr;
-    if (!(opts.flags & D2_NO_PIPE)) sweep = pick_sweep_pipe(m, &sweep_smem);
-    if (sweep) {
-        if (sweep_smem > 48 * 1024)
-            D2_CK(ctx, cudaFuncSetAttribute(sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem));
-    } else {
-        sweep = pick_sweep(m);
-        sweep_smem = 0;
-    }
-    // persistent grid: as many CTAs as fit on the device at once
     int dev_sms = 152, per_sm = 1;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep, SWEEP_THREADS, sweep_smem);
-    if (per_sm < 1) per_sm = 1;
+    const SweepTune* tuned = (opts.flags & D2_NO_PIPE) ? nullptr : find_tune(ctx, m);
+    if (tuned) {  // launch shape chosen earlier by the autotuner
+        sweep = reinterpret_cast<SweepFn>(const_cast<void*>(tuned->fn));
+        sweep_smem = tuned->smem;
+        per_sm = tuned->per_sm;
+    } else {
+        if (!(opts.flags & D2_NO_PIPE)) sweep = pick_sweep_pipe(m, &sweep_smem);
+        if (!sweep) {
+            sweep = pick_sweep(m);
+            sweep_smem = 0;
+        }
+    }
+    // (the shared-memory attribute must be set before the occupancy query)
+    if (sweep_smem > 48 * 1024)
+        D2_CK(ctx, cudaFuncSetAttribute(sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem));
+    if (!tuned) {
+        // persistent grid: as many CTAs as fit on the device at once
+        D2_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep, SWEEP_THREADS, sweep_smem));
+        if (per_sm < 1) per_sm = 1;
+    }
     const unsigned grid = (unsigned)std::min<int64_t>(d2_ceil_div(P, SWEEP_WARPS), (int64_t)dev_sms * per_sm);
+    // autotuning: the first fused passes cycle through the candidates
+    const bool tuning = (opts.flags & D2_AUTOTUNE) && !(opts.flags & D2_NO_PIPE) && !tuned;
+    std::vector<SweepCand> cands;
+    std::vector<cudaEvent_t> tev;
+    std::vector<int> tev_cand;
+    int fused_seen = 0, tune_reps = 0;
+    if (tuning) {
+        if ((rc = sweep_candidates(ctx, m, &cands))) return rc;
+        const int fused_total = std::max(0, opts.iters - 1 - (fix_x ? 0 : (opts.iters - 1) / opts.tau));
+        tune_reps = cands.empty() ? 0 : std::min(3, fused_total / (int)cands.size());
+    }
     const int T = opts.iters, tau = opts.tau;
     // the d % 4 == 0 and m % 4 == 0 path copies 16-byte slices of plan and y rows
     const bool xp_pipe = (d % 4 == 0) && (m % 4 == 0) &&
@@ -1052,8 +1188,24 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
         s.flags = flags | rflag;
         s.w_cur = wcur;
         s.w_next = fix_w ? nullptr : wnext;
-        d2_time_begin(ctx, ((flags & SW_A) && (flags & SW_B)) ? D2_KT_SWEEP_FUSED : D2_KT_SWEEP_HALF, st);
-        sweep<<<grid, SWEEP_THREADS, sweep_smem, st>>>(s);
+        const bool fused = (flags & SW_A) && (flags & SW_B);
+        d2_time_begin(ctx, fused ? D2_KT_SWEEP_FUSED : D2_KT_SWEEP_HALF, st);
+        if (fused && fused_seen < (int)cands.size() * tune_reps) {
+            const SweepCand& cd = cands[fused_seen % cands.size()];
+            const unsigned g = (unsigned)std::min<int64_t>(d2_ceil_div(P, SWEEP_WARPS), (int64_t)dev_sms * cd.per_sm);
+            cudaEvent_t e0, e1;
+            D2_CK(ctx, cudaEventCreate(&e0));
+            D2_CK(ctx, cudaEventCreate(&e1));
+            tev.push_back(e0);
+            tev.push_back(e1);
+            tev_cand.push_back(fused_seen % (int)cands.size());
+            D2_CK(ctx, cudaEventRecord(e0, st));
+            cd.fn<<<g, SWEEP_THREADS, cd.smem, st>>>(s);
+            D2_CK(ctx, cudaEventRecord(e1, st));
+        } else {
+            sweep<<<grid, SWEEP_THREADS, sweep_smem, st>>>(s);
+        }
+        if (fused) ++fused_seen;
         d2_time_end(ctx, st);
         D2_LAUNCH_CK(ctx, "k_sweep");
         if ((flags & SW_A) && s.w_next) {
@@ -1114,6 +1266,12 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
     // non-default stream that is not itself being captured, with per-launch
     // timing off.  The graph is rebuilt whenever anything it bakes in changes
     // (pointers, sizes, options, workspace placement).
+    if (tuning) {  // direct launches; read the candidates' times and keep the fastest
+        rc = enqueue();
+        if (rc == D2_OK) rc = d2_tune_finish(ctx, m, cands, tev, tev_cand, st);
+        for (auto e : tev) cudaEventDestroy(e);
+        return rc;
+    }
     const bool want_graph = !(opts.flags & D2_NO_GRAPH) && !ctx->timing && st != nullptr;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (want_graph && cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
@@ -1131,7 +1289,7 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
         u(bags->offsets), u(bags->supp), u(bags->vocab_idx), u(bags->vocab), (uint64_t)bags->V, u(bags->wt),
         u(cluster_offsets), u(members), (uint64_t)P, (uint64_t)K, (uint64_t)m, u(x), u(w), u(plan),
         u(warm_mask), u(obj), rho_bits, rho0_bits, eps_bits, (uint64_t)opts.iters, (uint64_t)opts.tau,
-        (uint64_t)opts.rule, (uint64_t)opts.flags};
+        (uint64_t)opts.rule, (uint64_t)opts.flags, u(reinterpret_cast<const void*>(sweep)), (uint64_t)per_sm};
     if (ctx->graph_exec && ctx->graph_key == key) {
         D2_CK(ctx, cudaGraphLaunch(ctx->graph_exec, st));
         ctx->launches += ctx->graph_launches;

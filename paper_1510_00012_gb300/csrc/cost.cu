@@ -498,5 +498,8 @@ extern "C" int d2_cost(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_
     if (rc) return rc;
     const int prec = d2_cost_prec(flags);
     if ((rc = d2_cost_prepare(ctx, bags, m, prec))) return rc;
-    return d2_cost_rows(ctx, bags, members, P, K, m, cw, C_out, false, prec, st);
+    ctx->expire_test = (flags & D2_TEST_EXPIRE_WAIT) ? 1 : 0;
+    rc = d2_cost_rows(ctx, bags, members, P, K, m, cw, C_out, false, prec, st);
+    ctx->expire_test = 0;
+    return rc;
 }

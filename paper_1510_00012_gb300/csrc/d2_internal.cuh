@@ -33,6 +33,18 @@ enum WsSlot {
     WS_NSLOTS
 };
 
+// Launch shape of the plan sweep chosen by the autotuner for one plan width m
+// (D2_TUNE_MAX candidates at most, see d2.h).
+struct SweepTune {
+    int m = 0;
+    const void* fn = nullptr;       // kernel
+    size_t smem = 0;                // dynamic shared memory
+    int per_sm = 1;                 // persistent CTAs per SM
+    int ncand = 0, chosen = -1;
+    float ms[D2_TUNE_MAX] = {};     // mean fused-pass time per candidate
+    int shape[D2_TUNE_MAX][4] = {}; // kind (0 pipelined, 1 prefetch), lanes/row, float4s/lane, CTAs/SM
+};
+
 struct TimedLaunch {
     int kind;
     cudaEvent_t a, b;
@@ -57,6 +69,10 @@ struct d2_ctx {
     int64_t graph_launches = 0;
     // exact W^2 solves and pruner fall-backs of the last d2_cluster call
     int64_t cluster_solves = 0, cluster_fallbacks = 0;
+    // sweep launch shapes chosen by the autotuner, one per plan width m
+    std::vector<SweepTune> tuned;
+    // testing: the next tensor-core cost build lets its first wait expire
+    int expire_test = 0;
 };
 
 // Event bracket around one launch when timing is on (no-ops otherwise).

@@ -274,3 +274,26 @@ def test_graph_replay_matches_direct_launches(d2, ctx):
         for a, b in zip(results[i], results[i + 1]):
             assert torch.equal(a, b)
     assert not torch.equal(results[0][0], results[2][0])
+
+
+def test_autotuned_sweep(d2):
+    """The autotuning call cycles its fused passes through every candidate
+    launch shape (all compute the same iteration) and keeps the fastest; that
+    call and a later one using the kept shape both match the oracle."""
+    ctx = d2.Context(0)
+    K, m = 5, 32
+    bags, co, mem, x0, w0 = ragged_case(16, K, m, d=8, N=200, mk=(4, 40))
+    assert ctx.sweep_tuning(m) is None
+    for call in range(2):
+        gx, gw, gplan, gobj = run_gpu_badmm(d2, ctx, bags, co, mem, x0, w0, iters=41, tau=10,
+                                            autotune=(call == 0))
+        rec = ctx.sweep_tuning(m)
+        assert rec is not None and 0 <= rec["chosen"] < len(rec["candidates"])
+        assert len(rec["candidates"]) >= 3 and all(c["ms"] > 0 for c in rec["candidates"])
+        for c in range(K):
+            ids, members = cluster_members(bags, co, mem, c)
+            if not ids:
+                continue
+            ref = oracle_badmm(members, x0[c].double().numpy(), w0[c].double().numpy(), T=41, tau=10)
+            compare_cluster(bags, co, mem, c, gx, gw, gplan, gobj, ref, x_tol=x_tol(ref))
+    print("autotune m=32:", rec)

@@ -182,3 +182,22 @@ def test_badmm_tensor_core_vocabulary(d2, ctx, precision):
     gx, gw, gplan, gobj = run_gpu_badmm(d2, ctx, bags, co, mem, x0, w0, iters=25, tau=10, cost=precision)
     assert ctx.device_errors() == 0
     _check_badmm(bags, co, mem, x0, w0, gx, gw, gplan, gobj, precision, 25, 10)
+
+
+def test_bounded_wait_expiry_is_reported(d2, ctx):
+    """The build's only device-side wait (its MMA completion) is bounded: with
+    the testing flag the first tile's MMAs are not issued, the wait expires
+    after about 2 s, the CTA stops and frees its tensor memory, and the host
+    reads D2_ETIMEOUT; the context stays usable for the next call."""
+    bags = synth.gaussian_class_bags(47, 6, 64, 1, mk=(4, 16))
+    co, mem = split_clusters(torch.zeros(bags.N, dtype=torch.int64), 1)
+    x0, _ = synth.sample_initial_barycenters(48, bags, co, mem, 32)
+    db = d2.DeviceBags.from_synth(bags)
+    assert ctx.device_errors() == 0
+    d2.d2_cost(ctx, db, co.cuda(), mem.cuda(), x0.cuda(), precision="bf16x3",
+               extra_flags=d2.D2_TEST_EXPIRE_WAIT)
+    with pytest.raises(d2.D2Error) as e:
+        ctx.device_errors()
+    assert e.value.code == d2.D2_ETIMEOUT
+    assert ctx.device_errors() == 0  # cleared by the read
+    _check_cost(d2, ctx, bags, co, mem, x0, "bf16x3")
