@@ -401,7 +401,8 @@ def pick_ids(bags, K, m, seed):
     Fisher-Yates over the ids with m_k >= m), for the plain-form replay."""
     M = (1 << 64) - 1
     sizes = (bags.offsets[1:] - bags.offsets[:-1]).cpu().tolist()
-    elig = [k for k, s_ in enumerate(sizes) if s_ >= m]
+    thr = min(m, sorted(sizes, reverse=True)[K - 1])
+    elig = [k for k, s_ in enumerate(sizes) if s_ >= thr]
     st = seed & M
     for t in range(K):
         st = (st + 0x9E3779B97F4A7C15) & M

@@ -333,7 +333,9 @@ int d2_merge_init(d2_ctx* ctx, const d2_bags* bags, const int64_t* ids, int64_t 
 
 /* D2-clustering (Algorithm 1 with the Section 5 choices), all on the device:
  * K distinct bags with m_k >= m chosen by a partial Fisher-Yates shuffle
- * driven by SplitMix64(seed) and reduced by Eq. (merge); then `rounds` rounds
+ * driven by SplitMix64(seed) and reduced by Eq. (merge) (when fewer than K
+ * bags have m points, the threshold drops to the K-th largest m_k and the
+ * picks are padded with zero-weight copies); then `rounds` rounds
  * of { d2_assign (with `prune` if non-NULL; else, with D2_ELKAN in
  * opts->flags, Elkan's triangle-inequality skipping of Section 5 with the
  * metric W = sqrt(W^2): lower bounds per (bag, centroid) carried across

@@ -36,10 +36,17 @@ def splitmix64(state):
 
 
 def init_pick(sizes, K, m, seed):
-    """Ids of the K members whose merged supports seed the centroids."""
-    eligible = [k for k, s in enumerate(sizes) if s >= m]
-    if len(eligible) < K:
-        raise ValueError("fewer than K distributions have at least m support points")
+    """Ids of the K members whose merged supports seed the centroids.
+
+    Eligible: the ids with m_k >= m (the merge of Eq. (merge) then reduces each
+    to m points).  The paper leaves the case of fewer than K such members
+    open; the reading taken is to lower the threshold to the K-th largest m_k,
+    so the K picks are drawn among the largest distributions (those with fewer
+    than m points are later padded with zero-weight copies)."""
+    if K > len(sizes):
+        raise ValueError("fewer than K distributions")
+    thr = min(m, sorted(sizes, reverse=True)[K - 1])
+    eligible = [k for k, s in enumerate(sizes) if s >= thr]
     state = seed & MASK64
     E = len(eligible)
     for t in range(K):
@@ -47,6 +54,17 @@ def init_pick(sizes, K, m, seed):
         j = t + int(z % (E - t))
         eligible[t], eligible[j] = eligible[j], eligible[t]
     return eligible[:K]
+
+
+def pad_support(x, w, m):
+    """A centroid seeded by a distribution with fewer than m points keeps m
+    support points: the missing ones are zero-weight copies of its last point
+    (reading taken where the paper assumes m_k >= m)."""
+    q = x.shape[0]
+    if q >= m:
+        return x, w
+    return (np.vstack([x, np.repeat(x[-1:], m - q, axis=0)]),
+            np.concatenate([w, np.zeros(m - q)]))
 
 
 def d2_assign(bags_list, cents):
@@ -75,7 +93,7 @@ def d2_cluster(bags_list, K, m, seed, rounds, *, rho0=2.0, T=100, tau=10, eps=1e
     """
     sizes = [y.shape[0] for y, _ in bags_list]
     picks = init_pick(sizes, K, m, seed)
-    cents = [merge_reduce(bags_list[k][0], bags_list[k][1], m) for k in picks]
+    cents = [pad_support(*merge_reduce(bags_list[k][0], bags_list[k][1], m), m) for k in picks]
     N = len(bags_list)
     prev_labels = None
     cache = [None] * N

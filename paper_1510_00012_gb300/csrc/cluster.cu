@@ -4,6 +4,8 @@
 #include <cstring>
 #include <vector>
 
+#include <functional>
+
 #include "d2_internal.cuh"
 
 struct AssignArgs;
@@ -266,16 +268,21 @@ extern "C" int d2_cluster(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m
     cudaStream_t st = d2_stream(stream);
     const int64_t N = bags->N, n = bags->n;
 
-    // seeded pick: partial Fisher-Yates over the ids with m_k >= m (ascending)
+    // seeded pick: partial Fisher-Yates over the ids with m_k >= min(m, the
+    // K-th largest m_k) in ascending order (with fewer than K distributions of
+    // m points, the largest ones seed the centroids and are padded by the merge)
+    if (K > N) return d2_fail(ctx, D2_EINVAL, "d2_cluster: K = %d exceeds N = %lld", K, (long long)N);
     std::vector<int64_t> off(N + 1);
     D2_CK(ctx, cudaMemcpyAsync(off.data(), bags->offsets, (N + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     D2_CK(ctx, cudaStreamSynchronize(st));
+    std::vector<int64_t> sz(N);
+    for (int64_t k = 0; k < N; ++k) sz[k] = off[k + 1] - off[k];
+    std::vector<int64_t> srt(sz);
+    std::nth_element(srt.begin(), srt.begin() + (K - 1), srt.end(), std::greater<int64_t>());
+    const int64_t thr = std::min<int64_t>(m, srt[K - 1]);
     std::vector<int64_t> elig;
     for (int64_t k = 0; k < N; ++k)
-        if (off[k + 1] - off[k] >= m) elig.push_back(k);
-    if ((int64_t)elig.size() < K)
-        return d2_fail(ctx, D2_EINVAL, "d2_cluster: only %zu distributions have m_k >= m = %d (K = %d)",
-                       elig.size(), m, K);
+        if (sz[k] >= thr) elig.push_back(k);
     uint64_t state = seed;
     const uint64_t E = elig.size();
     for (int t = 0; t < K; ++t) {

@@ -115,6 +115,22 @@ def test_d2_cluster_matches_oracle(d2, ctx):
     np.testing.assert_allclose(x.cpu().double().numpy(), ref["x"], atol=2e-4 * (1 + np.abs(ref["x"]).max()))
 
 
+def test_d2_cluster_with_m_above_every_bag(d2, ctx):
+    """m larger than every m_k (the document workload has m = 64 > 60): the
+    largest bags seed the centroids, padded with zero-weight copies."""
+    bags = synth.gaussian_class_bags(33, 60, 3, 3, mk=(2, 7), mu_sigma=4.0, alpha=1.0)
+    db = d2.DeviceBags.from_synth(bags)
+    K, m, rounds, T = 3, 9, 2, 15
+    x, w, labels, objs = d2.d2_cluster(ctx, db, K, m, seed=78, rounds=rounds,
+                                       opts=d2.badmm_opts(iters=T, tau=10))
+    members = [bags.bag(k) for k in range(bags.N)]
+    ref = oracle_cluster(members, K, m, seed=78, rounds=rounds, T=T, tau=10)
+    np.testing.assert_array_equal(labels.cpu().numpy(), ref["labels"])
+    for r in range(rounds):
+        assert abs(objs[r] - ref["obj_per_round"][r]) <= 1e-4 * ref["obj_per_round"][r]
+    np.testing.assert_allclose(w.cpu().double().numpy(), ref["w"], atol=1e-5, rtol=0)
+
+
 def test_d2_cluster_m1_is_kmeans_on_means(d2, ctx):
     bags = synth.gaussian_class_bags(32, 120, 3, 4, mk=(1, 8), mu_sigma=3.0)
     db = d2.DeviceBags.from_synth(bags)

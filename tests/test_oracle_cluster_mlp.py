@@ -164,3 +164,17 @@ def test_prune_assign_exact_when_margin_holds_and_falls_back():
     lab, b, fb, n = mlp.prune_assign_one(np.array([0.4, 1.1, 3.5, 1.5]), np.array([0.1, 0.2, 2.0, 0.1]),
                                          lambda i: exact[i], r=2, delta=1.0)
     assert (lab, b, fb, n) == (3, 0.5, True, 4)
+
+
+def test_init_pick_falls_back_to_the_largest():
+    """With fewer than K distributions of m points, the picks are the largest
+    distributions (threshold = the K-th largest m_k), distinct, seeded; with
+    enough of them the threshold is m itself."""
+    sizes = [3, 9, 5, 9, 2, 7, 8, 4, 6, 9]
+    for seed in range(20):
+        p = init_pick(sizes, 4, 12, seed)          # nobody has 12 points
+        assert len(set(p)) == 4 and all(sizes[k] >= 8 for k in p)   # 4th largest size is 8
+        q = init_pick(sizes, 3, 6, seed)           # 7 bags have >= 6 points
+        assert len(set(q)) == 3 and all(sizes[k] >= 6 for k in q)
+    # the fallback threshold equals m when exactly K bags qualify
+    assert sorted(init_pick(sizes, 3, 9, 1)) == [1, 3, 9]
