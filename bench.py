@@ -335,13 +335,15 @@ DOCS_WORKLOAD = dict(N=200_000, V=50_000, d=300, mk=(10, 60), K=64, m=64, rounds
                           "tensor-core cost build")
 
 
-def docs_clustering(d2, ctx, dev, seed):
+def docs_clustering(d2, ctx, dev, seed, n_docs=None):
     """D2-clustering of the document-like workload with the tensor-core cost
     build: seconds per round with the learned pruner (trained on 100k exact
     W^2 pairs against the merge-initialised centroids) and the B-ADMM share of
     a round; the exact full-K assignment of the plain form is timed on a
     sample of bags and scaled to all N (its full run takes minutes)."""
-    W = DOCS_WORKLOAD
+    W = dict(DOCS_WORKLOAD)
+    if n_docs:
+        W["N"] = n_docs
     K, m, R = W["K"], W["m"], W["rounds"]
 
     def timed(fn):
@@ -354,7 +356,7 @@ def docs_clustering(d2, ctx, dev, seed):
     bags, t_gen = timed(lambda: synth.document_bags(seed, W["N"], V=W["V"], d=W["d"], mk=W["mk"], device=dev))
     db = d2.DeviceBags(bags.offsets, bags.wt, bags.d, vocab_idx=bags.vocab_idx, vocab=bags.vocab)
     opts = d2.badmm_opts(iters=W["iters"], tau=W["tau"], cost="bf16x3")
-    out = {"workload": W["desc"], "N": bags.N, "support_rows": bags.n, "generate_s": t_gen}
+    out = {"workload": W["desc"] if not n_docs else W["desc"] + " (N=%d)" % n_docs, "N": bags.N, "support_rows": bags.n, "generate_s": t_gen}
     # centroids of Algorithm 1's initialisation, for the pruner's training pairs
     x0, w0 = d2.d2_merge_init(ctx, db, torch.tensor(pick_ids(bags, K, m, 11), device=dev), m)
     g = torch.Generator(device=dev).manual_seed(seed + 5)
@@ -373,9 +375,19 @@ def docs_clustering(d2, ctx, dev, seed):
     d2.d2_assign(ctx, dsub, x0, w0)
     (le, _), t_ex = timed(lambda: d2.d2_assign(ctx, dsub, x0, w0))
     (lp, _, st), t_pr = timed(lambda: d2.d2_assign(ctx, dsub, x0, w0, prune=pr, want_stats=True))
-    # pruned D2-clustering, all rounds, timed as one call
-    (xq, wq, lq, oq), t_cl = timed(lambda: d2.d2_cluster(ctx, db, K, m, 11, R, opts, prune=pr))
+    (lbd, _, stb), t_bd = timed(lambda: d2.d2_assign(ctx, dsub, x0, w0, want_stats=True, bounded=True))
+    # D2-clustering, all rounds, timed as one call: exact assignment by
+    # certified bounds (d2_assign_bounded), without and with the pruner's
+    # candidates solved first
+    bopts = d2.badmm_opts(iters=W["iters"], tau=W["tau"], cost="bf16x3", assign_bounded=True)
+    (xq, wq, lq, oq), t_cl = timed(lambda: d2.d2_cluster(ctx, db, K, m, 11, R, bopts))
     cs = ctx.cluster_stats()
+    (xr, wr, lr_, orr), t_cp = timed(lambda: d2.d2_cluster(ctx, db, K, m, 11, R, bopts, prune=pr))
+    csp = ctx.cluster_stats()
+    out.update({"bounded_s_per_round": t_cl / R, "bounded_exact_solves": cs["exact_solves"],
+                "bounded_pruned_s_per_round": t_cp / R, "bounded_pruned_exact_solves": csp["exact_solves"],
+                "labels_equal_bounded_vs_bounded_pruned": bool(torch.equal(lq, lr_)),
+                "obj_per_round": oq})
     # one B-ADMM update of all clusters at the final labels (the update step of a round)
     order = torch.sort(lq.long(), stable=True).indices
     co = torch.zeros(K + 1, dtype=torch.int64, device=dev)
@@ -384,16 +396,177 @@ def docs_clustering(d2, ctx, dev, seed):
     d2.badmm_barycenter(ctx, db, co, order.contiguous(), xb, wb, None, None, opts)
     xb, wb = xq.clone(), wq.clone()
     _, t_b = timed(lambda: d2.badmm_barycenter(ctx, db, co, order.contiguous(), xb, wb, None, None, opts))
-    out.update({"pruned_s_per_round": t_cl / R, "obj_per_round": oq,
-                "badmm_update_s": t_b, "badmm_updates_per_s": m * bags.n * W["iters"] / t_b,
-                "exact_solves": cs["exact_solves"], "fallbacks": cs["fallbacks"],
+    out.update({"badmm_update_s": t_b, "badmm_updates_per_s": m * bags.n * W["iters"] / t_b,
                 "full_K_solves_per_round": bags.N * K,
                 "pruner": {"r": 8, "delta": delta, "train_pairs": npairs, "target_s": t_tg, "train_s": t_train,
                            "sample_bags": ns, "misassignment_vs_exact_on_sample": float((lp != le).float().mean()),
                            "sample_exact_solves": st["exact_solves"], "sample_fallbacks": st["fallbacks"]},
                 "exact_pairs_per_s": ns * K / t_ex,
+                "sample_bounded": {"s": t_bd, "full_K_s": t_ex, "exact_solves": stb["exact_solves"],
+                                   "labels_equal_full_K": bool(torch.equal(lbd, le))},
                 "plain_assign_s_per_round_est": bags.N * K / (ns * K / t_ex)})
     return out
+
+
+def grouped_resident(d2, dev, bags, co, x0, w0, W, T, entries, steps, groups, cost, dist, world):
+    """The same step with inputs resident in HBM, issued as `groups` cluster
+    groups of about equal support rows round-robin on two streams (one
+    context each): independent clusters, so the groups' launches overlap each
+    other's tails and the HBM-bound sweeps overlap the cost builds."""
+    K, m, d = W["clusters"], W["m"], W["d"]
+    off = bags.offsets
+    n = bags.n
+    rows_at = off[co].cpu()
+    cuts = [0] + [int(torch.searchsorted(rows_at, torch.tensor(n * g // groups))) for g in range(1, groups)] + [K]
+    cuts = sorted(set(cuts))
+    co_h = co.cpu()
+    off_h = off.cpu()
+    x = torch.empty_like(x0)
+    w = torch.empty_like(w0)
+    obj = torch.empty(K, dtype=torch.float64, device=dev)
+    plan = torch.empty(n, m, dtype=torch.float32, device=dev)
+    parts = []
+    for c0, c1 in zip(cuts[:-1], cuts[1:]):
+        b0, b1 = int(co_h[c0]), int(co_h[c1])
+        r0, r1 = int(off_h[b0]), int(off_h[b1])
+        gb = d2.DeviceBags((off[b0:b1 + 1] - r0).contiguous(), bags.wt[r0:r1], d, supp=bags.supp[r0:r1],
+                           max_mk=W["mk"][1])
+        parts.append(dict(c0=c0, c1=c1, r0=r0, r1=r1, bags=gb, co=(co[c0:c1 + 1] - b0).contiguous(),
+                          mem=torch.arange(b1 - b0, dtype=torch.int64, device=dev)))
+    slots = [dict(stream=torch.cuda.Stream(device=dev), ctx=d2.Context(dev.index)) for _ in range(2)]
+    opts = d2.badmm_opts(iters=T, tau=W["tau"], cost=cost, graph=False)
+
+    def one_step():
+        for gi, p in enumerate(parts):
+            sl = slots[gi % 2]
+            with torch.cuda.stream(sl["stream"]):
+                xg, wg = x[p["c0"]:p["c1"]], w[p["c0"]:p["c1"]]
+                xg.copy_(x0[p["c0"]:p["c1"]])
+                wg.copy_(w0[p["c0"]:p["c1"]])
+                d2.badmm_barycenter(sl["ctx"], p["bags"], p["co"], p["mem"], xg, wg, plan[p["r0"]:p["r1"]], None,
+                                    opts, obj[p["c0"]:p["c1"]])
+
+    main = torch.cuda.current_stream(dev)
+    for sl in slots:
+        sl["stream"].wait_stream(main)
+    one_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(main)
+    for sl in slots:
+        sl["stream"].wait_event(e0)
+    for _ in range(steps):
+        one_step()
+    for sl in slots:
+        ev = torch.cuda.Event()
+        ev.record(sl["stream"])
+        main.wait_event(ev)
+    e1.record(main)
+    torch.cuda.synchronize()
+    assert torch.isfinite(obj).all()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev) / steps
+    for sl in slots:
+        sl["ctx"].close()
+    del plan
+    return {"value": job_rate(entries, T, world, ms), "ms_per_step": ms, "groups": len(parts), "steps": steps}
+
+
+def e2e_pipelined(d2, dev, h, W, T, entries, steps, groups, cost, dist, world):
+    """End to end through the public API from pinned host buffers: every step
+    copies its inputs host -> device (offsets, weights, supports, clustering,
+    initial barycenters), runs badmm_barycenter and copies x, w and the
+    objectives back.  The clusters are split into `groups` groups of about
+    equal support rows, issued round-robin on two streams, each with its own
+    context and device buffers, so the copies of group g+1 overlap the B-ADMM
+    update of group g (clusters are independent in the update step)."""
+    co_h, off_h = h["co"], h["offsets"]
+    K, m, d = W["clusters"], W["m"], W["d"]
+    n = int(off_h[-1])
+    rows_at = off_h[co_h]                       # first support row of each cluster (K+1)
+    cuts = [0]
+    for g in range(1, groups):
+        cuts.append(int(torch.searchsorted(rows_at, torch.tensor(n * g // groups))))
+    cuts.append(K)
+    cuts = sorted(set(cuts))
+    parts = []
+    for c0, c1 in zip(cuts[:-1], cuts[1:]):
+        b0, b1 = int(co_h[c0]), int(co_h[c1])
+        r0, r1 = int(off_h[b0]), int(off_h[b1])
+        parts.append(dict(c0=c0, c1=c1, b0=b0, b1=b1, r0=r0, r1=r1,
+                          off=(off_h[b0:b1 + 1] - r0).pin_memory(),
+                          co=(co_h[c0:c1 + 1] - b0).pin_memory(),
+                          mem=torch.arange(b1 - b0, dtype=torch.int64).pin_memory()))
+    out_x = torch.empty_like(h["x0"]).pin_memory()
+    out_w = torch.empty_like(h["w0"]).pin_memory()
+    out_o = torch.empty(K, dtype=torch.float64).pin_memory()
+    nb_max = max(p["b1"] - p["b0"] for p in parts)
+    nr_max = max(p["r1"] - p["r0"] for p in parts)
+    nc_max = max(p["c1"] - p["c0"] for p in parts)
+    slots = []
+    for _ in range(2):
+        slots.append(dict(stream=torch.cuda.Stream(device=dev), ctx=d2.Context(dev.index),
+                          off=torch.empty(nb_max + 1, dtype=torch.int64, device=dev),
+                          wt=torch.empty(nr_max, dtype=torch.float32, device=dev),
+                          supp=torch.empty(nr_max, d, dtype=torch.float32, device=dev),
+                          co=torch.empty(nc_max + 1, dtype=torch.int64, device=dev),
+                          mem=torch.empty(nb_max, dtype=torch.int64, device=dev),
+                          x=torch.empty(nc_max, m, d, dtype=torch.float32, device=dev),
+                          w=torch.empty(nc_max, m, dtype=torch.float32, device=dev),
+                          plan=torch.empty(nr_max, m, dtype=torch.float32, device=dev),
+                          obj=torch.empty(nc_max, dtype=torch.float64, device=dev)))
+    opts = d2.badmm_opts(iters=T, tau=W["tau"], cost=cost, graph=False)
+    bi = sum(t.numel() * t.element_size() for t in h.values())
+    bo = sum(t.numel() * t.element_size() for t in (out_x, out_w, out_o))
+
+    def one_step():
+        for gi, p in enumerate(parts):
+            sl = slots[gi % 2]
+            nb, nr, nc = p["b1"] - p["b0"], p["r1"] - p["r0"], p["c1"] - p["c0"]
+            with torch.cuda.stream(sl["stream"]):
+                off, wt, supp = sl["off"][:nb + 1], sl["wt"][:nr], sl["supp"][:nr]
+                cog, memg = sl["co"][:nc + 1], sl["mem"][:nb]
+                x, w, obj = sl["x"][:nc], sl["w"][:nc], sl["obj"][:nc]
+                off.copy_(p["off"], non_blocking=True)
+                wt.copy_(h["wt"][p["r0"]:p["r1"]], non_blocking=True)
+                supp.copy_(h["supp"][p["r0"]:p["r1"]], non_blocking=True)
+                cog.copy_(p["co"], non_blocking=True)
+                memg.copy_(p["mem"], non_blocking=True)
+                x.copy_(h["x0"][p["c0"]:p["c1"]], non_blocking=True)
+                w.copy_(h["w0"][p["c0"]:p["c1"]], non_blocking=True)
+                eb = d2.DeviceBags(off, wt, d, supp=supp, max_mk=W["mk"][1])
+                d2.badmm_barycenter(sl["ctx"], eb, cog, memg, x, w, sl["plan"][:nr], None, opts, obj)
+                out_x[p["c0"]:p["c1"]].copy_(x, non_blocking=True)
+                out_w[p["c0"]:p["c1"]].copy_(w, non_blocking=True)
+                out_o[p["c0"]:p["c1"]].copy_(obj, non_blocking=True)
+
+    one_step()  # untimed: workspaces grow to their sizes
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    main = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(main)
+    for sl in slots:
+        sl["stream"].wait_event(e0)
+    for _ in range(steps):
+        one_step()
+    for sl in slots:
+        ev = torch.cuda.Event()
+        ev.record(sl["stream"])
+        main.wait_event(ev)
+    e1.record(main)
+    torch.cuda.synchronize()
+    assert torch.isfinite(out_o).all()
+    e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    e_step = e_ms / steps
+    for sl in slots:
+        sl["ctx"].close()
+    return {"value": job_rate(entries, T, world, e_step), "unit": UNIT, "ms_per_step": e_step, "steps": steps,
+            "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "groups": len(parts),
+            "pipeline": "%d cluster groups round-robin on 2 streams, one context each; the host->device "
+                        "copies of a group overlap the B-ADMM update of the previous one" % len(parts)}
 
 
 def pick_ids(bags, K, m, seed):
@@ -476,17 +649,20 @@ def main():
     ap.add_argument("--workload", default="ragged4096", choices=sorted(WORKLOADS))
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-groups", type=int, default=8, help="cluster groups pipelined in the e2e run")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-d2", action="store_true", help="skip the D2-clustering s/round comparison")
     ap.add_argument("--pruning", action="store_true", help="also run the learned-pruning assignment at scale")
+    ap.add_argument("--docs-n", type=int, default=None, help="document count of --docs (default 200,000)")
     ap.add_argument("--docs", action="store_true",
                     help="also run D2-clustering of the 200k document-like bags (d=300, K=64, m=64)")
     ap.add_argument("--cost", default="bf16x3", choices=["fp32", "bf16", "bf16x3", "bf16x6"],
                     help="cost-build precision (bf16*: tensor cores)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default sweep launch shape")
+    ap.add_argument("--no-grouped", action="store_true", help="skip the grouped two-stream measurement")
     ap.add_argument("--no-cost-variants", action="store_true",
                     help="skip the timing of the other cost-build precisions")
     args = ap.parse_args()
@@ -540,7 +716,6 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler.start()
     time.sleep(0.3)
-    ctx.timing(True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -554,11 +729,16 @@ def main():
         dist.barrier()
     launches = ctx.launch_count() - l0
     clocks = sampler.stop()
-    kt = ctx.timing_read()
-    ctx.timing(False)
     ms_total = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     ms_step = ms_total / args.steps
     value = job_rate(entries, T, world, ms_step)
+    # one more step with per-launch CUDA events for the kernel split and rooflines
+    ctx.timing(True)
+    step()
+    torch.cuda.synchronize()
+    kt = ctx.timing_read()
+    ctx.timing(False)
+    kt_steps = 1
 
     # roofline of the dominant kernel (the fused plan sweep)
     f_ms, f_n = kt["sweep_fused"]
@@ -580,9 +760,8 @@ def main():
                 "traffic": None if tpe is None else tpe * entries,
                 "algorithmic_bytes_per_launch": BYTES_PER_ENTRY * entries,
                 "avg_launch_ms": f_ms / f_n, "launches": f_n,
-                "share_of_step": f_ms / max(ms_total, 1e-9)}
-    breakdown = {k: {"ms": v[0] / args.steps, "launches": v[1] // max(args.steps, 1)} for k, v in kt.items()
-                 if v[1]}
+                "share_of_step": f_ms / kt_steps / max(ms_step, 1e-9)}
+    breakdown = {k: {"ms": v[0] / kt_steps, "launches": v[1] // kt_steps} for k, v in kt.items() if v[1]}
     # the cost build (tensor cores for d >= 32): HBM roofline of its launches
     c_ms, c_n = kt["cost"]
     cost_roof = None
@@ -593,6 +772,11 @@ def main():
                      if args.cost != "fp32" else "k_cost_pipe<32>", "precision": args.cost,
                      "achieved": c_ach, "peak": peak, "unit": "GB/s", "frac": c_ach / peak,
                      "algorithmic_bytes_per_launch": cbytes, "avg_launch_ms": c_ms / c_n}
+
+    grouped = None
+    if not args.no_grouped:
+        grouped = grouped_resident(d2, dev, bags, co, x0, w0, W, T, entries, max(2, args.steps // 2),
+                                   args.e2e_groups, args.cost, dist, world)
 
     # the same step with the other cost-build precisions (fewer steps)
     variants = None
@@ -629,40 +813,9 @@ def main():
         h = {k: t.cpu().pin_memory() for k, t in (("offsets", bags.offsets), ("wt", bags.wt),
                                                   ("supp", bags.supp), ("co", co), ("mem", mem),
                                                   ("x0", x0), ("w0", w0))}
-        out_x = torch.empty_like(x, device="cpu").pin_memory()
-        out_w = torch.empty_like(w, device="cpu").pin_memory()
-        out_o = torch.empty_like(obj, device="cpu").pin_memory()
-        d_off, d_wt, d_supp = torch.empty_like(bags.offsets), torch.empty_like(bags.wt), torch.empty_like(bags.supp)
-        d_co, d_mem = torch.empty_like(co), torch.empty_like(mem)
-        bi = sum(t.numel() * t.element_size() for t in h.values())
-        bo = sum(t.numel() * t.element_size() for t in (out_x, out_w, out_o))
-        del bags, db
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        for it in range(1 + args.e2e_steps):  # one untimed step first (graph capture on new buffers)
-            if it == 1:
-                torch.cuda.synchronize()
-                e0.record(stream)
-            d_off.copy_(h["offsets"], non_blocking=True)
-            d_wt.copy_(h["wt"], non_blocking=True)
-            d_supp.copy_(h["supp"], non_blocking=True)
-            d_co.copy_(h["co"], non_blocking=True)
-            d_mem.copy_(h["mem"], non_blocking=True)
-            x.copy_(h["x0"], non_blocking=True)
-            w.copy_(h["w0"], non_blocking=True)
-            eb = d2.DeviceBags(d_off, d_wt, W["d"], supp=d_supp, max_mk=W["mk"][1])
-            d2.badmm_barycenter(ctx, eb, d_co, d_mem, x, w, plan, None, opts, obj)
-            out_x.copy_(x, non_blocking=True)
-            out_w.copy_(w, non_blocking=True)
-            out_o.copy_(obj, non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
-        e_step = e_ms / args.e2e_steps
-        e2e = {"value": job_rate(entries, T, world, e_step), "unit": UNIT, "ms_per_step": e_step,
-               "steps": args.e2e_steps, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+        del bags, db, plan
+        torch.cuda.empty_cache()
+        e2e = e2e_pipelined(d2, dev, h, W, T, entries, args.e2e_steps, args.e2e_groups, args.cost, dist, world)
 
     d2cmp = None
     if rank == 0 and not args.no_d2:
@@ -681,7 +834,7 @@ def main():
     docs_res = None
     if rank == 0 and args.docs:
         try:
-            docs_res = docs_clustering(d2, ctx, dev, args.seed + 41)
+            docs_res = docs_clustering(d2, ctx, dev, args.seed + 41, args.docs_n)
         except Exception as exc:
             docs_res = {"error": repr(exc)}
 
@@ -700,7 +853,7 @@ def main():
                            % (12 * entries / 1e9),
                            "parallelism": "independent problem per GPU" if world > 1 else "single GPU"},
                 "roofline": roof, "cost_roofline": cost_roof, "cost_variants": variants,
-                "sweep_autotune": ctx.sweep_tuning(m),
+                "sweep_autotune": ctx.sweep_tuning(m), "grouped_two_streams": grouped,
                 "kernel_breakdown_ms_per_step": breakdown, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "d2_round": d2cmp}
         if prune_res is not None:

@@ -58,6 +58,7 @@ extern "C" {
                              shared-memory pipelined one (both compute the same)  */
 #define D2_ELKAN     0x20 /* d2_cluster: skip assignment pairs by the triangle
                              inequality of W (Section 5), when no pruner is given */
+#define D2_ASSIGN_BOUNDED 0x200 /* d2_cluster: each round's assignment by d2_assign_bounded */
 #define D2_AUTOTUNE  0x100 /* badmm_barycenter: choose the plan sweep's launch shape
                              for this plan width m by timing candidates (see
                              d2_sweep_tuning); kept in the context for later calls */
@@ -297,6 +298,21 @@ int d2_assign(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,
               const float* x, const float* w, const d2_prune* prune,
               int32_t* labels, float* dist, int64_t* stats, void* stream);
 
+/* Assignment step of Algorithm 1 with the same result as d2_assign without a
+ * pruner (exact argmin of W^2, ties -> lowest i), solving far fewer LPs.  For
+ * every (bag, centroid) pair it computes a certified lower bound on W^2:
+ * the larger of the two one-sided relaxations of the LP of Eq. (primal)
+ * (each bag point ships its mass to its nearest centroid point, and the
+ * reverse) and ||mu_P - mu_Q||^2 (Jensen).  It solves each bag's r
+ * smallest-bound centroids exactly (r = 2, or the pruner's r candidates when
+ * `prune` is given), then every other centroid whose bound does not exceed
+ * the best value found times (1 + 1e-4) (covering FP32 rounding).  Requires
+ * max_mk <= 128 and the conditions of d2_assign.  stats: as for d2_assign
+ * (fall-backs stay 0). */
+int d2_assign_bounded(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,
+                      const float* x, const float* w, const d2_prune* prune,
+                      int32_t* labels, float* dist, int64_t* stats, void* stream);
+
 /* Exact W^2 (Eq. primal, the same solver as d2_assign) for an explicit list
  * of npairs (bag pair_bag[p], centroid pair_cent[p]) -> out[p] (device
  * floats).  Used to produce training targets for the pruner. */
@@ -340,7 +356,8 @@ int d2_merge_init(d2_ctx* ctx, const d2_bags* bags, const int64_t* ids, int64_t 
  * opts->flags, Elkan's triangle-inequality skipping of Section 5 with the
  * metric W = sqrt(W^2): lower bounds per (bag, centroid) carried across
  * rounds and lowered by the centroid shifts, centroid-centroid distances,
- * and an exact distance to each bag's current centroid every round);
+ * and an exact distance to each bag's current centroid every round; with
+ * D2_ASSIGN_BOUNDED, d2_assign_bounded, which also takes `prune`);
  * badmm_barycenter over all K clusters, warm-starting Pi^(k,2) of every bag
  * whose label is unchanged }.
  *   x_out, w_out, labels_out : device, K x m x d, K x m, N

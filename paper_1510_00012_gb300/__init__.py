@@ -24,6 +24,7 @@ D2_RULE_R1, D2_RULE_R2 = 1, 2
 D2_FIX_X, D2_FIX_W, D2_VALIDATE, D2_NO_GRAPH, D2_NO_PIPE, D2_ELKAN = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
 D2_COST_BF16, D2_COST_BF16X3, D2_COST_BF16X6 = 0x40, 0x80, 0xC0
 D2_AUTOTUNE = 0x100
+D2_ASSIGN_BOUNDED = 0x200
 D2_TEST_EXPIRE_WAIT = 0x8000
 D2_TUNE_MAX = 16
 COST_PRECISION = {"fp32": 0, "bf16": D2_COST_BF16, "bf16x3": D2_COST_BF16X3, "bf16x6": D2_COST_BF16X6}
@@ -67,6 +68,8 @@ _SIGS = {
                                  c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "d2_assign": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
                           c_void_p, c_void_p, c_void_p, c_void_p]),
+    "d2_assign_bounded": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
+                                  c_void_p, c_void_p, c_void_p, c_void_p]),
     "d2_assign_noalloc": (c_int, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "d2_w2_pairs": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                             c_int64, c_void_p, c_void_p]),
@@ -240,7 +243,8 @@ def _cost_flag(precision):
 
 
 def badmm_opts(rho0=2.0, iters=100, tau=10, eps=1e-16, rule="R1", fix_x=False, fix_w=False,
-               validate=False, rho=0.0, graph=True, elkan=False, cost="fp32", autotune=False):
+               validate=False, rho=0.0, graph=True, elkan=False, cost="fp32", autotune=False,
+               assign_bounded=False):
     """d2_badmm_opts; cost = "fp32" | "bf16" | "bf16x3" | "bf16x6" selects the cost build."""
     o = _Opts()
     lib().d2_badmm_opts_default(ctypes.byref(o))
@@ -248,7 +252,7 @@ def badmm_opts(rho0=2.0, iters=100, tau=10, eps=1e-16, rule="R1", fix_x=False, f
     o.rule = D2_RULE_R2 if rule == "R2" else D2_RULE_R1
     o.flags = ((D2_FIX_X if fix_x else 0) | (D2_FIX_W if fix_w else 0) | (D2_VALIDATE if validate else 0)
                | (0 if graph else D2_NO_GRAPH) | (D2_ELKAN if elkan else 0) | _cost_flag(cost)
-               | (D2_AUTOTUNE if autotune else 0))
+               | (D2_AUTOTUNE if autotune else 0) | (D2_ASSIGN_BOUNDED if assign_bounded else 0))
     return o
 
 
@@ -308,17 +312,18 @@ def d2_merge_init(ctx, bags, ids, m):
     return x, w
 
 
-def d2_assign(ctx, bags, x, w, prune=None, want_stats=False):
-    """Exact (or pruned) assignment: labels (N int32), W^2 to the chosen centroid (N float32)[, stats]."""
+def d2_assign(ctx, bags, x, w, prune=None, want_stats=False, bounded=False):
+    """Exact (or pruned) assignment: labels (N int32), W^2 to the chosen centroid (N float32)[, stats].
+    bounded=True calls d2_assign_bounded (same result, certified lower bounds skip most LPs)."""
     _need(x, torch.float32, "x")
     _need(w, torch.float32, "w")
     K, m = x.shape[0], x.shape[1]
     labels = torch.empty(bags.N, dtype=torch.int32, device=x.device)
     dist = torch.empty(bags.N, dtype=torch.float32, device=x.device)
     st = (c_int64 * 3)() if want_stats else None
-    ctx.check(lib().d2_assign(ctx.h, bags.ref(), K, m, _ptr(x), _ptr(w),
-                              None if prune is None else c_void_p(prune.h), _ptr(labels), _ptr(dist),
-                              st, _stream()))
+    fn = lib().d2_assign_bounded if bounded else lib().d2_assign
+    ctx.check(fn(ctx.h, bags.ref(), K, m, _ptr(x), _ptr(w),
+                 None if prune is None else c_void_p(prune.h), _ptr(labels), _ptr(dist), st, _stream()))
     if want_stats:
         return labels, dist, dict(exact_solves=st[0], fallbacks=st[1], limit_hits=st[2])
     return labels, dist

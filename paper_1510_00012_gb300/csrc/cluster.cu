@@ -222,8 +222,28 @@ __global__ void k_mean_dist(const float* dist, int64_t N, double* out) {
 // d2_assign
 // ---------------------------------------------------------------------------
 
+int d2_assign_bounded_impl(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w,
+                           const d2_prune* prune, int r_first, int32_t* labels, float* dist, int64_t* counters,
+                           cudaStream_t st);
+
+static int assign_any(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, const float* x, const float* w,
+                      const d2_prune* prune, bool bounded, int32_t* labels, float* dist, int64_t* stats,
+                      void* stream);
+
 extern "C" int d2_assign(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, const float* x, const float* w,
                          const d2_prune* prune, int32_t* labels, float* dist, int64_t* stats, void* stream) {
+    return assign_any(ctx, bags, K, m, x, w, prune, false, labels, dist, stats, stream);
+}
+
+extern "C" int d2_assign_bounded(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, const float* x,
+                                 const float* w, const d2_prune* prune, int32_t* labels, float* dist,
+                                 int64_t* stats, void* stream) {
+    return assign_any(ctx, bags, K, m, x, w, prune, true, labels, dist, stats, stream);
+}
+
+static int assign_any(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, const float* x, const float* w,
+                      const d2_prune* prune, bool bounded, int32_t* labels, float* dist, int64_t* stats,
+                      void* stream) {
     if (!ctx) return D2_EINVAL;
     int rc = d2_check_bags_host(ctx, bags);
     if (rc) return rc;
@@ -235,8 +255,16 @@ extern "C" int d2_assign(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,
     if ((rc = d2_ws(ctx, WS_SCAN, 64, &sc))) return rc;
     int64_t* counters = static_cast<int64_t*>(sc);  // [0] exact solves, [1] fall-backs, [2] limit hits
     D2_CK(ctx, cudaMemsetAsync(counters, 0, 3 * sizeof(int64_t), st));
-    if (prune) rc = d2_assign_pruned(ctx, bags, K, m, x, w, prune, labels, dist, counters, st);
-    else rc = d2_assign_exact(ctx, bags, K, m, x, w, labels, dist, counters, st);
+    if (bounded) {
+        int32_t r = 2;
+        float delta = 0.f;
+        if (prune) d2_prune_get_margin(prune, &r, &delta);
+        rc = d2_assign_bounded_impl(ctx, bags, K, m, x, w, prune, r, labels, dist, counters, st);
+    } else if (prune) {
+        rc = d2_assign_pruned(ctx, bags, K, m, x, w, prune, labels, dist, counters, st);
+    } else {
+        rc = d2_assign_exact(ctx, bags, K, m, x, w, labels, dist, counters, st);
+    }
     if (rc) return rc;
     if (stats) {
         D2_CK(ctx, cudaMemcpyAsync(stats, counters, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -334,7 +362,7 @@ extern "C" int d2_cluster(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m
     d2_badmm_opts o;
     if (opts) o = *opts; else d2_badmm_opts_default(&o);
     o.flags &= ~D2_VALIDATE;
-    const bool elkan = (o.flags & D2_ELKAN) && !prune;
+    const bool elkan = (o.flags & D2_ELKAN) && !prune && !(o.flags & D2_ASSIGN_BOUNDED);
     const unsigned gN = (unsigned)d2_ceil_div(N, 256);
     D2_CK(ctx, cudaMemsetAsync(solves, 0, 3 * sizeof(int64_t), st));
     void* scnt = nullptr;
@@ -348,7 +376,9 @@ extern "C" int d2_cluster(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m
             D2_CK(ctx, cudaMemcpyAsync(x_prev, x_out, (size_t)K * m * bags->d * 4, cudaMemcpyDeviceToDevice, st));
             D2_CK(ctx, cudaMemcpyAsync(w_prev, w_out, (size_t)K * m * 4, cudaMemcpyDeviceToDevice, st));
         } else {
-            if ((rc = d2_assign(ctx, bags, K, m, x_out, w_out, prune, lab, dist, nullptr, stream))) return rc;
+            if ((rc = assign_any(ctx, bags, K, m, x_out, w_out, prune, (o.flags & D2_ASSIGN_BOUNDED) != 0, lab, dist,
+                                 nullptr, stream)))
+                return rc;
             k_acc_counts<<<1, 1, 0, st>>>(solves, acounters);
             D2_LAUNCH_CK(ctx, "k_acc_counts");
         }

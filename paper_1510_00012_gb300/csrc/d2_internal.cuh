@@ -141,6 +141,13 @@ __device__ __forceinline__ float group_max(float v) {
 }
 
 template <int W>
+__device__ __forceinline__ float group_min(float v) {
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <int W>
 __device__ __forceinline__ double group_sum_d(double v) {
 #pragma unroll
     for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -711,6 +711,46 @@ int d2_prune_solve_pairs(d2_ctx* ctx, const d2_bags* b, int K, int m, const floa
                          int64_t npairs, const int64_t* npairs_dev, const int32_t* cand, int r,
                          const int64_t* bag_list, float* out, int64_t* fail_count, cudaStream_t st);
 
+// The pruner's r candidates per bag (smallest What^2) into cand (N x r).
+int d2_prune_candidates(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w,
+                        const d2_prune* p, int r, int32_t* cand, cudaStream_t st) {
+    if (p->d != b->d) return d2_fail(ctx, D2_EINVAL, "d2_assign: pruner dimension %d != bag dimension %d", p->d, b->d);
+    if (r > 16) return d2_fail(ctx, D2_ENOTSUP, "d2_assign: r > 16");
+    const int64_t N = b->N;
+    const int d = p->d, E = p->E;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_fb = take(N * E * 4), o_mub = take(N * d * 4), o_fc = take((size_t)K * E * 4),
+                 o_muc = take((size_t)K * d * 4);
+    void* base = nullptr;
+    int rc = d2_ws(ctx, WS_PRUNE, off, &base);
+    if (rc) return rc;
+    char* bb = static_cast<char*>(base);
+    float* fb = reinterpret_cast<float*>(bb + o_fb);
+    float* mub = reinterpret_cast<float*>(bb + o_mub);
+    float* fc = reinterpret_cast<float*>(bb + o_fc);
+    float* muc = reinterpret_cast<float*>(bb + o_muc);
+    MlpArgs a = mlp_args(p, b, x, w, m);
+    a.nslots = N;
+    a.nbag_slots = N;
+    a.f = fb;
+    a.mu = mub;
+    if ((rc = launch_fwd(ctx, p, a, st))) return rc;
+    MlpArgs ac = mlp_args(p, b, x, w, m);
+    ac.nslots = K;
+    ac.nbag_slots = 0;
+    ac.f = fc;
+    ac.mu = muc;
+    if ((rc = launch_fwd(ctx, p, ac, st))) return rc;
+    k_topr<<<(unsigned)d2_ceil_div(N, 8), 256, 0, st>>>(N, K, E, d, r, fb, mub, fc, muc, cand);
+    D2_LAUNCH_CK(ctx, "k_topr");
+    return D2_OK;
+}
+
 int d2_assign_pruned(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w,
                      const d2_prune* p, int32_t* labels, float* dist, int64_t* counters, cudaStream_t st) {
     if (p->d != b->d) return d2_fail(ctx, D2_EINVAL, "d2_assign: pruner dimension %d != bag dimension %d", p->d, b->d);

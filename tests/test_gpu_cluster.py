@@ -159,3 +159,53 @@ def test_elkan_skipping_matches_exact_clustering(d2, ctx):
     assert torch.equal(x1, x2) and torch.equal(w1, w2)
     assert full["exact_solves"] == bags.N * K * rounds
     assert skip["exact_solves"] < full["exact_solves"]
+
+
+@pytest.mark.parametrize("case", ["dense", "vocab", "m_above"])
+def test_bounded_assignment_equals_full_exact(d2, ctx, case):
+    """d2_assign_bounded skips every LP whose certified lower bound exceeds the
+    best value found; its labels and distances equal the full N x K solve."""
+    if case == "dense":
+        bags = synth.gaussian_class_bags(61, 300, 16, 6, mk=(4, 40), mu_sigma=2.0)
+        K, m = 12, 16
+    elif case == "vocab":
+        bags = synth.document_bags(62, 200, V=300, d=48, mk=(8, 60))
+        K, m = 10, 24
+    else:
+        bags = synth.gaussian_class_bags(63, 150, 8, 4, mk=(2, 9), mu_sigma=3.0)
+        K, m = 7, 12
+    db = d2.DeviceBags.from_synth(bags)
+    g = torch.Generator().manual_seed(5)
+    ids = torch.randperm(bags.N, generator=g)[:K].cuda()
+    x, w = d2.d2_merge_init(ctx, db, ids, m)
+    lf, df_, sf = d2.d2_assign(ctx, db, x, w, want_stats=True)
+    lb, db_, sb = d2.d2_assign(ctx, db, x, w, want_stats=True, bounded=True)
+    assert torch.equal(lf, lb)
+    assert torch.equal(df_, db_)
+    assert sf["exact_solves"] == bags.N * K
+    assert sb["exact_solves"] < sf["exact_solves"]
+    print("%s: bounded solves %d of %d" % (case, sb["exact_solves"], sf["exact_solves"]))
+
+
+def test_bounded_assignment_with_pruner_candidates(d2, ctx):
+    bags = synth.gaussian_class_bags(64, 400, 8, 5, mk=(4, 30), mu_sigma=2.5)
+    db = d2.DeviceBags.from_synth(bags)
+    K, m = 8, 8
+    x, w = d2.d2_merge_init(ctx, db, torch.arange(K, device="cuda") * 7, m)
+    pr = d2.Pruner(ctx, 8, hidden=32, embed=16, seed=1)
+    pr.set_margin(3, 0.0)
+    lf, df_ = d2.d2_assign(ctx, db, x, w)
+    lb, db_, st = d2.d2_assign(ctx, db, x, w, prune=pr, want_stats=True, bounded=True)
+    assert torch.equal(lf, lb) and torch.equal(df_, db_)
+    assert st["exact_solves"] < bags.N * K
+
+
+def test_d2_cluster_bounded_assignment_matches_exact(d2, ctx):
+    bags = synth.gaussian_class_bags(65, 240, 6, 4, mk=(4, 20), mu_sigma=3.0)
+    db = d2.DeviceBags.from_synth(bags)
+    K, m, rounds = 4, 6, 3
+    a = d2.d2_cluster(ctx, db, K, m, seed=9, rounds=rounds, opts=d2.badmm_opts(iters=20))
+    b = d2.d2_cluster(ctx, db, K, m, seed=9, rounds=rounds, opts=d2.badmm_opts(iters=20, assign_bounded=True))
+    assert torch.equal(a[2], b[2])
+    assert a[3] == b[3]
+    assert ctx.cluster_stats()["exact_solves"] < bags.N * K * rounds
