@@ -663,6 +663,8 @@ def main():
                     help="cost-build precision (bf16*: tensor cores)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default sweep launch shape")
     ap.add_argument("--no-grouped", action="store_true", help="skip the grouped two-stream measurement")
+    ap.add_argument("--no-split", action="store_true",
+                    help="one stream per call (no D2_SPLIT_STREAMS) for the timed steps")
     ap.add_argument("--no-cost-variants", action="store_true",
                     help="skip the timing of the other cost-build precisions")
     args = ap.parse_args()
@@ -696,7 +698,7 @@ def main():
     w = w0.clone()
     plan = torch.empty(bags.n, m, dtype=torch.float32, device=dev)
     obj = torch.empty(K, dtype=torch.float64, device=dev)
-    opts = d2.badmm_opts(iters=T, tau=W["tau"], cost=args.cost)
+    opts = d2.badmm_opts(iters=T, tau=W["tau"], cost=args.cost, split_streams=not args.no_split)
     ctx = d2.Context(local)
 
     def step(o=opts):
@@ -704,7 +706,8 @@ def main():
         w.copy_(w0)
         d2.badmm_barycenter(ctx, db, co, mem, x, w, plan, None, o, obj)
 
-    # the first warm-up step lets the autotuner pick the sweep's launch shape
+    # the first warm-up step (one call, no split) lets the autotuner pick the
+    # sweep's launch shape; split calls hand it to their child contexts
     for i in range(args.warmup):
         step(d2.badmm_opts(iters=T, tau=W["tau"], cost=args.cost, autotune=not args.no_autotune)
              if i == 0 else opts)
@@ -732,9 +735,10 @@ def main():
     ms_total = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     ms_step = ms_total / args.steps
     value = job_rate(entries, T, world, ms_step)
-    # one more step with per-launch CUDA events for the kernel split and rooflines
+    # one more step, as one call on one stream, with per-launch CUDA events for
+    # the kernel split and the rooflines of isolated launches
     ctx.timing(True)
-    step()
+    step(d2.badmm_opts(iters=T, tau=W["tau"], cost=args.cost))
     torch.cuda.synchronize()
     kt = ctx.timing_read()
     ctx.timing(False)
@@ -849,7 +853,8 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": W["desc"], "clusters": K, "distributions_per_gpu": int(mem.numel()),
                            "support_rows_per_gpu": int(entries // m), "plan_entries_per_gpu": int(entries),
-                           "iters": T, "cost_precision": args.cost, "l2": "inputs larger than L2 (Pi, Lambda, C: %.1f GB per GPU)"
+                           "iters": T, "cost_precision": args.cost,
+                           "split_streams": not args.no_split, "l2": "inputs larger than L2 (Pi, Lambda, C: %.1f GB per GPU)"
                            % (12 * entries / 1e9),
                            "parallelism": "independent problem per GPU" if world > 1 else "single GPU"},
                 "roofline": roof, "cost_roofline": cost_roof, "cost_variants": variants,

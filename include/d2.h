@@ -59,6 +59,16 @@ extern "C" {
 #define D2_ELKAN     0x20 /* d2_cluster: skip assignment pairs by the triangle
                              inequality of W (Section 5), when no pruner is given */
 #define D2_ASSIGN_BOUNDED 0x200 /* d2_cluster: each round's assignment by d2_assign_bounded */
+#define D2_SPLIT_STREAMS 0x400 /* badmm_barycenter: run two halves of the clusters
+                             (split at half the members) concurrently on two
+                             internal streams, each in a child context that
+                             shares this context's per-entry workspaces; the
+                             caller's stream waits for both.  Clusters are
+                             independent in the update, so the results are
+                             those of the single call.  Reads the split point
+                             from cluster_offsets (one small synchronous copy),
+                             so such a call cannot be captured in a CUDA graph
+                             (it then runs as one half).                      */
 #define D2_AUTOTUNE  0x100 /* badmm_barycenter: choose the plan sweep's launch shape
                              for this plan width m by timing candidates (see
                              d2_sweep_tuning); kept in the context for later calls */
@@ -108,7 +118,7 @@ typedef struct {
     int32_t tau;       /* support update every tau iterations, default 10               */
     int32_t rule;      /* D2_RULE_R1 (default) or D2_RULE_R2                            */
     int32_t flags;     /* D2_FIX_X | D2_FIX_W | D2_VALIDATE | D2_NO_GRAPH | D2_NO_PIPE |
-                          D2_ELKAN | D2_AUTOTUNE |
+                          D2_ELKAN | D2_AUTOTUNE | D2_SPLIT_STREAMS |
                           one of D2_COST_BF16, _BF16X3, _BF16X6                        */
 } d2_badmm_opts;
 

@@ -58,8 +58,14 @@ extern "C" void d2_destroy(d2_ctx* ctx) {
     }
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    for (int h = 0; h < 2; ++h) {
+        if (ctx->child[h]) d2_destroy(ctx->child[h]);
+        if (ctx->cstream[h]) cudaStreamDestroy(ctx->cstream[h]);
+    }
+    for (int e = 0; e < 3; ++e)
+        if (ctx->cev[e]) cudaEventDestroy(ctx->cev[e]);
     for (int s = 0; s < WS_NSLOTS; ++s)
-        if (ctx->ws[s]) cudaFree(ctx->ws[s]);
+        if (ctx->ws[s] && !((ctx->borrowed >> s) & 1u)) cudaFree(ctx->ws[s]);
     if (ctx->dev_flags) cudaFree(ctx->dev_flags);
     delete ctx;
 }
@@ -120,6 +126,8 @@ static void drain_timing(d2_ctx* ctx) {
 
 extern "C" int d2_timing_enable(d2_ctx* ctx, int on) {
     if (!ctx) return D2_EINVAL;
+    for (int h = 0; h < 2; ++h)
+        if (ctx->child[h]) d2_timing_enable(ctx->child[h], on);
     drain_timing(ctx);
     for (int k = 0; k < D2_KT_COUNT; ++k) {
         ctx->t_ms[k] = 0.0;
@@ -135,6 +143,18 @@ extern "C" int d2_timing_read(d2_ctx* ctx, double* ms, int64_t* launches) {
     for (int k = 0; k < D2_KT_COUNT; ++k) {
         if (ms) ms[k] = ctx->t_ms[k];
         if (launches) launches[k] = ctx->t_n[k];
+    }
+    // launches of split calls run in the child contexts (concurrently: their
+    // times add up to more than the wall time)
+    for (int h = 0; h < 2; ++h) {
+        if (!ctx->child[h]) continue;
+        double cm[D2_KT_COUNT];
+        int64_t cn[D2_KT_COUNT];
+        d2_timing_read(ctx->child[h], cm, cn);
+        for (int k = 0; k < D2_KT_COUNT; ++k) {
+            if (ms) ms[k] += cm[k];
+            if (launches) launches[k] += cn[k];
+        }
     }
     return D2_OK;
 }
@@ -156,6 +176,8 @@ extern "C" int d2_device_errors(d2_ctx* ctx, int32_t* bits) {
 
 int d2_ws(d2_ctx* ctx, int slot, size_t bytes, void** out) {
     if (bytes == 0) bytes = 256;
+    if (((ctx->borrowed >> slot) & 1u) && ctx->ws_bytes[slot] < bytes)
+        return d2_fail(ctx, D2_EINVAL, "workspace slot %d lent by the parent is too small", slot);
     if (ctx->ws_bytes[slot] < bytes) {
         if (ctx->ws[slot]) {
             cudaDeviceSynchronize();  // a pending kernel may still use it

@@ -1050,6 +1050,108 @@ static int d2_tune_finish(d2_ctx* ctx, int m, const std::vector<SweepCand>& cand
 }
 
 // ---------------------------------------------------------------------------
+// split calls: two halves of the clusters on two streams (D2_SPLIT_STREAMS)
+// ---------------------------------------------------------------------------
+
+__global__ void k_rebase_offsets(const int64_t* src, int64_t cnt, int64_t* dst) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < cnt) dst[t] = src[t] - src[0];
+}
+
+// Runs clusters [0, K1) and [K1, K) (K1: half the members) as two calls in the
+// child contexts on their own streams; *done = false when the call should run
+// as one (fewer than two clusters, a capturing stream, offsets not from 0).
+static int badmm_split(d2_ctx* ctx, const d2_bags* bags, const int64_t* cofs, const int64_t* members, int64_t P,
+                       int32_t K, int32_t m, float* x, float* w, float* plan, const uint8_t* warm_mask,
+                       const d2_badmm_opts& opts, double* obj, cudaStream_t st, bool* done) {
+    *done = false;
+    if (K < 2) return D2_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return D2_OK;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return D2_OK;
+    std::vector<int64_t> hc((size_t)K + 1);
+    D2_CK(ctx, cudaMemcpyAsync(hc.data(), cofs, ((size_t)K + 1) * 8, cudaMemcpyDeviceToHost, st));
+    D2_CK(ctx, cudaStreamSynchronize(st));
+    if (hc[0] != 0 || hc[K] != P) return D2_OK;
+    int K1 = (int)(std::lower_bound(hc.begin(), hc.end(), P / 2) - hc.begin());
+    K1 = std::max(1, std::min(K - 1, K1));
+    const int64_t P1 = hc[K1];
+    if (P1 <= 0 || P1 >= P) return D2_OK;
+    for (int h = 0; h < 2; ++h) {
+        if (!ctx->child[h]) {
+            ctx->child[h] = d2_create(ctx->device);
+            if (!ctx->child[h]) return d2_fail(ctx, D2_ENOMEM, "badmm_barycenter: cannot create a child context");
+            D2_CK(ctx, cudaStreamCreateWithFlags(&ctx->cstream[h], cudaStreamNonBlocking));
+        }
+    }
+    for (int e = 0; e < 3; ++e)
+        if (!ctx->cev[e]) D2_CK(ctx, cudaEventCreateWithFlags(&ctx->cev[e], cudaEventDisableTiming));
+    // the per-entry arrays are indexed by global support row: the halves touch
+    // disjoint rows, so both children use this context's arrays
+    const size_t ent = (size_t)bags->n * m * 4;
+    void* pv = nullptr;
+    int rc;
+    if ((rc = d2_ws(ctx, WS_LAM, ent, &pv))) return rc;
+    if ((rc = d2_ws(ctx, WS_COST, ent, &pv))) return rc;
+    for (int h = 0; h < 2; ++h) {
+        d2_ctx* c = ctx->child[h];
+        for (int slot : {(int)WS_LAM, (int)WS_COST}) {
+            if (!((c->borrowed >> slot) & 1u) && c->ws[slot]) {
+                cudaDeviceSynchronize();
+                cudaFree(c->ws[slot]);
+            }
+            c->borrowed |= 1u << slot;
+            if (c->ws[slot] != ctx->ws[slot] || c->ws_bytes[slot] != ctx->ws_bytes[slot]) {
+                c->ws[slot] = ctx->ws[slot];
+                c->ws_bytes[slot] = ctx->ws_bytes[slot];
+                c->generation++;  // graphs captured with the old pointers are stale
+            }
+        }
+        c->timing = ctx->timing;
+        if (!find_tune(c, m)) {
+            const SweepTune* t = find_tune(ctx, m);
+            if (t) c->tuned.push_back(*t);
+        }
+    }
+    void* vs = nullptr;
+    if ((rc = d2_ws(ctx, WS_SPLIT, ((size_t)K - K1 + 1) * 8, &vs))) return rc;
+    int64_t* cofs2 = static_cast<int64_t*>(vs);
+    k_rebase_offsets<<<(unsigned)d2_ceil_div(K - K1 + 1, 256), 256, 0, st>>>(cofs + K1, K - K1 + 1, cofs2);
+    D2_LAUNCH_CK(ctx, "k_rebase_offsets");
+    D2_CK(ctx, cudaEventRecord(ctx->cev[0], st));
+    for (int h = 0; h < 2; ++h) D2_CK(ctx, cudaStreamWaitEvent(ctx->cstream[h], ctx->cev[0], 0));
+    d2_badmm_opts o = opts;
+    o.flags &= ~(D2_SPLIT_STREAMS | D2_VALIDATE);
+    const int64_t l0 = ctx->child[0]->launches + ctx->child[1]->launches;
+    const int d = bags->d;
+    rc = badmm_barycenter(ctx->child[0], bags, cofs, members, P1, K1, m, x, w, plan, warm_mask, &o, obj,
+                          ctx->cstream[0]);
+    if (rc == D2_OK)
+        rc = badmm_barycenter(ctx->child[1], bags, cofs2, members + P1, P - P1, K - K1, m,
+                              x + (size_t)K1 * m * d, w + (size_t)K1 * m, plan, warm_mask, &o, obj + K1,
+                              ctx->cstream[1]);
+    // join: the caller's stream waits for both halves
+    cudaEventRecord(ctx->cev[1], ctx->cstream[0]);
+    cudaEventRecord(ctx->cev[2], ctx->cstream[1]);
+    cudaStreamWaitEvent(st, ctx->cev[1], 0);
+    cudaStreamWaitEvent(st, ctx->cev[2], 0);
+    ctx->launches += ctx->child[0]->launches + ctx->child[1]->launches - l0;
+    if (!find_tune(ctx, m)) {
+        const SweepTune* t = find_tune(ctx->child[0], m);
+        if (t) ctx->tuned.push_back(*t);
+    }
+    if (rc != D2_OK) {
+        const d2_ctx* bad = ctx->child[0]->err.empty() ? ctx->child[1] : ctx->child[0];
+        return d2_fail(ctx, rc, "%s", bad->err.c_str());
+    }
+    *done = true;
+    return D2_OK;
+}
+
+// ---------------------------------------------------------------------------
 // entry point
 // ---------------------------------------------------------------------------
 
@@ -1075,6 +1177,12 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
         if (rc) return rc;
     }
     if (P == 0) return D2_OK;
+    if (opts.flags & D2_SPLIT_STREAMS) {
+        bool done = false;
+        rc = badmm_split(ctx, bags, cluster_offsets, members, P, K, m, x, w, plan, warm_mask, opts, obj, st, &done);
+        if (rc || done) return rc;
+        opts.flags &= ~D2_SPLIT_STREAMS;
+    }
     const int d = bags->d;
     const int64_t n = bags->n;
 

@@ -30,6 +30,7 @@ enum WsSlot {
     WS_CLUSTER_LOOP, // d2_cluster state (labels, plan cache, ...)
     WS_PRUNE,        // pruning scratch
     WS_ELKAN,        // triangle-inequality bounds carried across rounds
+    WS_SPLIT,        // rebased cluster offsets of the second half of a split call
     WS_NSLOTS
 };
 
@@ -73,6 +74,12 @@ struct d2_ctx {
     std::vector<SweepTune> tuned;
     // testing: the next tensor-core cost build lets its first wait expire
     int expire_test = 0;
+    // split calls (D2_SPLIT_STREAMS): two child contexts, each on its own
+    // stream, with the per-entry workspaces lent by this context
+    d2_ctx* child[2] = {nullptr, nullptr};
+    cudaStream_t cstream[2] = {nullptr, nullptr};
+    cudaEvent_t cev[3] = {nullptr, nullptr, nullptr};
+    unsigned borrowed = 0;          // bit s: ws[s] belongs to the parent
 };
 
 // Event bracket around one launch when timing is on (no-ops otherwise).

@@ -297,3 +297,33 @@ def test_autotuned_sweep(d2):
             ref = oracle_badmm(members, x0[c].double().numpy(), w0[c].double().numpy(), T=41, tau=10)
             compare_cluster(bags, co, mem, c, gx, gw, gplan, gobj, ref, x_tol=x_tol(ref))
     print("autotune m=32:", rec)
+
+
+@pytest.mark.parametrize("side_stream", [False, True])
+def test_split_streams_equal_single_call(d2, side_stream):
+    """D2_SPLIT_STREAMS runs two halves of the clusters concurrently in child
+    contexts; clusters are independent in the update, so every output is
+    bitwise the single call's (also on a side stream, where the children
+    replay CUDA graphs, and on a second call with new data)."""
+    ctx = d2.Context(0)
+    K, m = 9, 16
+    bags, co, mem, x0, w0 = ragged_case(17, K, m, d=8, N=240, mk=(2, 30))
+    db = d2.DeviceBags.from_synth(bags)
+    s = torch.cuda.Stream() if side_stream else torch.cuda.current_stream()
+    outs = []
+    for split in (False, True):
+        for shift in (0.0, 0.25):
+            with torch.cuda.stream(s):
+                x, w = (x0 + shift).cuda(), w0.clone().cuda()
+                plan = torch.zeros(bags.n, m, device="cuda")
+                obj = torch.empty(K, dtype=torch.float64, device="cuda")
+                d2.badmm_barycenter(ctx, db, co.cuda(), mem.cuda(), x, w, plan, None,
+                                    d2.badmm_opts(iters=23, tau=10, split_streams=split), obj)
+            s.synchronize()
+            outs.append((x.cpu(), w.cpu(), plan.cpu(), obj.cpu()))
+    for a, b in zip(outs[:2], outs[2:]):
+        for u, v in zip(a, b):
+            assert torch.equal(u, v)
+    ref = oracle_badmm(cluster_members(bags, co, mem, 1)[1], x0[1].double().numpy(), w0[1].double().numpy(),
+                       T=23, tau=10)
+    compare_cluster(bags, co, mem, 1, *outs[2], ref, x_tol=x_tol(ref))
