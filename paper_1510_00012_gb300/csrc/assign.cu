@@ -76,7 +76,20 @@ __device__ __forceinline__ void warp_argmin(float& v, int& idx) {
     }
 }
 
-// Solve one pair; returns W^2 (all lanes).
+// Value of node v's register (slot v / 32 of owner lane v mod 32), broadcast.
+// (a predicated move per slot, so that the array stays in registers)
+template <int TV>
+__device__ __forceinline__ float node_bcast(const float (&r)[TV], int v) {
+    const int tv = v >> 5;
+    float x = r[0];
+#pragma unroll
+    for (int t = 1; t < TV; ++t) asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %2, %3;\n\t@p mov.f32 %0, %1;\n\t}"
+                                     : "+f"(x) : "f"(r[t]), "r"(t), "r"(tv));
+    return __shfl_sync(0xffffffffu, x, v & 31);
+}
+
+// Solve one pair; returns W^2 (all lanes).  TV >= (m + n) / 32 node slots per lane.
+template <int TV>
 __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int cent, bool& hit_limit) {
     const int lane = threadIdx.x & 31;
     const int m = a.m, d = a.d;
@@ -144,13 +157,23 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
     }
     __syncwarp();
     const float tol = 1e-9f;
-    int phase = 0;
     hit_limit = false;
+    // node state in registers: node v is owned by lane v mod 32, slot v / 32
+    float pot[TV], exc[TV], dist[TV];
+#pragma unroll
+    for (int t = 0; t < TV; ++t) {
+        const int v = lane + 32 * t;
+        pot[t] = v < V ? s.pot[v] : 0.f;
+        exc[t] = v < V ? s.exc[v] : 0.f;
+    }
+    int phase = 0;
     for (;;) {
         // anything left to route?
         bool src = false, snk = false;
-        for (int v = lane; v < V; v += 32) {
-            if (s.exc[v] > tol) {
+#pragma unroll
+        for (int t = 0; t < TV; ++t) {
+            const int v = lane + 32 * t;
+            if (v < V && exc[t] > tol) {
                 if (v < m) src = true; else snk = true;
             }
         }
@@ -162,103 +185,113 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
             break;
         }
         // ---- Dijkstra from every source with remaining supply
-        for (int v = lane; v < V; v += 32) {
-            s.dist[v] = (v < m && s.exc[v] > tol) ? 0.f : AS_INF;
-            s.vis[v] = 0;
-            s.pred[v] = -1;
+        unsigned vis = 0;  // bit t: node lane + 32 t is settled
+#pragma unroll
+        for (int t = 0; t < TV; ++t) {
+            const int v = lane + 32 * t;
+            dist[t] = (v < m && exc[t] > tol) ? 0.f : AS_INF;
+            if (v < V) s.pred[v] = -1;
         }
-        __syncwarp();
         int target = -1;
         for (int it = 0; it < V; ++it) {
+            // warp argmin over unsettled nodes: smallest distance, then lowest index
             float bv = AS_INF;
             int bi = 0x7fffffff;
-            for (int v = lane; v < V; v += 32) {
-                if (!s.vis[v]) {
-                    float dv = s.dist[v];
-                    if (dv < bv) {
-                        bv = dv;
-                        bi = v;
-                    }
+#pragma unroll
+            for (int t = 0; t < TV; ++t) {
+                const int v = lane + 32 * t;
+                if (v < V && !((vis >> t) & 1u) && dist[t] < bv) {
+                    bv = dist[t];
+                    bi = v;
                 }
             }
-            warp_argmin(bv, bi);
-            if (bv >= AS_INF) break;
-            const int u = bi;
-            const float du = bv;
-            __syncwarp();
-            if (lane == 0) s.vis[u] = 1;
-            if (u >= m && s.exc[u] > tol) {
+            // non-negative floats order like their bit patterns
+            const unsigned kmin = __reduce_min_sync(0xffffffffu, __float_as_uint(bv));
+            if (__uint_as_float(kmin) >= AS_INF) break;
+            const int u = (int)__reduce_min_sync(0xffffffffu, __float_as_uint(bv) == kmin ? (unsigned)bi : 0xffffffffu);
+            const float du = __uint_as_float(kmin);
+            if ((u & 31) == lane) vis |= 1u << (u >> 5);
+            if (u >= m && node_bcast<TV>(exc, u) > tol) {
                 target = u;
                 break;
             }
+            const float pu = node_bcast<TV>(pot, u);
             if (u < m) {
-                const float pu = s.pot[u];
-                for (int j = lane; j < n; j += 32) {
-                    const int v = m + j;
-                    if (!s.vis[v]) {
-                        float rc = fmaxf(s.C[u * n + j] + pu - s.pot[v], 0.f);
-                        float nd = du + rc;
-                        if (nd < s.dist[v]) {
-                            s.dist[v] = nd;
+                const float* crow = s.C + u * n;
+#pragma unroll
+                for (int t = 0; t < TV; ++t) {
+                    const int v = lane + 32 * t;
+                    if (v >= m && v < V && !((vis >> t) & 1u)) {
+                        const float rc = fmaxf(crow[v - m] + pu - pot[t], 0.f);
+                        const float nd = du + rc;
+                        if (nd < dist[t]) {
+                            dist[t] = nd;
                             s.pred[v] = (short)u;
                         }
                     }
                 }
             } else {
                 const int j = u - m;
-                const float pu = s.pot[u];
-                for (int i = lane; i < m; i += 32) {
-                    if (!s.vis[i] && s.F[i * n + j] > tol) {
-                        float rc = fmaxf(-s.C[i * n + j] + pu - s.pot[i], 0.f);
-                        float nd = du + rc;
-                        if (nd < s.dist[i]) {
-                            s.dist[i] = nd;
+#pragma unroll
+                for (int t = 0; t < TV; ++t) {
+                    const int i = lane + 32 * t;
+                    if (i < m && !((vis >> t) & 1u) && s.F[i * n + j] > tol) {
+                        const float rc = fmaxf(-s.C[i * n + j] + pu - pot[t], 0.f);
+                        const float nd = du + rc;
+                        if (nd < dist[t]) {
+                            dist[t] = nd;
                             s.pred[i] = (short)u;
                         }
                     }
                 }
             }
-            __syncwarp();
         }
-        __syncwarp();
         if (target < 0) {
             hit_limit = true;  // no augmenting path (cannot happen with balanced supplies)
             break;
         }
         // ---- potentials: pot += min(dist, dist[target])
-        const float dt = s.dist[target];
-        for (int v = lane; v < V; v += 32) s.pot[v] += s.vis[v] ? fminf(s.dist[v], dt) : dt;
+        const float dt = node_bcast<TV>(dist, target);
+#pragma unroll
+        for (int t = 0; t < TV; ++t) pot[t] += ((vis >> t) & 1u) ? fminf(dist[t], dt) : dt;
         __syncwarp();
-        // ---- augment along the path (lane 0)
+        // ---- augment along the path: lane 0 walks it (flows in shared memory)
+        float dflow = AS_INF;
+        int src_node = target;
         if (lane == 0) {
-            float delta = s.exc[target];
-            int v = target, src_node = target;
+            int v = target;
             for (int guard = 0; guard <= V; ++guard) {
-                int p = s.pred[v];
+                const int p = s.pred[v];
                 if (p < 0) {
                     src_node = v;
                     break;
                 }
-                if (v < m) {  // reached source v by the backward arc (v, p - m)
-                    delta = fminf(delta, s.F[v * n + (p - m)]);
-                }
+                if (v < m) dflow = fminf(dflow, s.F[v * n + (p - m)]);  // backward arc (v, p - m)
                 v = p;
             }
-            delta = fminf(delta, s.exc[src_node]);
-            v = target;
+        }
+        src_node = __shfl_sync(0xffffffffu, src_node, 0);
+        dflow = __shfl_sync(0xffffffffu, dflow, 0);
+        const float delta = fminf(fminf(dflow, node_bcast<TV>(exc, target)), node_bcast<TV>(exc, src_node));
+        if (lane == 0) {
+            int v = target;
             for (int guard = 0; guard <= V; ++guard) {
-                int p = s.pred[v];
+                const int p = s.pred[v];
                 if (p < 0) break;
                 if (v >= m) {  // forward arc p -> v
                     s.F[p * n + (v - m)] += delta;
                 } else {       // backward arc: flow on (v, p - m) decreases
-                    float f = s.F[v * n + (p - m)] - delta;
+                    const float f = s.F[v * n + (p - m)] - delta;
                     s.F[v * n + (p - m)] = f > 0.f ? f : 0.f;
                 }
                 v = p;
             }
-            s.exc[target] -= delta;
-            s.exc[src_node] -= delta;
+        }
+#pragma unroll
+        for (int t = 0; t < TV; ++t) {
+            const int v = lane + 32 * t;
+            if (v == target) exc[t] -= delta;
+            if (v == src_node) exc[t] -= delta;
         }
         __syncwarp();
     }
@@ -269,6 +302,7 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
     return acc;
 }
 
+template <int TV>
 __global__ void k_w2_pairs(AssignArgs a) {
     extern __shared__ float4 dyn4[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -321,7 +355,7 @@ __global__ void k_w2_pairs(AssignArgs a) {
             slot = p;
         }
         bool lim = false;
-        double v = solve_pair(a, s, bag, cent, lim);
+        double v = solve_pair<TV>(a, s, bag, cent, lim);
         if (lane == 0) {
             a.out[slot] = (float)v;
             if (lim) {
@@ -374,26 +408,37 @@ static int pick_wpb(size_t warp_bytes) {
     return best;
 }
 
+// Solver instance for m + nmax nodes (node slots per lane), or null past 256.
+typedef void (*W2Fn)(AssignArgs);
+static W2Fn w2_kernel_for(int V) {
+    if (V <= 64) return k_w2_pairs<2>;
+    if (V <= 128) return k_w2_pairs<4>;
+    if (V <= 256) return k_w2_pairs<8>;
+    return nullptr;
+}
+
 // Launch the pair solver; grid is a bound (persistent stride loop).
 int d2_launch_pairs(d2_ctx* ctx, AssignArgs a, int64_t max_units, cudaStream_t st) {
     a.warp_bytes = d2_assign_warp_bytes(a.m, a.nmax);
     if (a.warp_bytes > 200 * 1024)
         return d2_fail(ctx, D2_ENOTSUP, "d2_assign: m * max_mk too large for the per-warp tableau");
+    const W2Fn fn = w2_kernel_for(a.m + a.nmax);
+    if (!fn) return d2_fail(ctx, D2_ENOTSUP, "d2_assign: m + max_mk = %d exceeds 256", a.m + a.nmax);
     const int wpb = pick_wpb(a.warp_bytes);
     size_t smem = a.warp_bytes * wpb;
-    cudaError_t e = cudaFuncSetAttribute(k_w2_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return d2_cuda_fail(ctx, e, "k_w2_pairs smem attribute");
     int dev_sms = 152;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_w2_pairs, wpb * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, smem);
     if (per_sm < 1) per_sm = 1;
     int64_t want = d2_ceil_div(std::max<int64_t>(max_units, 1), wpb);
     int64_t cap = (int64_t)dev_sms * per_sm * 8;
     unsigned grid = (unsigned)std::max<int64_t>(1, std::min(want, cap));
     a.max_phase = 8 * (a.m + a.nmax) + 64;
     d2_time_begin(ctx, D2_KT_ASSIGN, st);
-    k_w2_pairs<<<grid, wpb * 32, smem, st>>>(a);
+    fn<<<grid, wpb * 32, smem, st>>>(a);
     d2_time_end(ctx, st);
     D2_LAUNCH_CK(ctx, "k_w2_pairs");
     return D2_OK;
@@ -497,18 +542,20 @@ cudaError_t d2_assign_exact_into(const d2_bags* b, int K, int m, const float* x,
     a.out = D;
     a.warp_bytes = d2_assign_warp_bytes(m, b->max_mk);
     if (a.warp_bytes > 200 * 1024) return cudaErrorInvalidValue;
+    const W2Fn fn = w2_kernel_for(m + b->max_mk);
+    if (!fn) return cudaErrorInvalidValue;
     const int wpb = pick_wpb(a.warp_bytes);
     const size_t smem = a.warp_bytes * wpb;
-    cudaError_t e = cudaFuncSetAttribute(k_w2_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int sms = 152, per_sm = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_w2_pairs, wpb * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, smem);
     per_sm = std::max(per_sm, 1);
     const int64_t want = d2_ceil_div(std::max<int64_t>(a.npairs, 1), wpb);
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min(want, (int64_t)sms * per_sm * 8));
     a.max_phase = 8 * (a.m + a.nmax) + 64;
-    k_w2_pairs<<<grid, wpb * 32, smem, st>>>(a);
+    fn<<<grid, wpb * 32, smem, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_argmin_rows<<<(unsigned)d2_ceil_div(b->N, 256), 256, 0, st>>>(D, b->N, K, labels, dist);
     return cudaGetLastError();

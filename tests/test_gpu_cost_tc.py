@@ -201,3 +201,17 @@ def test_bounded_wait_expiry_is_reported(d2, ctx):
     assert e.value.code == d2.D2_ETIMEOUT
     assert ctx.device_errors() == 0  # cleared by the read
     _check_cost(d2, ctx, bags, co, mem, x0, "bf16x3")
+
+
+@pytest.mark.parametrize("d,m", [(32, 128), (124, 8), (64, 20), (48, 64)])
+def test_badmm_tensor_core_cost_shapes(d2, ctx, d, m):
+    """B-ADMM on the split-BF16 cost build across plan widths and support
+    dimensions: N padded to 16 (m = 20), TMEM widths up to 128 columns,
+    several K blocks per tile (d = 124), several tiles per chunk."""
+    K = 3
+    bags = synth.gaussian_class_bags(70 + d + m, 60, d, K, mk=(1, 70), mu_sigma=3.0)
+    co, mem = split_clusters(bags.labels, K)
+    x0, w0 = synth.sample_initial_barycenters(71, bags, co, mem, m)
+    gx, gw, gplan, gobj = run_gpu_badmm(d2, ctx, bags, co, mem, x0, w0, iters=21, tau=10, cost="bf16x3")
+    assert ctx.device_errors() == 0
+    _check_badmm(bags, co, mem, x0, w0, gx, gw, gplan, gobj, "bf16x3", 21, 10)
