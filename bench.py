@@ -228,6 +228,15 @@ def _d2_round_comparison(d2, ctx, dev, seed):
     (xp, wp, lp, op), tp = timed(plain)
     out["plain_s_per_round"] = tp / R
     out["batched_s_per_round"] = tb / R
+    # the two halves of a batched round: the exact assignment and the update
+    (la, _), t_as = timed(lambda: d2.d2_assign(ctx, db, xb, wb))
+    co_a = torch.zeros(K + 1, dtype=torch.int64, device=dev)
+    co_a[1:] = torch.cumsum(torch.bincount(la.long(), minlength=K), 0)
+    mem_a = torch.sort(la.long(), stable=True).indices.contiguous()
+    xu, wu = xb.clone(), wb.clone()
+    _, t_up = timed(lambda: d2.badmm_barycenter(ctx, db, co_a, mem_a, xu, wu, None, None, opts))
+    out["batched_round_split_s"] = {"exact_assignment": t_as, "badmm_update": t_up,
+                                    "assignment_pairs_per_s": bags.N * K / t_as}
     out["obj_plain"] = op
     out["obj_batched"] = ob
     out["max_rel_obj_diff_batched_vs_plain"] = max(abs(a - b) / b for a, b in zip(ob, op))
@@ -376,18 +385,26 @@ def docs_clustering(d2, ctx, dev, seed, n_docs=None):
     (le, _), t_ex = timed(lambda: d2.d2_assign(ctx, dsub, x0, w0))
     (lp, _, st), t_pr = timed(lambda: d2.d2_assign(ctx, dsub, x0, w0, prune=pr, want_stats=True))
     (lbd, _, stb), t_bd = timed(lambda: d2.d2_assign(ctx, dsub, x0, w0, want_stats=True, bounded=True))
-    # D2-clustering, all rounds, timed as one call: exact assignment by
-    # certified bounds (d2_assign_bounded), without and with the pruner's
-    # candidates solved first
-    bopts = d2.badmm_opts(iters=W["iters"], tau=W["tau"], cost="bf16x3", assign_bounded=True)
-    (xq, wq, lq, oq), t_cl = timed(lambda: d2.d2_cluster(ctx, db, K, m, 11, R, bopts))
+    # D2-clustering, all rounds, timed as one call: the learned pruner with its
+    # margin test (fall-back to all K), and the pruner's candidates followed by
+    # the certified-bound solves (exact by construction)
+    popts = d2.badmm_opts(iters=W["iters"], tau=W["tau"], cost="bf16x3")
+    (xq, wq, lq, oq), t_cl = timed(lambda: d2.d2_cluster(ctx, db, K, m, 11, R, popts, prune=pr))
     cs = ctx.cluster_stats()
+    # the same with the margin recalibrated against each round's centroids
+    ropts = d2.badmm_opts(iters=W["iters"], tau=W["tau"], cost="bf16x3", recalibrate=True)
+    (xc, wc, lc, oc), t_rc = timed(lambda: d2.d2_cluster(ctx, db, K, m, 11, R, ropts, prune=pr))
+    csr = ctx.cluster_stats()
+    out.update({"recalibrated_pruned_s_per_round": t_rc / R, "recalibrated_exact_solves": csr["exact_solves"],
+                "recalibrated_fallbacks": csr["fallbacks"], "obj_per_round_recalibrated": oc})
+    bopts = d2.badmm_opts(iters=W["iters"], tau=W["tau"], cost="bf16x3", assign_bounded=True)
     (xr, wr, lr_, orr), t_cp = timed(lambda: d2.d2_cluster(ctx, db, K, m, 11, R, bopts, prune=pr))
     csp = ctx.cluster_stats()
-    out.update({"bounded_s_per_round": t_cl / R, "bounded_exact_solves": cs["exact_solves"],
+    out.update({"pruned_s_per_round": t_cl / R, "pruned_exact_solves": cs["exact_solves"],
+                "pruned_fallbacks": cs["fallbacks"],
                 "bounded_pruned_s_per_round": t_cp / R, "bounded_pruned_exact_solves": csp["exact_solves"],
-                "labels_equal_bounded_vs_bounded_pruned": bool(torch.equal(lq, lr_)),
-                "obj_per_round": oq})
+                "labels_equal_pruned_vs_bounded": bool(torch.equal(lq, lr_)),
+                "obj_per_round": orr, "obj_per_round_pruned": oq})
     # one B-ADMM update of all clusters at the final labels (the update step of a round)
     order = torch.sort(lq.long(), stable=True).indices
     co = torch.zeros(K + 1, dtype=torch.int64, device=dev)

@@ -59,6 +59,10 @@ extern "C" {
 #define D2_ELKAN     0x20 /* d2_cluster: skip assignment pairs by the triangle
                              inequality of W (Section 5), when no pruner is given */
 #define D2_ASSIGN_BOUNDED 0x200 /* d2_cluster: each round's assignment by d2_assign_bounded */
+#define D2_PRUNE_RECALIBRATE 0x800 /* d2_cluster with a pruner: before every round's
+                             assignment, d2_prune_calibrate on 1,000 bags (evenly
+                             spaced ids) against the current centroids, quantile
+                             0.999 (this updates the pruner's delta)          */
 #define D2_SPLIT_STREAMS 0x400 /* badmm_barycenter: run two halves of the clusters
                              (split at half the members) concurrently on two
                              internal streams, each in a child context that
@@ -267,6 +271,15 @@ int d2_prune_set_params(d2_ctx* ctx, d2_prune* p, const float* host_in);
  * held-out pairs. */
 int d2_prune_set_margin(d2_prune* p, int32_t r, float delta);
 int d2_prune_get_margin(const d2_prune* p, int32_t* r, float* delta);
+
+/* Recalibrate the margin delta against centroids (x, w): exact W^2 of every
+ * (bag ids[t], centroid) pair (device ids, nids) by the solver of d2_assign,
+ * and delta := the `quantile` (in (0, 1]) of |What^2 - W^2| over those pairs.
+ * Centroids move between the rounds of Algorithm 1, so a delta measured on
+ * the training centroids need not cover later ones.  Synchronous. */
+int d2_prune_calibrate(d2_ctx* ctx, d2_prune* p, const d2_bags* bags, int32_t K, int32_t m,
+                       const float* x, const float* w, const int64_t* ids, int64_t nids,
+                       float quantile, void* stream);
 
 /* Embeddings f(P) of the bags listed in `ids` (device, cnt) -> emb (device,
  * cnt x E) and their means mu (device, cnt x d). */

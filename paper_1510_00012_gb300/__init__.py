@@ -26,6 +26,7 @@ D2_COST_BF16, D2_COST_BF16X3, D2_COST_BF16X6 = 0x40, 0x80, 0xC0
 D2_AUTOTUNE = 0x100
 D2_ASSIGN_BOUNDED = 0x200
 D2_SPLIT_STREAMS = 0x400
+D2_PRUNE_RECALIBRATE = 0x800
 D2_TEST_EXPIRE_WAIT = 0x8000
 D2_TUNE_MAX = 16
 COST_PRECISION = {"fp32": 0, "bf16": D2_COST_BF16, "bf16x3": D2_COST_BF16X3, "bf16x6": D2_COST_BF16X6}
@@ -85,6 +86,8 @@ _SIGS = {
     "d2_prune_set_params": (c_int, [c_void_p, c_void_p, c_void_p]),
     "d2_prune_set_margin": (c_int, [c_void_p, c_int32, c_float]),
     "d2_prune_get_margin": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "d2_prune_calibrate": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
+                                   c_void_p, c_int64, c_float, c_void_p]),
     "d2_prune_embed": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p,
                                c_void_p]),
     "d2_prune_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
@@ -245,7 +248,7 @@ def _cost_flag(precision):
 
 def badmm_opts(rho0=2.0, iters=100, tau=10, eps=1e-16, rule="R1", fix_x=False, fix_w=False,
                validate=False, rho=0.0, graph=True, elkan=False, cost="fp32", autotune=False,
-               assign_bounded=False, split_streams=False):
+               assign_bounded=False, split_streams=False, recalibrate=False):
     """d2_badmm_opts; cost = "fp32" | "bf16" | "bf16x3" | "bf16x6" selects the cost build."""
     o = _Opts()
     lib().d2_badmm_opts_default(ctypes.byref(o))
@@ -254,7 +257,7 @@ def badmm_opts(rho0=2.0, iters=100, tau=10, eps=1e-16, rule="R1", fix_x=False, f
     o.flags = ((D2_FIX_X if fix_x else 0) | (D2_FIX_W if fix_w else 0) | (D2_VALIDATE if validate else 0)
                | (0 if graph else D2_NO_GRAPH) | (D2_ELKAN if elkan else 0) | _cost_flag(cost)
                | (D2_AUTOTUNE if autotune else 0) | (D2_ASSIGN_BOUNDED if assign_bounded else 0)
-               | (D2_SPLIT_STREAMS if split_streams else 0))
+               | (D2_SPLIT_STREAMS if split_streams else 0) | (D2_PRUNE_RECALIBRATE if recalibrate else 0))
     return o
 
 
@@ -416,6 +419,14 @@ class Pruner:
         r, dl = c_int32(), c_float()
         lib().d2_prune_get_margin(self.h, ctypes.byref(r), ctypes.byref(dl))
         return int(r.value), float(dl.value)
+
+    def calibrate(self, bags, x, w, ids, quantile=0.999):
+        """delta := quantile of |What^2 - W^2| over every (ids[t], centroid) pair (exact W^2)."""
+        _need(ids, torch.int64, "ids")
+        K, m = x.shape[0], x.shape[1]
+        self.ctx.check(lib().d2_prune_calibrate(self.ctx.h, self.h, bags.ref(), K, m, _ptr(x), _ptr(w),
+                                                _ptr(ids), ids.numel(), float(quantile), _stream()))
+        return self.margin()[1]
 
     def embed(self, bags, ids):
         _need(ids, torch.int64, "ids")

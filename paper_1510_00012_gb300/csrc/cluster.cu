@@ -376,6 +376,18 @@ extern "C" int d2_cluster(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m
             D2_CK(ctx, cudaMemcpyAsync(x_prev, x_out, (size_t)K * m * bags->d * 4, cudaMemcpyDeviceToDevice, st));
             D2_CK(ctx, cudaMemcpyAsync(w_prev, w_out, (size_t)K * m * 4, cudaMemcpyDeviceToDevice, st));
         } else {
+            if (prune && (o.flags & D2_PRUNE_RECALIBRATE)) {
+                // the margin of the current centroids, from exact W^2 of evenly spaced bags
+                const int64_t ns = std::min<int64_t>(N, 1000);
+                std::vector<int64_t> hid(ns);
+                for (int64_t t = 0; t < ns; ++t) hid[t] = t * N / ns;
+                void* vid = nullptr;
+                if ((rc = d2_ws(ctx, WS_SPLIT, (size_t)ns * 8, &vid))) return rc;
+                D2_CK(ctx, cudaMemcpyAsync(vid, hid.data(), (size_t)ns * 8, cudaMemcpyHostToDevice, st));
+                if ((rc = d2_prune_calibrate(ctx, const_cast<d2_prune*>(prune), bags, K, m, x_out, w_out,
+                                             static_cast<int64_t*>(vid), ns, 0.999f, stream)))
+                    return rc;
+            }
             if ((rc = assign_any(ctx, bags, K, m, x_out, w_out, prune, (o.flags & D2_ASSIGN_BOUNDED) != 0, lab, dist,
                                  nullptr, stream)))
                 return rc;

@@ -892,6 +892,93 @@ extern "C" int d2_prune_set_params(d2_ctx* ctx, d2_prune* p, const float* host_i
     return D2_OK;
 }
 
+__global__ void k_all_pairs(const int64_t* ids, int64_t nids, int K, int64_t* pb, int32_t* pc) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nids * K) return;
+    pb[t] = ids[t / K];
+    pc[t] = (int32_t)(t % K);
+}
+
+// from assign.cu
+int d2_solve_pair_list(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w,
+                       const int64_t* pair_bag, const int32_t* pair_cent, int64_t max_pairs,
+                       const int64_t* npairs_dev, float* out, int64_t* fail_count, cudaStream_t st);
+
+extern "C" int d2_prune_calibrate(d2_ctx* ctx, d2_prune* p, const d2_bags* bags, int32_t K, int32_t m,
+                                  const float* x, const float* w, const int64_t* ids, int64_t nids,
+                                  float quantile, void* stream) {
+    if (!ctx || !p) return D2_EINVAL;
+    int rc = d2_check_bags_host(ctx, bags);
+    if (rc) return rc;
+    if (K < 1 || m < 1 || !x || !w || nids < 1 || !ids || !(quantile > 0.f && quantile <= 1.f))
+        return d2_fail(ctx, D2_EINVAL, "d2_prune_calibrate: bad arguments");
+    if (p->d != bags->d) return d2_fail(ctx, D2_EINVAL, "d2_prune_calibrate: pruner dimension %d != %d", p->d, bags->d);
+    cudaStream_t st = d2_stream(stream);
+    const int64_t np = nids * K;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_pb = take(np * 8), o_pc = take(np * 4), o_t = take(np * 4), o_f = take(nids * p->E * 4),
+                 o_mu = take(nids * p->d * 4), o_fc = take((size_t)K * p->E * 4), o_muc = take((size_t)K * p->d * 4),
+                 o_cnt = take(64);
+    void* base = nullptr;
+    if ((rc = d2_ws(ctx, WS_ASSIGN, off, &base))) return rc;
+    char* b = static_cast<char*>(base);
+    int64_t* pb = reinterpret_cast<int64_t*>(b + o_pb);
+    int32_t* pc = reinterpret_cast<int32_t*>(b + o_pc);
+    float* tg = reinterpret_cast<float*>(b + o_t);
+    float* hf = reinterpret_cast<float*>(b + o_f);
+    float* hmu = reinterpret_cast<float*>(b + o_mu);
+    float* cf = reinterpret_cast<float*>(b + o_fc);
+    float* cmu = reinterpret_cast<float*>(b + o_muc);
+    int64_t* cnt = reinterpret_cast<int64_t*>(b + o_cnt);
+    D2_CK(ctx, cudaMemsetAsync(cnt, 0, 16, st));
+    k_all_pairs<<<(unsigned)d2_ceil_div(np, 256), 256, 0, st>>>(ids, nids, K, pb, pc);
+    D2_LAUNCH_CK(ctx, "k_all_pairs");
+    if ((rc = d2_solve_pair_list(ctx, bags, K, m, x, w, pb, pc, np, nullptr, tg, cnt + 1, st))) return rc;
+    MlpArgs a = mlp_args(p, bags, x, w, m);
+    a.nslots = nids;
+    a.nbag_slots = nids;
+    a.slot_id = ids;
+    a.f = hf;
+    a.mu = hmu;
+    if ((rc = launch_fwd(ctx, p, a, st))) return rc;
+    MlpArgs ac = mlp_args(p, bags, x, w, m);
+    ac.nslots = K;
+    ac.nbag_slots = 0;
+    ac.f = cf;
+    ac.mu = cmu;
+    if ((rc = launch_fwd(ctx, p, ac, st))) return rc;
+    D2_CK(ctx, cudaStreamSynchronize(st));
+    std::vector<float> F(nids * p->E), MU(nids * p->d), FC((size_t)K * p->E), MUC((size_t)K * p->d), T(np);
+    D2_CK(ctx, cudaMemcpy(F.data(), hf, F.size() * 4, cudaMemcpyDeviceToHost));
+    D2_CK(ctx, cudaMemcpy(MU.data(), hmu, MU.size() * 4, cudaMemcpyDeviceToHost));
+    D2_CK(ctx, cudaMemcpy(FC.data(), cf, FC.size() * 4, cudaMemcpyDeviceToHost));
+    D2_CK(ctx, cudaMemcpy(MUC.data(), cmu, MUC.size() * 4, cudaMemcpyDeviceToHost));
+    D2_CK(ctx, cudaMemcpy(T.data(), tg, T.size() * 4, cudaMemcpyDeviceToHost));
+    std::vector<double> err(np);
+    for (int64_t i = 0; i < nids; ++i)
+        for (int c = 0; c < K; ++c) {
+            double mt = 0, pr = 0;
+            for (int t = 0; t < p->d; ++t) {
+                const double v = (double)MU[i * p->d + t] - MUC[(size_t)c * p->d + t];
+                mt += v * v;
+            }
+            for (int e = 0; e < p->E; ++e) {
+                const double v = (double)F[i * p->E + e] - FC[(size_t)c * p->E + e];
+                pr += v * v;
+            }
+            err[i * K + c] = std::fabs(mt + pr - (double)T[i * K + c]);
+        }
+    const int64_t q = std::min<int64_t>(np - 1, std::max<int64_t>(0, (int64_t)std::ceil((double)quantile * np) - 1));
+    std::nth_element(err.begin(), err.begin() + q, err.end());
+    p->delta = (float)err[q];
+    return D2_OK;
+}
+
 extern "C" int d2_prune_set_margin(d2_prune* p, int32_t r, float delta) {
     if (!p || r < 1 || r > 16 || !(delta >= 0.f)) return D2_EINVAL;
     p->r = r;

@@ -128,3 +128,45 @@ def test_train_then_prune(d2, ctx):
     mis = float(np.mean(lab.cpu().numpy() != ref_lab))
     assert mis <= 0.02, mis
     assert st["exact_solves"] < N * K
+
+
+def test_calibrated_margin_follows_moved_centroids(d2, ctx):
+    """A margin measured on the training centroids need not hold once the
+    centroids move (as they do between rounds of Algorithm 1); recalibrating
+    delta on exact W^2 against the moved centroids restores a small
+    misassignment rate, and d2_cluster can recalibrate every round."""
+    K, m, d = 12, 8, 8
+    bags = synth.gaussian_class_bags(17, 800, d, K, mk=(8, 24), mu_sigma=1.5, alpha=1.0)
+    db = d2.DeviceBags.from_synth(bags)
+    co = torch.zeros(K + 1, dtype=torch.int64)
+    lab = bags.labels
+    order = torch.sort(lab, stable=True).indices
+    co[1:] = torch.cumsum(torch.bincount(lab, minlength=K), 0)
+    x, w = synth.sample_initial_barycenters(18, bags, co, order, m)
+    x, w = x.cuda(), w.cuda()
+    N = bags.N
+    pb = torch.arange(N, device="cuda").repeat_interleave(K)
+    pc = torch.arange(K, device="cuda", dtype=torch.int32).repeat(N)
+    tg = d2.d2_w2_pairs(ctx, db, x, w, pb, pc)
+    p = d2.Pruner(ctx, d, hidden=64, embed=32, seed=19)
+    p.train(db, x, w, pb, pc, tg, steps=300, batch=256, lr=2e-3, seed=2)
+    # move the centroids: one B-ADMM update on a perturbed clustering
+    g = torch.Generator().manual_seed(3)
+    lab2 = torch.where(torch.rand(N, generator=g) < 0.3, torch.randint(0, K, (N,), generator=g), lab)
+    o2 = torch.sort(lab2, stable=True).indices
+    co2 = torch.zeros(K + 1, dtype=torch.int64)
+    co2[1:] = torch.cumsum(torch.bincount(lab2, minlength=K), 0)
+    x2, w2 = x.clone(), w.clone()
+    d2.badmm_barycenter(ctx, db, co2.cuda(), o2.cuda(), x2, w2, None, None, d2.badmm_opts(iters=40))
+    ids = torch.arange(0, N, 4, device="cuda")
+    delta = p.calibrate(db, x2, w2, ids)
+    assert delta > 0
+    p.set_margin(3, delta)
+    ref, _ = d2.d2_assign(ctx, db, x2, w2)
+    got, _, st = d2.d2_assign(ctx, db, x2, w2, prune=p, want_stats=True)
+    mis = float((got != ref).float().mean())
+    assert mis <= 0.01, mis
+    assert st["exact_solves"] < N * K
+    xc, wc, lc, oc = d2.d2_cluster(ctx, db, K, m, seed=4, rounds=3,
+                                   opts=d2.badmm_opts(iters=20, recalibrate=True), prune=p)
+    assert all(np.isfinite(oc))
