@@ -901,11 +901,10 @@ __global__ void __launch_bounds__(128) k_xpartial_pipe(const int64_t* members, c
     const int R = s_pre[nm];
     const int ntile = (R + XP_ROWS - 1) / XP_ROWS;
     const int td = tid & 15, ti = tid >> 4;   // dd = td*4 .. +3, i = ti*4 .. +3
-    float acc[4][4];
+    // accumulators in pairs along dd: acc2[u][h] = (acc[u][2h], acc[u][2h+1])
+    unsigned long long acc2[4][2];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+    for (int u = 0; u < 4; ++u) acc2[u][0] = acc2[u][1] = 0ull;
 
     auto rows_of = [&](int t, int b) {  // global rows of tile t into s_row[b]
         if (tid < XP_ROWS) {
@@ -959,13 +958,26 @@ __global__ void __launch_bounds__(128) k_xpartial_pipe(const int64_t* members, c
             const float4 pv = *reinterpret_cast<const float4*>(&ps[b][r][ti * 4]);
             const float4 yv = *reinterpret_cast<const float4*>(&ys[b][r][td * 4]);
             const float pa[4] = {pv.x, pv.y, pv.z, pv.w};
-            const float ya[4] = {yv.x, yv.y, yv.z, yv.w};
+            unsigned long long y01, y23;
+            asm("mov.b64 %0, {%1, %2};" : "=l"(y01) : "f"(yv.x), "f"(yv.y));
+            asm("mov.b64 %0, {%1, %2};" : "=l"(y23) : "f"(yv.z), "f"(yv.w));
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(pa[u], ya[v], acc[u][v]);
+            for (int u = 0; u < 4; ++u) {
+                // two FP32 fused multiply-adds per instruction (each rounded once,
+                // as fmaf): acc[u][v] += pa[u] * ya[v]
+                unsigned long long pu;
+                asm("mov.b64 %0, {%1, %1};" : "=l"(pu) : "f"(pa[u]));
+                asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc2[u][0]) : "l"(pu), "l"(y01));
+                asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc2[u][1]) : "l"(pu), "l"(y23));
+            }
         }
         __syncthreads();
+    }
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[u][0]), "=f"(acc[u][1]) : "l"(acc2[u][0]));
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[u][2]), "=f"(acc[u][3]) : "l"(acc2[u][1]));
     }
     float* out = xpart + q * (int64_t)m * d;
 #pragma unroll
