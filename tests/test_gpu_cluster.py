@@ -209,3 +209,18 @@ def test_d2_cluster_bounded_assignment_matches_exact(d2, ctx):
     assert torch.equal(a[2], b[2])
     assert a[3] == b[3]
     assert ctx.cluster_stats()["exact_solves"] < bags.N * K * rounds
+
+
+def test_d2_cluster_with_split_streams_and_tensor_core_cost(d2, ctx):
+    """The clustering loop with every update as a split call on the
+    split-BF16 tensor-core cost build: labels and objectives per round equal
+    those of one-stream updates (clusters are independent in the update)."""
+    bags = synth.gaussian_class_bags(66, 300, 32, 5, mk=(8, 30), mu_sigma=2.0)
+    db = d2.DeviceBags.from_synth(bags)
+    K, m, rounds = 5, 8, 3
+    a = d2.d2_cluster(ctx, db, K, m, seed=12, rounds=rounds, opts=d2.badmm_opts(iters=20, cost="bf16x3"))
+    b = d2.d2_cluster(ctx, db, K, m, seed=12, rounds=rounds,
+                      opts=d2.badmm_opts(iters=20, cost="bf16x3", split_streams=True))
+    assert torch.equal(a[2], b[2])
+    assert a[3] == b[3]
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
