@@ -52,14 +52,15 @@ struct AssignArgs {
 // which is only cleared after the cost is built, whenever it fits there
 __host__ __device__ static inline bool staging_in_flows(int m, int nmax) { return AS_DC * (m + nmax) <= m * nmax; }
 
+// Per-warp shared memory: the cost and flow tableaus, the initial potentials
+// and excesses (moved to registers once the greedy start is done), the
+// predecessor of every node, and the cost-build staging.
 struct WarpMem {
     float* C;      // m x n
     float* F;      // m x n
     float* pot;    // V
-    float* dist;   // V
     float* exc;    // V
     short* pred;   // V
-    unsigned char* vis;  // V
     float* xs;     // AS_DC x m
     float* ys;     // AS_DC x n
 };
@@ -313,8 +314,7 @@ __global__ void k_w2_pairs(AssignArgs a) {
     s.C = reinterpret_cast<float*>(base);
     s.F = s.C + m * n;
     s.pot = s.F + m * n;
-    s.dist = s.pot + V;
-    s.exc = s.dist + V;
+    s.exc = s.pot + V;
     if (staging_in_flows(m, n)) {
         s.xs = s.F;
         s.ys = s.F + AS_DC * m;
@@ -324,7 +324,6 @@ __global__ void k_w2_pairs(AssignArgs a) {
         s.ys = s.xs + AS_DC * m;
         s.pred = reinterpret_cast<short*>(s.ys + AS_DC * n);
     }
-    s.vis = reinterpret_cast<unsigned char*>(s.pred + V);
 
     int64_t total;
     if (a.mode == 0) total = a.npairs;
@@ -389,7 +388,7 @@ __global__ void k_argmin_rows(const float* D, int64_t N, int K, int32_t* labels,
 size_t d2_assign_warp_bytes(int m, int nmax) {
     const int V = m + nmax;
     const int stage = staging_in_flows(m, nmax) ? 0 : AS_DC * (m + nmax);
-    size_t b = (size_t)(2 * m * nmax + 3 * V + stage) * 4 + (size_t)V * 2 + V;
+    size_t b = (size_t)(2 * m * nmax + 2 * V + stage) * 4 + (size_t)V * 2;
     return (b + 15) & ~(size_t)15;
 }
 
