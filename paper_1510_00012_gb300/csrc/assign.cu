@@ -100,7 +100,10 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
     const float* xc = a.x + (int64_t)cent * m * d;
 
     // ---- cost C[i][j] = sum_dd (x_i - y_j)^2 by direct differences
-    for (int e = lane; e < m * n; e += 32) s.C[e] = 0.f;
+    // tableau rows are ns = n | 1 floats apart (odd: a column walk across
+    // rows touches distinct banks)
+    const int ns = n | 1;
+    for (int e = lane; e < m * ns; e += 32) s.C[e] = 0.f;
     for (int d0 = 0; d0 < d; d0 += AS_DC) {
         const int dc = min(AS_DC, d - d0);
         __syncwarp();
@@ -115,16 +118,16 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
         __syncwarp();
         for (int e = lane; e < m * n; e += 32) {
             int i = e / n, j = e - i * n;
-            float acc = s.C[e];
+            float acc = s.C[i * ns + j];
             for (int t = 0; t < dc; ++t) {
                 float df = s.xs[t * m + i] - s.ys[t * n + j];
                 acc = fmaf(df, df, acc);
             }
-            s.C[e] = acc;
+            s.C[i * ns + j] = acc;
         }
     }
     // ---- initial state
-    for (int e = lane; e < m * n; e += 32) s.F[e] = 0.f;
+    for (int e = lane; e < m * ns; e += 32) s.F[e] = 0.f;
     for (int v = lane; v < V; v += 32) {
         s.exc[v] = (v < m) ? a.w[(int64_t)cent * m + v] : a.wt[r0 + (v - m)];
         s.pot[v] = 0.f;
@@ -135,7 +138,7 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
         float mn = AS_INF;
         int am = 0;
         for (int i = 0; i < m; ++i) {
-            float c = s.C[i * n + j];
+            float c = s.C[i * ns + j];
             if (c < mn) {
                 mn = c;
                 am = i;
@@ -150,7 +153,7 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
             int i = s.pred[m + j];
             float f = fminf(s.exc[m + j], s.exc[i]);
             if (f > 0.f) {
-                s.F[i * n + j] += f;
+                s.F[i * ns + j] += f;
                 s.exc[m + j] -= f;
                 s.exc[i] -= f;
             }
@@ -218,7 +221,7 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
             }
             const float pu = node_bcast<TV>(pot, u);
             if (u < m) {
-                const float* crow = s.C + u * n;
+                const float* crow = s.C + u * ns;
 #pragma unroll
                 for (int t = 0; t < TV; ++t) {
                     const int v = lane + 32 * t;
@@ -236,8 +239,8 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
 #pragma unroll
                 for (int t = 0; t < TV; ++t) {
                     const int i = lane + 32 * t;
-                    if (i < m && !((vis >> t) & 1u) && s.F[i * n + j] > tol) {
-                        const float rc = fmaxf(-s.C[i * n + j] + pu - pot[t], 0.f);
+                    if (i < m && !((vis >> t) & 1u) && s.F[i * ns + j] > tol) {
+                        const float rc = fmaxf(-s.C[i * ns + j] + pu - pot[t], 0.f);
                         const float nd = du + rc;
                         if (nd < dist[t]) {
                             dist[t] = nd;
@@ -267,7 +270,7 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
                     src_node = v;
                     break;
                 }
-                if (v < m) dflow = fminf(dflow, s.F[v * n + (p - m)]);  // backward arc (v, p - m)
+                if (v < m) dflow = fminf(dflow, s.F[v * ns + (p - m)]);  // backward arc (v, p - m)
                 v = p;
             }
         }
@@ -280,10 +283,10 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
                 const int p = s.pred[v];
                 if (p < 0) break;
                 if (v >= m) {  // forward arc p -> v
-                    s.F[p * n + (v - m)] += delta;
+                    s.F[p * ns + (v - m)] += delta;
                 } else {       // backward arc: flow on (v, p - m) decreases
-                    const float f = s.F[v * n + (p - m)] - delta;
-                    s.F[v * n + (p - m)] = f > 0.f ? f : 0.f;
+                    const float f = s.F[v * ns + (p - m)] - delta;
+                    s.F[v * ns + (p - m)] = f > 0.f ? f : 0.f;
                 }
                 v = p;
             }
@@ -298,7 +301,7 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
     }
     // ---- cost of the flow, FP64
     double acc = 0.0;
-    for (int e = lane; e < m * n; e += 32) acc += (double)s.F[e] * (double)s.C[e];
+    for (int e = lane; e < m * ns; e += 32) acc += (double)s.F[e] * (double)s.C[e];  // padding: F = 0, C = 0
     acc = group_sum_d<32>(acc);
     return acc;
 }
@@ -312,8 +315,8 @@ __global__ void k_w2_pairs(AssignArgs a) {
     const int m = a.m, n = a.nmax, V = m + n;
     WarpMem s;
     s.C = reinterpret_cast<float*>(base);
-    s.F = s.C + m * n;
-    s.pot = s.F + m * n;
+    s.F = s.C + m * (n | 1);
+    s.pot = s.F + m * (n | 1);
     s.exc = s.pot + V;
     if (staging_in_flows(m, n)) {
         s.xs = s.F;
@@ -388,7 +391,7 @@ __global__ void k_argmin_rows(const float* D, int64_t N, int K, int32_t* labels,
 size_t d2_assign_warp_bytes(int m, int nmax) {
     const int V = m + nmax;
     const int stage = staging_in_flows(m, nmax) ? 0 : AS_DC * (m + nmax);
-    size_t b = (size_t)(2 * m * nmax + 2 * V + stage) * 4 + (size_t)V * 2;
+    size_t b = (size_t)(2 * m * (nmax | 1) + 2 * V + stage) * 4 + (size_t)V * 2;
     return (b + 15) & ~(size_t)15;
 }
 
