@@ -20,6 +20,9 @@
 
 #define AS_DC 8        // support dimensions staged per step of the cost build
 #define AS_INF 3.0e38f
+// deficit sinks collected per shortest-path pass: 4 for problems of more than
+// 64 nodes (half the passes); small problems keep one (measured faster)
+#define AS_KT(TV) ((TV) <= 2 ? 1 : 4)
 
 struct AssignArgs {
     const int64_t* offsets;
@@ -196,7 +199,10 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
             dist[t] = (v < m && exc[t] > tol) ? 0.f : AS_INF;
             if (v < V) s.pred[v] = -1;
         }
-        int target = -1;
+        // up to AS_KT deficit sinks per pass (settled in order of distance);
+        // the shortest paths to all of them become tight arcs after the
+        // potential update, so flow is pushed along each (primal-dual step)
+        int kt = 0, tg0 = -1, tg1 = -1, tg2 = -1, tg3 = -1;
         for (int it = 0; it < V; ++it) {
             // warp argmin over unsettled nodes: smallest distance, then lowest index
             float bv = AS_INF;
@@ -216,8 +222,8 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
             const float du = __uint_as_float(kmin);
             if ((u & 31) == lane) vis |= 1u << (u >> 5);
             if (u >= m && node_bcast<TV>(exc, u) > tol) {
-                target = u;
-                break;
+                if (kt == 0) tg0 = u; else if (kt == 1) tg1 = u; else if (kt == 2) tg2 = u; else tg3 = u;
+                if (++kt == AS_KT(TV)) break;
             }
             const float pu = node_bcast<TV>(pot, u);
             if (u < m) {
@@ -250,54 +256,61 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
                 }
             }
         }
-        if (target < 0) {
+        if (kt == 0) {
             hit_limit = true;  // no augmenting path (cannot happen with balanced supplies)
             break;
         }
-        // ---- potentials: pot += min(dist, dist[target])
-        const float dt = node_bcast<TV>(dist, target);
+        // ---- potentials: pot += min(dist, dist of the last target)
+        const int tlast = kt == 1 ? tg0 : kt == 2 ? tg1 : kt == 3 ? tg2 : tg3;
+        const float dt = node_bcast<TV>(dist, tlast);
 #pragma unroll
         for (int t = 0; t < TV; ++t) pot[t] += ((vis >> t) & 1u) ? fminf(dist[t], dt) : dt;
         __syncwarp();
-        // ---- augment along the path: lane 0 walks it (flows in shared memory)
-        float dflow = AS_INF;
-        int src_node = target;
-        if (lane == 0) {
-            int v = target;
-            for (int guard = 0; guard <= V; ++guard) {
-                const int p = s.pred[v];
-                if (p < 0) {
-                    src_node = v;
-                    break;
+        // ---- augment along each target's path in turn: lane 0 walks it
+        // (flows in shared memory); a path whose bottleneck an earlier push
+        // used up carries nothing
+        for (int q = 0; q < kt; ++q) {
+            const int target = q == 0 ? tg0 : q == 1 ? tg1 : q == 2 ? tg2 : tg3;
+            float dflow = AS_INF;
+            int src_node = target;
+            if (lane == 0) {
+                int v = target;
+                for (int guard = 0; guard <= V; ++guard) {
+                    const int p = s.pred[v];
+                    if (p < 0) {
+                        src_node = v;
+                        break;
+                    }
+                    if (v < m) dflow = fminf(dflow, s.F[v * ns + (p - m)]);  // backward arc (v, p - m)
+                    v = p;
                 }
-                if (v < m) dflow = fminf(dflow, s.F[v * ns + (p - m)]);  // backward arc (v, p - m)
-                v = p;
             }
-        }
-        src_node = __shfl_sync(0xffffffffu, src_node, 0);
-        dflow = __shfl_sync(0xffffffffu, dflow, 0);
-        const float delta = fminf(fminf(dflow, node_bcast<TV>(exc, target)), node_bcast<TV>(exc, src_node));
-        if (lane == 0) {
-            int v = target;
-            for (int guard = 0; guard <= V; ++guard) {
-                const int p = s.pred[v];
-                if (p < 0) break;
-                if (v >= m) {  // forward arc p -> v
-                    s.F[p * ns + (v - m)] += delta;
-                } else {       // backward arc: flow on (v, p - m) decreases
-                    const float f = s.F[v * ns + (p - m)] - delta;
-                    s.F[v * ns + (p - m)] = f > 0.f ? f : 0.f;
+            src_node = __shfl_sync(0xffffffffu, src_node, 0);
+            dflow = __shfl_sync(0xffffffffu, dflow, 0);
+            const float delta = fminf(fminf(dflow, node_bcast<TV>(exc, target)), node_bcast<TV>(exc, src_node));
+            if (!(delta > 0.f)) continue;
+            if (lane == 0) {
+                int v = target;
+                for (int guard = 0; guard <= V; ++guard) {
+                    const int p = s.pred[v];
+                    if (p < 0) break;
+                    if (v >= m) {  // forward arc p -> v
+                        s.F[p * ns + (v - m)] += delta;
+                    } else {       // backward arc: flow on (v, p - m) decreases
+                        const float f = s.F[v * ns + (p - m)] - delta;
+                        s.F[v * ns + (p - m)] = f > 0.f ? f : 0.f;
+                    }
+                    v = p;
                 }
-                v = p;
             }
-        }
 #pragma unroll
-        for (int t = 0; t < TV; ++t) {
-            const int v = lane + 32 * t;
-            if (v == target) exc[t] -= delta;
-            if (v == src_node) exc[t] -= delta;
+            for (int t = 0; t < TV; ++t) {
+                const int v = lane + 32 * t;
+                if (v == target) exc[t] -= delta;
+                if (v == src_node) exc[t] -= delta;
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
     // ---- cost of the flow, FP64
     double acc = 0.0;
