@@ -184,12 +184,14 @@ def test_badmm_tensor_core_vocabulary(d2, ctx, precision):
     _check_badmm(bags, co, mem, x0, w0, gx, gw, gplan, gobj, precision, 25, 10)
 
 
-def test_bounded_wait_expiry_is_reported(d2, ctx):
+@pytest.mark.parametrize("d", [64, 128])
+def test_bounded_wait_expiry_is_reported(d2, ctx, d):
     """The build's only device-side wait (its MMA completion) is bounded: with
     the testing flag the first tile's MMAs are not issued, the wait expires
     after about 2 s, the CTA stops and frees its tensor memory, and the host
-    reads D2_ETIMEOUT; the context stays usable for the next call."""
-    bags = synth.gaussian_class_bags(47, 6, 64, 1, mk=(4, 16))
+    reads D2_ETIMEOUT; the context stays usable for the next call.  d = 64
+    has one K block per tile (single A buffer), d = 128 two (double-buffered)."""
+    bags = synth.gaussian_class_bags(47, 6, d, 1, mk=(4, 16))
     co, mem = split_clusters(torch.zeros(bags.N, dtype=torch.int64), 1)
     x0, _ = synth.sample_initial_barycenters(48, bags, co, mem, 32)
     db = d2.DeviceBags.from_synth(bags)
