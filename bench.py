@@ -420,6 +420,24 @@ def docs_clustering(d2, ctx, dev, seed, n_docs=None):
     d2.badmm_barycenter(ctx, db, co, order.contiguous(), xb, wb, None, None, opts)
     xb, wb = xq.clone(), wq.clone()
     _, t_b = timed(lambda: d2.badmm_barycenter(ctx, db, co, order.contiguous(), xb, wb, None, None, opts))
+    # the same update once more with per-launch CUDA events: the fused plan
+    # sweep's HBM roofline on this workload and the kernel split
+    xb, wb = xq.clone(), wq.clone()
+    ctx.timing(True)
+    d2.badmm_barycenter(ctx, db, co, order.contiguous(), xb, wb, None, None, opts)
+    torch.cuda.synchronize()
+    kt = ctx.timing_read()
+    ctx.timing(False)
+    f_ms, f_n = kt["sweep_fused"]
+    if f_n:
+        peak, peak_kind = load_peaks()
+        sbytes = BYTES_PER_ENTRY * m * bags.n
+        ach = sbytes / (f_ms / f_n * 1e-3) / 1e9
+        out["sweep_roofline"] = {"bound": "hbm", "kernel": "k_sweep_pipe (fused B+A pass, default shape)",
+                                 "achieved": ach, "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+                                 "frac": ach / peak, "algorithmic_bytes_per_launch": sbytes,
+                                 "avg_launch_ms": f_ms / f_n, "launches": f_n}
+    out["badmm_kernel_breakdown_ms"] = {k: {"ms": v[0], "launches": v[1]} for k, v in kt.items() if v[1]}
     out.update({"badmm_update_s": t_b, "badmm_updates_per_s": m * bags.n * W["iters"] / t_b,
                 "full_K_solves_per_round": bags.N * K,
                 "pruner": {"r": 8, "delta": delta, "train_pairs": npairs, "target_s": t_tg, "train_s": t_train,

@@ -650,13 +650,21 @@ static SweepFn pipe_with(int m, int nv, size_t* smem, int* lpr) {
     return pipe_variant<32, 1>(smem, lpr);
 }
 
+// Default shape without the autotuner: two float4s per lane unless that ring
+// leaves room for only one CTA per SM and the one-float4 ring exists (at
+// m = 64, 8 lanes x 2 float4 at 1 CTA/SM measured 18 % slower than 16 lanes x
+// 1 float4 at 3 CTAs/SM).
 static SweepFn pick_sweep_pipe(int m, size_t* smem) {
     int lpr = 0;
-    if (D2_PIPE_NV == 2) {
-        SweepFn f = pipe_with(m, 2, smem, &lpr);
-        if (f) return f;
+    size_t s2 = 0, s1 = 0;
+    SweepFn f2 = D2_PIPE_NV == 2 ? pipe_with(m, 2, &s2, &lpr) : nullptr;
+    SweepFn f1 = pipe_with(m, 1, &s1, &lpr);
+    if (f2 && (s2 <= 110 * 1024 || !f1)) {
+        *smem = s2;
+        return f2;
     }
-    return pipe_with(m, 1, smem, &lpr);
+    if (f1) *smem = s1;
+    return f1;
 }
 
 static SweepFn pick_sweep(int m, int* lpr = nullptr, int* nv = nullptr) {
