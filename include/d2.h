@@ -89,6 +89,12 @@ extern "C" {
                                about 16 mantissa bits                           */
 #define D2_COST_BF16X6 0xC0 /* each factor split hi + mid + lo (BF16, exact for
                                FP32 inputs), six products: FP32-level error     */
+/* Bags stored as vocabulary indices (symbolic supports, Section 5) with a
+ * tensor-core cost precision: by default each cluster's cost rows are built
+ * once per distinct word of its members (a per-call table) and gathered into
+ * the j-major rows; the result is bitwise that of building every row.  This
+ * flag builds every support row directly instead. */
+#define D2_COST_ROWS 0x1000
 /* Testing only (d2_cost): the tensor-core build issues no MMA for each CTA's
  * first tile, so that CTA's bounded wait expires (about 2 s); the CTA then
  * stops, the call's output is undefined and d2_device_errors reports

@@ -369,6 +369,14 @@ __global__ void k_chunk_fill(const int64_t* cofs, int K, const int64_t* chunk_fi
     }
 }
 
+int d2_build_chunks(d2_ctx* ctx, const int64_t* cofs, int K, const ClusterWs& cw, cudaStream_t st) {
+    k_chunk_scan<<<1, 1024, 0, st>>>(cofs, K, cw.chunk_first, cw.nchunks);
+    D2_LAUNCH_CK(ctx, "k_chunk_scan");
+    k_chunk_fill<<<(unsigned)d2_ceil_div(K, 256), 256, 0, st>>>(cofs, K, cw.chunk_first, cw.chunks);
+    D2_LAUNCH_CK(ctx, "k_chunk_fill");
+    return D2_OK;
+}
+
 int d2_setup_clusters(d2_ctx* ctx, const int64_t* cofs, int64_t P, int K, int32_t** pos_cluster,
                       ClusterWs* cw, cudaStream_t st) {
     void* pc = nullptr;

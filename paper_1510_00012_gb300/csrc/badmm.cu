@@ -1225,10 +1225,12 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
     void *vpc = nullptr, *vcs = nullptr;
     if ((rc = d2_ws(ctx, WS_POS_CLUSTER, (size_t)P * 4, &vpc))) return rc;
     if (need_sums && (rc = d2_ws(ctx, WS_CHUNK_SUM, (size_t)maxch * 16, &vcs))) return rc;
+    const int cost_prec = d2_cost_prec(opts.flags);
+    const bool use_vt = d2_vocab_table_applies(bags, K, m, cost_prec, opts.flags);
+    if (use_vt && (rc = d2_vocab_reserve(ctx, bags, K, m, cw))) return rc;
     // the cluster workspace may have moved while growing the others
     rc = d2_cluster_ws(ctx, K, m, d, P, &cw);
     if (rc) return rc;
-    const int cost_prec = d2_cost_prec(opts.flags);
     if ((rc = d2_cost_prepare(ctx, bags, m, cost_prec))) return rc;
     int32_t* pos_cluster = static_cast<int32_t*>(vpc);
     double* chunk_sum = need_sums ? static_cast<double*>(vcs) : nullptr;
@@ -1306,7 +1308,9 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
     D2_CK(ctx, cudaMemcpyAsync(cw.wb[0], w, (size_t)K * m * 4, cudaMemcpyDeviceToDevice, st));
     // initial cost and rho (Eq. rho)
     if ((rc = d2_prep_x(ctx, x, K, m, d, cw, st))) return rc;
-    if ((rc = d2_cost_rows(ctx, bags, members, P, K, m, cw, cost, need_sums, cost_prec, st))) return rc;
+    if ((rc = d2_cost_rows(ctx, bags, members, P, K, m, cw, cost, need_sums, cost_prec,
+                           use_vt ? D2_VT_SETUP : D2_VT_OFF, st)))
+        return rc;
     k_rho<<<(unsigned)d2_ceil_div(K, 128), 128, 0, st>>>(K, m, cw.chunk_first, chunk_sum, chunk_rows,
                                                         opts.rho0, opts.rho, cw.rho, cw.beta, cw.nrows);
     D2_LAUNCH_CK(ctx, "k_rho");
@@ -1374,7 +1378,9 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
             d2_time_end(ctx, st);
             D2_LAUNCH_CK(ctx, "k_xfinal");
             if ((rc = d2_prep_x(ctx, x, K, m, d, cw, st))) return rc;
-            if ((rc = d2_cost_rows(ctx, bags, members, P, K, m, cw, cost, false, cost_prec, st))) return rc;
+            if ((rc = d2_cost_rows(ctx, bags, members, P, K, m, cw, cost, false, cost_prec,
+                                   use_vt ? D2_VT_REUSE : D2_VT_OFF, st)))
+                return rc;
             // A step from Pi2^n
             if ((rc = launch(SW_A | objf, wbuf(it), wbuf(it + 1)))) return rc;
         } else {

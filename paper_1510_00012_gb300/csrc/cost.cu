@@ -431,8 +431,27 @@ int d2_cost_prepare(d2_ctx* ctx, const d2_bags* b, int m, int prec) {
 }
 
 int d2_cost_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t P, int K, int m,
-                 const ClusterWs& cw, float* C, bool want_sums, int prec, cudaStream_t st) {
-    int64_t maxch = d2_ceil_div(P, D2_CHUNK) + K + 1;
+                 const ClusterWs& cw, float* C, bool want_sums, int prec, int vt, cudaStream_t st) {
+    const int64_t maxch = d2_ceil_div(P, D2_CHUNK) + K + 1;
+    double* chunk_sum = nullptr;
+    int64_t* chunk_rows = nullptr;
+    if (want_sums) {
+        void* p = nullptr;
+        int rc = d2_ws(ctx, WS_CHUNK_SUM, (size_t)maxch * 16, &p);
+        if (rc) return rc;
+        chunk_sum = static_cast<double*>(p);
+        chunk_rows = reinterpret_cast<int64_t*>(static_cast<char*>(p) + (size_t)maxch * 8);
+    }
+    if (vt != D2_VT_OFF)
+        return d2_vocab_cost_rows(ctx, b, members, P, K, m, cw, C, chunk_sum, chunk_rows, vt == D2_VT_SETUP, prec,
+                                  st);
+    return d2_cost_rows_direct(ctx, b, members, P, K, m, cw, C, chunk_sum, chunk_rows, prec, st);
+}
+
+int d2_cost_rows_direct(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t P, int K, int m,
+                        const ClusterWs& cw, float* C, double* chunk_sum, int64_t* chunk_rows, int prec,
+                        cudaStream_t st) {
+    const int64_t maxch = d2_ceil_div(P, D2_CHUNK) + K + 1;
     CostArgs a;
     a.members = members;
     a.offsets = b->offsets;
@@ -447,15 +466,8 @@ int d2_cost_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t 
     a.chunks = cw.chunks;
     a.nchunks = cw.nchunks;
     a.C = C;
-    a.chunk_sum = nullptr;
-    a.chunk_rows = nullptr;
-    if (want_sums) {
-        void* p = nullptr;
-        int rc = d2_ws(ctx, WS_CHUNK_SUM, (size_t)maxch * 16, &p);
-        if (rc) return rc;
-        a.chunk_sum = static_cast<double*>(p);
-        a.chunk_rows = reinterpret_cast<int64_t*>(static_cast<char*>(p) + (size_t)maxch * 8);
-    }
+    a.chunk_sum = chunk_sum;
+    a.chunk_rows = chunk_rows;
     if (prec) {  // tensor cores where (d, m) make the build a dense contraction
         bool used = false;
         int rc = d2_cost_tc_rows(ctx, b, members, maxch, m, prec, cw, C, a.chunk_sum, a.chunk_rows, st, &used);
@@ -498,8 +510,9 @@ extern "C" int d2_cost(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_
     if (rc) return rc;
     const int prec = d2_cost_prec(flags);
     if ((rc = d2_cost_prepare(ctx, bags, m, prec))) return rc;
+    const int vt = d2_vocab_table_applies(bags, K, m, prec, flags) ? D2_VT_SETUP : D2_VT_OFF;
     ctx->expire_test = (flags & D2_TEST_EXPIRE_WAIT) ? 1 : 0;
-    rc = d2_cost_rows(ctx, bags, members, P, K, m, cw, C_out, false, prec, st);
+    rc = d2_cost_rows(ctx, bags, members, P, K, m, cw, C_out, false, prec, vt, st);
     ctx->expire_test = 0;
     return rc;
 }

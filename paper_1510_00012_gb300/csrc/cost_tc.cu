@@ -341,6 +341,11 @@ bool tc_plan(const d2_bags* b, int m, int prec, TcPlan* p) {
 
 }  // namespace
 
+bool d2_cost_tc_applies(const d2_bags* b, int m, int prec) {
+    TcPlan p;
+    return tc_plan(b, m, prec, &p);
+}
+
 int d2_cost_tc_prepare(d2_ctx* ctx, const d2_bags* b, int m, int prec, bool* used) {
     TcPlan p;
     *used = tc_plan(b, m, prec, &p);

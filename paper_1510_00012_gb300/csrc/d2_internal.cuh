@@ -31,6 +31,8 @@ enum WsSlot {
     WS_PRUNE,        // pruning scratch
     WS_ELKAN,        // triangle-inequality bounds carried across rounds
     WS_SPLIT,        // rebased cluster offsets of the second half of a split call
+    WS_VOCAB,        // vocabulary cost table: word flags, slots, pseudo-members, chunks
+    WS_VOCAB_T,      // vocabulary cost table rows (<= min(n, K V) x m floats)
     WS_NSLOTS
 };
 
@@ -213,6 +215,28 @@ int d2_cost_tc_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64
                     const ClusterWs& cw, float* C, double* chunk_sum, int64_t* chunk_rows, cudaStream_t st,
                     bool* used);
 
-// Cost rows of every member position; accumulates FP64 sums per cluster when csum.
+// Builds the chunk table of a cluster-offsets array (no position map).
+int d2_build_chunks(d2_ctx* ctx, const int64_t* cofs, int K, const ClusterWs& cw, cudaStream_t st);
+
+// Whether the tensor-core build covers (d, m, prec) for these bags.
+bool d2_cost_tc_applies(const d2_bags* b, int m, int prec);
+
+// Vocabulary cost table (cost_vocab.cu): used for bags stored as vocabulary
+// indices when the tensor-core build applies, unless flags has D2_COST_ROWS.
+enum { D2_VT_OFF = 0, D2_VT_SETUP = 1, D2_VT_REUSE = 2 };
+bool d2_vocab_table_applies(const d2_bags* b, int K, int m, int prec, int flags);
+// Sizes its workspaces (before a graph capture, so the capture allocates nothing).
+int d2_vocab_reserve(d2_ctx* ctx, const d2_bags* b, int K, int m, const ClusterWs& cw);
+int d2_vocab_cost_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t P, int K, int m,
+                       const ClusterWs& cw, float* C, double* chunk_sum, int64_t* chunk_rows, bool setup,
+                       int prec, cudaStream_t st);
+
+// Cost rows of every member position; FP64 sums per chunk for Eq. (rho) when
+// want_sums.  vt: D2_VT_OFF builds every row directly; D2_VT_SETUP builds the
+// vocabulary table's word lists for this membership first; D2_VT_REUSE reuses
+// the lists of the previous D2_VT_SETUP call with the same membership.
 int d2_cost_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t P, int K, int m,
-                 const ClusterWs& cw, float* C, bool want_sums, int prec, cudaStream_t st);
+                 const ClusterWs& cw, float* C, bool want_sums, int prec, int vt, cudaStream_t st);
+int d2_cost_rows_direct(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t P, int K, int m,
+                        const ClusterWs& cw, float* C, double* chunk_sum, int64_t* chunk_rows, int prec,
+                        cudaStream_t st);
