@@ -62,7 +62,11 @@ extern "C" {
 #define D2_PRUNE_RECALIBRATE 0x800 /* d2_cluster with a pruner: before every round's
                              assignment, d2_prune_calibrate on 1,000 bags (evenly
                              spaced ids) against the current centroids, quantile
-                             0.999 (this updates the pruner's delta)          */
+                             0.999 (this updates the pruner's delta); a round
+                             whose sample says the pruner cannot pay (r + f K >=
+                             0.8 K, f its fall-back fraction) skips it: exact
+                             assignment (certified-bound with D2_ASSIGN_BOUNDED),
+                             every bag counted as a fall-back                 */
 #define D2_SPLIT_STREAMS 0x400 /* badmm_barycenter: run two halves of the clusters
                              (split at half the members) concurrently on two
                              internal streams, each in a child context that
@@ -286,6 +290,10 @@ int d2_prune_get_margin(const d2_prune* p, int32_t* r, float* delta);
 int d2_prune_calibrate(d2_ctx* ctx, d2_prune* p, const d2_bags* bags, int32_t K, int32_t m,
                        const float* x, const float* w, const int64_t* ids, int64_t nids,
                        float quantile, void* stream);
+/* Fraction of the last d2_prune_calibrate sample whose margin test fails
+ * under the new delta (those bags would be solved against all K); -1 before
+ * any calibration. */
+int d2_prune_get_calibration(const d2_prune* p, float* fallback_frac);
 
 /* Embeddings f(P) of the bags listed in `ids` (device, cnt) -> emb (device,
  * cnt x E) and their means mu (device, cnt x d). */

@@ -89,6 +89,7 @@ _SIGS = {
     "d2_prune_get_margin": (c_int, [c_void_p, c_void_p, c_void_p]),
     "d2_prune_calibrate": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
                                    c_void_p, c_int64, c_float, c_void_p]),
+    "d2_prune_get_calibration": (c_int, [c_void_p, c_void_p]),
     "d2_prune_embed": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p,
                                c_void_p]),
     "d2_prune_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
@@ -429,6 +430,12 @@ class Pruner:
         self.ctx.check(lib().d2_prune_calibrate(self.ctx.h, self.h, bags.ref(), K, m, _ptr(x), _ptr(w),
                                                 _ptr(ids), ids.numel(), float(quantile), _stream()))
         return self.margin()[1]
+
+    def calibration_fallbacks(self):
+        """Fraction of the last calibration sample whose margin test fails (-1 before any)."""
+        f = c_float()
+        self.ctx.check(lib().d2_prune_get_calibration(self.h, ctypes.byref(f)))
+        return float(f.value)
 
     def embed(self, bags, ids):
         _need(ids, torch.int64, "ids")

@@ -368,7 +368,9 @@ extern "C" int d2_cluster(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m
     void* scnt = nullptr;
     if ((rc = d2_ws(ctx, WS_SCAN, 64, &scnt))) return rc;
     int64_t* acounters = static_cast<int64_t*>(scnt);
+    int64_t bypass_fallbacks = 0;  // bags of the rounds that skipped the pruner
     for (int r = 0; r < rounds; ++r) {
+        bool use_prune = prune != nullptr;
         if (elkan) {
             if ((rc = d2_assign_elkan(ctx, bags, K, m, x_out, w_out, r == 0 ? nullptr : x_prev,
                                       r == 0 ? nullptr : w_prev, lab, dist, solves, st)))
@@ -387,9 +389,16 @@ extern "C" int d2_cluster(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m
                 if ((rc = d2_prune_calibrate(ctx, const_cast<d2_prune*>(prune), bags, K, m, x_out, w_out,
                                              static_cast<int64_t*>(vid), ns, 0.999f, stream)))
                     return rc;
+                // a round where most bags would fall back to all K anyway skips the pruner
+                int32_t pr_r = 0;
+                float pr_delta = 0.f, fb = 0.f;
+                d2_prune_get_margin(prune, &pr_r, &pr_delta);
+                d2_prune_get_calibration(prune, &fb);
+                use_prune = !((double)pr_r + (double)fb * K >= 0.8 * K);
+                if (!use_prune) bypass_fallbacks += N;
             }
-            if ((rc = assign_any(ctx, bags, K, m, x_out, w_out, prune, (o.flags & D2_ASSIGN_BOUNDED) != 0, lab, dist,
-                                 nullptr, stream)))
+            if ((rc = assign_any(ctx, bags, K, m, x_out, w_out, use_prune ? prune : nullptr,
+                                 (o.flags & D2_ASSIGN_BOUNDED) != 0, lab, dist, nullptr, stream)))
                 return rc;
             k_acc_counts<<<1, 1, 0, st>>>(solves, acounters);
             D2_LAUNCH_CK(ctx, "k_acc_counts");
@@ -417,7 +426,7 @@ extern "C" int d2_cluster(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m
     D2_CK(ctx, cudaMemcpyAsync(hs, solves, sizeof(hs), cudaMemcpyDeviceToHost, st));
     D2_CK(ctx, cudaStreamSynchronize(st));
     ctx->cluster_solves = hs[0];
-    ctx->cluster_fallbacks = hs[1];
+    ctx->cluster_fallbacks = hs[1] + bypass_fallbacks;
     return D2_OK;
 }
 

@@ -30,6 +30,7 @@ struct d2_prune {
     int d = 0, H = 0, E = 0;
     int r = 8;
     float delta = 0.f;
+    float fb_frac = -1.f;      // fall-back fraction estimated by the last d2_prune_calibrate
     int64_t nparam = 0;
     int64_t oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0;
     float* params = nullptr;   // FP32 masters
@@ -959,7 +960,7 @@ extern "C" int d2_prune_calibrate(d2_ctx* ctx, d2_prune* p, const d2_bags* bags,
     D2_CK(ctx, cudaMemcpy(FC.data(), cf, FC.size() * 4, cudaMemcpyDeviceToHost));
     D2_CK(ctx, cudaMemcpy(MUC.data(), cmu, MUC.size() * 4, cudaMemcpyDeviceToHost));
     D2_CK(ctx, cudaMemcpy(T.data(), tg, T.size() * 4, cudaMemcpyDeviceToHost));
-    std::vector<double> err(np);
+    std::vector<double> err(np), MT(np), PRED(np);
     for (int64_t i = 0; i < nids; ++i)
         for (int c = 0; c < K; ++c) {
             double mt = 0, pr = 0;
@@ -971,11 +972,41 @@ extern "C" int d2_prune_calibrate(d2_ctx* ctx, d2_prune* p, const d2_bags* bags,
                 const double v = (double)F[i * p->E + e] - FC[(size_t)c * p->E + e];
                 pr += v * v;
             }
+            MT[i * K + c] = mt;
+            PRED[i * K + c] = mt + pr;
             err[i * K + c] = std::fabs(mt + pr - (double)T[i * K + c]);
         }
     const int64_t q = std::min<int64_t>(np - 1, std::max<int64_t>(0, (int64_t)std::ceil((double)quantile * np) - 1));
     std::nth_element(err.begin(), err.begin() + q, err.end());
     p->delta = (float)err[q];
+    // the margin test of the pruned assignment replayed on the sample with the
+    // new delta: candidates = the r smallest predictions (ties: lower index),
+    // b = their best exact W^2; the bag falls back to all K when some other
+    // centroid's bound max(mean term, prediction - delta) does not exceed b
+    const int r = std::min(p->r, (int)K);
+    int64_t fails = 0;
+    std::vector<int> order(K);
+    for (int64_t i = 0; i < nids; ++i) {
+        const double* pi = PRED.data() + i * K;
+        for (int c = 0; c < K; ++c) order[c] = c;
+        std::partial_sort(order.begin(), order.begin() + r, order.end(),
+                          [&](int a, int b) { return pi[a] < pi[b] || (pi[a] == pi[b] && a < b); });
+        double b = 3.0e38;
+        for (int t = 0; t < r; ++t) b = std::min(b, (double)T[i * K + order[t]]);
+        bool fail = false;
+        for (int t = r; t < K && !fail; ++t) {
+            const int c = order[t];
+            fail = !(std::max(MT[i * K + c], pi[c] - (double)p->delta) > b);
+        }
+        fails += fail;
+    }
+    p->fb_frac = (float)((double)fails / (double)nids);
+    return D2_OK;
+}
+
+extern "C" int d2_prune_get_calibration(const d2_prune* p, float* fallback_frac) {
+    if (!p || !fallback_frac) return D2_EINVAL;
+    *fallback_frac = p->fb_frac;
     return D2_OK;
 }
 

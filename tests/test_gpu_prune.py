@@ -170,3 +170,52 @@ def test_calibrated_margin_follows_moved_centroids(d2, ctx):
     xc, wc, lc, oc = d2.d2_cluster(ctx, db, K, m, seed=4, rounds=3,
                                    opts=d2.badmm_opts(iters=20, recalibrate=True), prune=p)
     assert all(np.isfinite(oc))
+
+
+def test_calibration_fallback_estimate_and_round_bypass(d2, ctx):
+    """The calibration replays the margin test on its sample: its fall-back
+    fraction matches the pruned assignment of the same bags.  On near-tie
+    document bags an untrained pruner (random weights, wide delta) would send
+    almost every bag to all K, so every recalibrated round of d2_cluster skips
+    it: the labels are those of the exact loop and every bag of every round
+    counts as a fall-back."""
+    K, m, d = 10, 8, 8
+    bags = synth.gaussian_class_bags(23, 600, d, K, mk=(8, 24), mu_sigma=1.5, alpha=1.0)
+    db = d2.DeviceBags.from_synth(bags)
+    lab = bags.labels
+    order = torch.sort(lab, stable=True).indices
+    co = torch.zeros(K + 1, dtype=torch.int64)
+    co[1:] = torch.cumsum(torch.bincount(lab, minlength=K), 0)
+    x, w = synth.sample_initial_barycenters(24, bags, co, order, m)
+    x, w = x.cuda(), w.cuda()
+    N = bags.N
+    pb = torch.arange(N, device="cuda").repeat_interleave(K)
+    pc = torch.arange(K, device="cuda", dtype=torch.int32).repeat(N)
+    tg = d2.d2_w2_pairs(ctx, db, x, w, pb, pc)
+    p = d2.Pruner(ctx, d, hidden=64, embed=32, seed=25)
+    assert p.calibration_fallbacks() == -1.0
+    p.train(db, x, w, pb, pc, tg, steps=300, batch=256, lr=2e-3, seed=2)
+    p.set_margin(3, p.margin()[1])
+    p.calibrate(db, x, w, torch.arange(N, device="cuda"))
+    est = p.calibration_fallbacks()
+    _, _, st = d2.d2_assign(ctx, db, x, w, prune=p, want_stats=True)
+    assert 0.0 <= est <= 1.0
+    assert abs(est - st["fallbacks"] / N) <= 0.02, (est, st["fallbacks"] / N)
+
+    # near-tie document bags (random unit word vectors: every W^2 close to the
+    # others, bag means near 0 so the mean term separates nothing)
+    K, m, d = 8, 8, 16
+    bags = synth.document_bags(27, 300, V=200, d=d, mk=(5, 20))
+    db = d2.DeviceBags.from_synth(bags)
+    N = bags.N
+    rounds = 3
+    xe, we, le, oe = d2.d2_cluster(ctx, db, K, m, seed=4, rounds=rounds, opts=d2.badmm_opts(iters=20))
+    raw = d2.Pruner(ctx, d, hidden=64, embed=32, seed=26)
+    raw.set_margin(1, 0.0)
+    xr, wr, lr_, orr = d2.d2_cluster(ctx, db, K, m, seed=4, rounds=rounds,
+                                     opts=d2.badmm_opts(iters=20, recalibrate=True), prune=raw)
+    cs = ctx.cluster_stats()
+    assert raw.calibration_fallbacks() >= 0.8 - 1.0 / K
+    assert torch.equal(le, lr_)
+    assert cs["fallbacks"] == N * rounds
+    assert cs["exact_solves"] == N * K * rounds
