@@ -449,7 +449,8 @@ def docs_clustering(d2, ctx, dev, seed, n_docs=None):
                 "exact_pairs_per_s": ns * K / t_ex,
                 "sample_bounded": {"s": t_bd, "full_K_s": t_ex, "exact_solves": stb["exact_solves"],
                                    "labels_equal_full_K": bool(torch.equal(lbd, le))},
-                "plain_assign_s_per_round_est": bags.N * K / (ns * K / t_ex)})
+                # (against the merge-initialised centroids; later rounds' LPs take longer)
+                "full_K_assign_s_initial_centroids_est": bags.N * K / (ns * K / t_ex)})
     return out
 
 
