@@ -7,8 +7,10 @@
 // residual arc's reduced cost non-negative, so each phase is a dense Dijkstra
 // (warp argmin over unvisited nodes, lanes relax one node's arcs in
 // parallel) from all sources with remaining supply to the nearest sink with
-// remaining demand, followed by an augmentation of the largest feasible amount
-// along that path.  Reduced-cost optimality holds throughout, so the final
+// remaining demand (for problems of more than 64 nodes: until 4 such sinks
+// are settled), followed by augmentations of the largest feasible amount
+// along the shortest path to each (after the potential update every such
+// path is tight).  Reduced-cost optimality holds throughout, so the final
 // flow is optimal; unlike a simplex there are no degenerate pivots.  Start:
 // pot_i = 0, pot_j = min_i C_ij and every sink sends what it can to its
 // cheapest source (those arcs have zero reduced cost).  Costs, flows and

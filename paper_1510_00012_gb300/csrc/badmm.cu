@@ -331,7 +331,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep(SweepArg
 
 
 // ---------------------------------------------------------------------------
-// Pipelined variant for m % 4 == 0, m <= 128 (one float4 per lane per row).
+// Pipelined variant for m % 4 == 0 (NV float4s per lane per row: NV = 1 for
+// m <= 128, NV = 2 for m % 8 == 0 up to 256).
 // Each warp runs a PIPE_S-stage ring in shared memory: stage s holds one row
 // group (RPW rows) of the plan buffer, Lambda and C, the rows' weights and,
 // on the first row group of a member, that member's r_k and w slice.  Lanes
@@ -868,8 +869,9 @@ __global__ void __launch_bounds__(XU_THREADS) k_xpartial(const int64_t* members,
 
 
 // Pipelined support partials for m % 4 == 0 and d % 4 == 0: 128 threads own a
-// 32 (i) x 64 (d) output tile, 4 x 4 per thread; rows arrive in tiles of 64
-// through double-buffered cp.async copies of the matching Pi2 and y slices.
+// 32 (i) x 64 (d) output tile, 4 x 4 per thread; rows arrive in tiles of
+// XP_ROWS = 32 through double-buffered cp.async copies of the matching Pi2
+// and y slices.
 #define XP_ROWS 32
 #define XP_PS (32 + 4)
 #define XP_YS (64 + 4)
@@ -930,7 +932,7 @@ __global__ void __launch_bounds__(128) k_xpartial_pipe(const int64_t* members, c
         }
     };
     auto issue = [&](int b) {
-        // Pi2 slices: 64 rows x 8 segments; y slices: 64 rows x 16 segments
+        // Pi2 slices: XP_ROWS rows x 8 segments; y slices: XP_ROWS rows x 16 segments
         for (int e = tid; e < XP_ROWS * 8; e += 128) {
             const int r = e >> 3, sg = e & 7;
             const int64_t g = s_row[b][r];

@@ -9,6 +9,11 @@
 //     C[j, i] = ||xt_i||^2 + ||y_j - mu_c||^2 - 2 <xt_i, y_j - mu_c>.
 // Centring removes the catastrophic cancellation of the plain norm expansion
 // when the data sit far from the origin.
+//
+// d2_cost_rows dispatches: with a BF16 precision flag and d >= 32 the
+// tensor-core build (cost_tc.cu) runs instead, and for bags stored as
+// vocabulary indices the per-(cluster, word) table (cost_vocab.cu) on top
+// of it; otherwise these FP32 kernels.
 #include "d2_internal.cuh"
 
 #define COST_THREADS 256
