@@ -22,9 +22,11 @@
 
 #define AS_DC 8        // support dimensions staged per step of the cost build
 #define AS_INF 3.0e38f
-// deficit sinks collected per shortest-path pass: 4 for problems of more than
-// 64 nodes (half the passes); small problems keep one (measured faster)
-#define AS_KT(TV) ((TV) <= 2 ? 1 : 4)
+// deficit sinks collected per shortest-path pass: one for problems of <= 64
+// nodes (measured faster), else 4, or 8 with >= 64 centroid points
+// (measured on one GPU: 8 is 5-7 % faster than 4 on 64 x 10..60 problems and
+// 5 % slower on 32 x 16..64 ones; 4 halves the passes of one)
+__device__ __forceinline__ int as_kt(int m, int V) { return V <= 64 ? 1 : m >= 64 ? 8 : 4; }
 
 struct AssignArgs {
     const int64_t* offsets;
@@ -201,10 +203,11 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
             dist[t] = (v < m && exc[t] > tol) ? 0.f : AS_INF;
             if (v < V) s.pred[v] = -1;
         }
-        // up to AS_KT deficit sinks per pass (settled in order of distance);
+        // up to kt_max deficit sinks per pass (settled in order of distance);
         // the shortest paths to all of them become tight arcs after the
         // potential update, so flow is pushed along each (primal-dual step)
-        int kt = 0, tg0 = -1, tg1 = -1, tg2 = -1, tg3 = -1;
+        int kt = 0, tgl = -1;  // lane q < kt holds the q-th target
+        const int kt_max = as_kt(m, V);
         for (int it = 0; it < V; ++it) {
             // warp argmin over unsettled nodes: smallest distance, then lowest index
             float bv = AS_INF;
@@ -224,8 +227,8 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
             const float du = __uint_as_float(kmin);
             if ((u & 31) == lane) vis |= 1u << (u >> 5);
             if (u >= m && node_bcast<TV>(exc, u) > tol) {
-                if (kt == 0) tg0 = u; else if (kt == 1) tg1 = u; else if (kt == 2) tg2 = u; else tg3 = u;
-                if (++kt == AS_KT(TV)) break;
+                if (lane == kt) tgl = u;
+                if (++kt == kt_max) break;
             }
             const float pu = node_bcast<TV>(pot, u);
             if (u < m) {
@@ -263,7 +266,7 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
             break;
         }
         // ---- potentials: pot += min(dist, dist of the last target)
-        const int tlast = kt == 1 ? tg0 : kt == 2 ? tg1 : kt == 3 ? tg2 : tg3;
+        const int tlast = __shfl_sync(0xffffffffu, tgl, kt - 1);
         const float dt = node_bcast<TV>(dist, tlast);
 #pragma unroll
         for (int t = 0; t < TV; ++t) pot[t] += ((vis >> t) & 1u) ? fminf(dist[t], dt) : dt;
@@ -272,7 +275,7 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
         // (flows in shared memory); a path whose bottleneck an earlier push
         // used up carries nothing
         for (int q = 0; q < kt; ++q) {
-            const int target = q == 0 ? tg0 : q == 1 ? tg1 : q == 2 ? tg2 : tg3;
+            const int target = __shfl_sync(0xffffffffu, tgl, q);
             float dflow = AS_INF;
             int src_node = target;
             if (lane == 0) {
