@@ -133,6 +133,7 @@ typedef struct {
     int32_t rule;      /* D2_RULE_R1 (default) or D2_RULE_R2                            */
     int32_t flags;     /* D2_FIX_X | D2_FIX_W | D2_VALIDATE | D2_NO_GRAPH | D2_NO_PIPE |
                           D2_ELKAN | D2_AUTOTUNE | D2_SPLIT_STREAMS |
+                          D2_ASSIGN_BOUNDED | D2_PRUNE_RECALIBRATE | D2_COST_ROWS |
                           one of D2_COST_BF16, _BF16X3, _BF16X6                        */
 } d2_badmm_opts;
 
@@ -199,7 +200,9 @@ int d2_check_bags(d2_ctx* ctx, const d2_bags* bags, void* stream);
  *   C_out           : device, n x m; the j-major rows of every listed member
  *                     are written, other rows are left untouched
  *   flags           : 0 (FP32) or D2_COST_BF16 / _BF16X3 / _BF16X6 (tensor
- *                     cores, see those flags)
+ *                     cores, see those flags); with vocabulary bags and a
+ *                     tensor-core precision the rows come from the
+ *                     per-(cluster, word) table unless D2_COST_ROWS is set
  * Requires 1 <= m <= 256.  Arithmetic on coordinates centred at the mean of
  * each cluster's barycenter points; entries are clamped at 0. */
 int d2_cost(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_offsets,
