@@ -10,6 +10,7 @@ matrices and for whole B-ADMM calls; the direct build itself is held to the
 oracle by test_gpu_cost_tc.py, and the B-ADMM vocabulary case there now runs
 through the table.
 """
+import numpy as np
 import pytest
 import torch
 
@@ -90,3 +91,52 @@ def test_badmm_vocab_table_is_bitwise_the_direct_build(d2, ctx, split):
     assert ctx.device_errors() == 0
     for u, v in zip(ra, rb):
         assert torch.equal(u, v)
+
+
+def test_full_size_documents_update(d2, ctx):
+    """The document workload at full size (200,000 bags of 10..60 words from a
+    50,000-word vocabulary, d = 300, K = 64, m = 64, T = 100, tau = 10) in the
+    configuration the benchmark times (split-BF16 tensor-core cost through the
+    vocabulary table).  Clusters 0..3 hold 20 bags each, the other 60 share the
+    rest, all in one call.  Plan marginals on every cluster (Eq. badmmc1: the
+    row sums of each member's Pi2 are w), w in the simplex, and full parity
+    against the FP64 oracle on the four small clusters."""
+    from tests.helpers import cluster_members, oracle_clusters
+    N, K, m = 200_000, 64, 64
+    bags = synth.document_bags(71, N, V=50_000, d=300, mk=(10, 60), device="cuda")
+    lab = torch.empty(N, dtype=torch.int64)
+    small = torch.arange(80) * (N // 80)
+    rest = torch.ones(N, dtype=torch.bool)
+    rest[small] = False
+    lab[small] = torch.arange(80) // 20
+    lab[rest] = 4 + torch.arange(int(rest.sum())) % (K - 4)
+    co, mem = split_clusters(lab, K)
+    x0, w0 = synth.sample_initial_barycenters(72, bags, co.cuda(), mem.cuda(), m)
+    db = d2.DeviceBags.from_synth(bags)
+    x, w = x0.clone().cuda(), w0.clone().cuda()
+    plan = torch.empty(bags.n, m, dtype=torch.float32, device="cuda")
+    obj = torch.empty(K, dtype=torch.float64, device="cuda")
+    d2.badmm_barycenter(ctx, db, co.cuda(), mem.cuda(), x, w, plan, None,
+                        d2.badmm_opts(iters=100, tau=10, cost="bf16x3"), obj)
+    torch.cuda.synchronize()
+    assert ctx.device_errors() == 0
+    owner = torch.repeat_interleave(torch.arange(N, device="cuda"), bags.offsets[1:] - bags.offsets[:-1])
+    rows = torch.zeros(N, m, dtype=torch.float64, device="cuda").index_add_(0, owner, plan.double())
+    assert torch.allclose(rows, w[lab.cuda()].double(), atol=1e-6, rtol=0)
+    assert torch.allclose(w.double().sum(1), torch.ones(K, dtype=torch.float64, device="cuda"), atol=1e-6)
+    assert torch.isfinite(obj).all() and (obj > 0).all()
+    host = bags.to("cpu")
+    jobs = []
+    for c in range(4):
+        _, members = cluster_members(host, co, mem, c)
+        jobs.append((members, x0[c].double().cpu().numpy(), w0[c].double().cpu().numpy(), 100, 10))
+    refs = oracle_clusters(jobs)
+    gw, gobj, gx, gplan = w.cpu(), obj.cpu(), x.cpu(), plan
+    for c, ref in enumerate(refs):
+        ids, _ = cluster_members(host, co, mem, c)
+        assert float(np.abs(gw[c].double().numpy() - ref["w"]).max()) <= 1e-5
+        assert abs(float(gobj[c]) - ref["obj"]) <= 1e-4 * abs(ref["obj"])
+        assert float(np.abs(gx[c].double().numpy() - ref["x"]).max()) <= 2e-4 * (1 + float(np.abs(ref["x"]).max()))
+        for t, k in enumerate(ids):
+            a, b = int(host.offsets[k]), int(host.offsets[k + 1])
+            assert float(np.abs(gplan[a:b].double().cpu().numpy().T - ref["P2"][t]).max()) <= 1e-5
