@@ -219,3 +219,51 @@ def test_calibration_fallback_estimate_and_round_bypass(d2, ctx):
     assert torch.equal(le, lr_)
     assert cs["fallbacks"] == N * rounds
     assert cs["exact_solves"] == N * K * rounds
+
+
+def test_full_size_learned_pruning(d2, ctx):
+    """The learned-pruning workload at full size: K = 256 centroids (m = 32,
+    d = 32) from one B-ADMM update on 256 Gaussian classes, N = 500,000 bags of
+    16..64 points; the MLP (128 hidden, 64-wide embedding) trained on 100k
+    exact W^2 pairs (half the 8 nearest centroids by mean distance, half
+    random); r = 8.  On 20,000 bags the pruned assignment agrees with the
+    exact full-K one (misassignment <= 0.1 %) with far fewer exact solves; all
+    500,000 bags are then assigned through the pruner."""
+    K, m, d, r = 256, 32, 32, 8
+    bags = synth.gaussian_class_bags(5, 500_000, d, K, mk=(16, 64), mu_sigma=2.0, alpha=1.0, device="cuda")
+    db = d2.DeviceBags(bags.offsets, bags.wt, bags.d, supp=bags.supp)
+    lab = bags.labels
+    order = torch.sort(lab, stable=True).indices
+    co = torch.zeros(K + 1, dtype=torch.int64, device="cuda")
+    co[1:] = torch.cumsum(torch.bincount(lab, minlength=K), 0)
+    x, w = synth.sample_initial_barycenters(6, bags, co, order, m)
+    d2.badmm_barycenter(ctx, db, co, order.contiguous(), x, w, None, None, d2.badmm_opts(iters=100, tau=10))
+    g = torch.Generator(device="cuda").manual_seed(7)
+    npairs, half = 100_000, 50_000
+    tb = torch.randint(0, bags.N, (npairs,), generator=g, device="cuda")
+    owner = torch.repeat_interleave(torch.arange(bags.N, device="cuda"), bags.offsets[1:] - bags.offsets[:-1])
+    mu_b = torch.zeros(bags.N, d, device="cuda").index_add_(0, owner, bags.supp * bags.wt[:, None])
+    mu_c = (w[:, :, None] * x).sum(1)
+    near = torch.cdist(mu_b[tb[:half]], mu_c).topk(8, largest=False).indices
+    pick = torch.randint(0, 8, (half,), generator=g, device="cuda")
+    pc = torch.empty(npairs, dtype=torch.int32, device="cuda")
+    pc[:half] = near.gather(1, pick[:, None]).squeeze(1).to(torch.int32)
+    pc[half:] = torch.randint(0, K, (npairs - half,), generator=g, device="cuda", dtype=torch.int32)
+    tg = d2.d2_w2_pairs(ctx, db, x, w, tb.contiguous(), pc.contiguous())
+    pr = d2.Pruner(ctx, d, hidden=128, embed=64, seed=8)
+    pr.train(db, x, w, tb.contiguous(), pc.contiguous(), tg, steps=1500, batch=1024, lr=1e-3, seed=9)
+    pr.set_margin(r, pr.margin()[1])
+    ev = 20_000
+    sub = synth.subset_bags(bags, torch.arange(ev, device="cuda"))
+    dsub = d2.DeviceBags(sub.offsets, sub.wt, sub.d, supp=sub.supp)
+    le, de = d2.d2_assign(ctx, dsub, x, w)
+    lp, dp, st = d2.d2_assign(ctx, dsub, x, w, prune=pr, want_stats=True)
+    assert ctx.device_errors() == 0
+    mis = float((lp != le).float().mean())
+    print("full-size pruning: misassignment %.2e, exact solves %d of %d, fall-backs %d"
+          % (mis, st["exact_solves"], ev * K, st["fallbacks"]))
+    assert mis <= 1e-3
+    assert st["exact_solves"] <= ev * K // 10
+    la, da, sa = d2.d2_assign(ctx, db, x, w, prune=pr, want_stats=True)
+    assert torch.equal(la[:ev], lp)
+    assert sa["exact_solves"] <= bags.N * K // 10
