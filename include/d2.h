@@ -43,7 +43,8 @@ extern "C" {
 #define D2_ECUDA    (-3)  /* a CUDA runtime call or kernel launch failed       */
 #define D2_ETIMEOUT (-4)  /* a bounded device-side wait expired                */
 #define D2_ENOTSUP  (-5)  /* valid request outside what this build implements  */
-#define D2_ENOCONV  (-6)  /* exact OT hit its pivot limit on some pair          */
+#define D2_ENOCONV  (-6)  /* an exact W^2 solve reached its phase cap: that
+                             pair's value (and the label it decides) is wrong */
 #define D2_ESCRATCH (-7)  /* problem larger than d2_assign_noalloc's fixed scratch */
 
 /* ---- options flags ---------------------------------------------------- */
@@ -178,10 +179,20 @@ int64_t d2_launch_count(const d2_ctx* ctx);
 /* Sticky device-side error bits raised by this context's kernels since the
  * last call (synchronous; the bits are cleared).  Kernels never trap: a
  * bounded wait on the device that expires (about 2 s; the tensor-core cost
- * build waits on its MMAs) sets bit 0x40 and the kernel returns early.
- * Returns D2_ETIMEOUT when that bit was set, else D2_OK; *bits (host,
+ * build waits on its MMAs) sets bit 0x40 and the kernel returns early; an
+ * exact W^2 solve (d2_assign, d2_assign_bounded, d2_w2_pairs, d2_cluster,
+ * d2_prune_calibrate) that reaches its phase cap sets bit 0x10 and returns
+ * the cost of its unfinished flow.  Returns D2_ETIMEOUT when bit 0x40 was
+ * set, else D2_ENOCONV when bit 0x10 was set, else D2_OK; *bits (host,
  * optional) receives the raw bits. */
 int d2_device_errors(d2_ctx* ctx, int32_t* bits);
+
+/* Cap on the shortest-path phases of one exact W^2 solve on this context
+ * (0 restores the default 8 (m + max_mk) + 64; every phase routes flow to at
+ * least one deficit sink, so a solve needs far fewer).  For testing the
+ * reporting path: a low cap makes solves stop early, without any fault, and
+ * report D2_ENOCONV.  Returns D2_EINVAL for a negative cap. */
+int d2_set_phase_limit(d2_ctx* ctx, int32_t max_phases);
 
 /* Validate a bag set on the device (synchronous): offsets non-decreasing with
  * offsets[N] == n and every m_k in [1, max_mk]; weights finite, >= 0 and each
@@ -330,10 +341,16 @@ int d2_prune_train(d2_ctx* ctx, d2_prune* p, const d2_bags* bags,
  *            among them when every other centroid has
  *            max(||mu_P - mu_Qi||^2, What^2_i - delta) > b; else solve all K.
  *   labels : device, N int32;  dist : device, N floats
- *   stats  : optional host int64[3]: exact solves, fall-backs, pairs that hit
- *            the pivot limit (synchronises when given)
- * The exact solver is a transportation simplex per pair in FP32 with the
- * final cost summed in FP64.  Requires m + max_mk <= 256 and m*max_mk <= 8192. */
+ *   stats  : optional host int64[3]: exact solves, fall-backs, solves that
+ *            reached the phase cap (synchronises when given)
+ * The exact solver is successive shortest paths with node potentials, one
+ * warp per (bag, centroid) pair, flows and costs in FP32, the final cost
+ * summed in FP64.  Requires m + max_mk <= 256 and the two m x max_mk FP32
+ * tableaus of a pair within 200 KiB (D2_ENOTSUP otherwise).  A solve that
+ * reaches its phase cap (see d2_set_phase_limit) gives a wrong value: with
+ * stats the call then returns D2_ENOCONV; without stats (asynchronous) it
+ * sets the context's sticky bit 0x10, which d2_device_errors reports as
+ * D2_ENOCONV. */
 int d2_assign(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,
               const float* x, const float* w, const d2_prune* prune,
               int32_t* labels, float* dist, int64_t* stats, void* stream);
@@ -347,15 +364,17 @@ int d2_assign(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,
  * smallest-bound centroids exactly (r = 2, or the pruner's r candidates when
  * `prune` is given), then every other centroid whose bound does not exceed
  * the best value found times (1 + 1e-4) (covering FP32 rounding).  Requires
- * max_mk <= 128 and the conditions of d2_assign.  stats: as for d2_assign
- * (fall-backs stay 0). */
+ * max_mk <= 128 and the conditions of d2_assign.  stats and D2_ENOCONV: as
+ * for d2_assign (fall-backs stay 0). */
 int d2_assign_bounded(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,
                       const float* x, const float* w, const d2_prune* prune,
                       int32_t* labels, float* dist, int64_t* stats, void* stream);
 
 /* Exact W^2 (Eq. primal, the same solver as d2_assign) for an explicit list
  * of npairs (bag pair_bag[p], centroid pair_cent[p]) -> out[p] (device
- * floats).  Used to produce training targets for the pruner. */
+ * floats).  Used to produce training targets for the pruner.  Asynchronous: a
+ * solve that reaches its phase cap sets the sticky bit that d2_device_errors
+ * reports as D2_ENOCONV. */
 int d2_w2_pairs(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,
                 const float* x, const float* w, const int64_t* pair_bag,
                 const int32_t* pair_cent, int64_t npairs, float* out, void* stream);
@@ -371,11 +390,17 @@ int d2_w2_pairs(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,
  * the array (about 4 MiB) until the process exits.  The first call on a
  * device resolves the array's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture.
+ * The cached address is not refreshed after cudaDeviceReset: do not call
+ * this entry point again in a process that has reset the device.
  * All calls share the array and it keeps the last call's contents (the
  * counters are cleared by each call): calls that overlap on the GPU, on any
- * streams, race.  Other arguments and results as for d2_assign.  Returns
- * D2_OK, D2_EINVAL, D2_ESCRATCH, D2_ENOTSUP (m * max_mk too large) or
- * D2_ECUDA. */
+ * streams, race.  Other arguments and results as for d2_assign.  The call is
+ * synchronous: it reads back how many solves reached the phase cap.
+ * Returns D2_OK, D2_EINVAL (bad pointers or sizes; supp and vocab both given
+ * or both missing), D2_ESCRATCH (N * K > D2_NOALLOC_MAX_PAIRS), D2_ENOTSUP
+ * (m + max_mk > 256, or the per-pair tableaus of d2_assign exceed 200 KiB),
+ * D2_ENOCONV (some solve reached the phase cap: its value and label are
+ * wrong) or D2_ECUDA. */
 #define D2_NOALLOC_MAX_PAIRS (1 << 20)
 int d2_assign_noalloc(const d2_bags* bags, int32_t K, int32_t m, const float* x, const float* w,
                       int32_t* labels, float* dist, void* stream);
@@ -403,7 +428,9 @@ int d2_merge_init(d2_ctx* ctx, const d2_bags* bags, const int64_t* ids, int64_t 
  *   x_out, w_out, labels_out : device, K x m x d, K x m, N
  *   obj_per_round : host, rounds doubles: (1/N) sum_k W^2(Q_{l_k}, P^(k)) at
  *                   each round's assignment
- * Synchronous.  Empty clusters keep their previous centroid. */
+ * Synchronous.  Empty clusters keep their previous centroid.  Returns
+ * D2_ENOCONV (after writing every output) when some exact W^2 solve of the
+ * assignment steps reached its phase cap. */
 int d2_cluster(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, uint64_t seed,
                int32_t rounds, const d2_badmm_opts* opts, const d2_prune* prune,
                float* x_out, float* w_out, int32_t* labels_out, double* obj_per_round,

@@ -63,6 +63,7 @@ _SIGS = {
     "d2_timing_read": (c_int, [c_void_p, c_void_p, c_void_p]),
     "d2_launch_count": (c_int64, [c_void_p]),
     "d2_device_errors": (c_int, [c_void_p, c_void_p]),
+    "d2_set_phase_limit": (c_int, [c_void_p, c_int32]),
     "d2_sweep_tuning": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "d2_cluster_stats": (c_int, [c_void_p, c_void_p]),
     "d2_cost": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32,
@@ -189,6 +190,11 @@ class Context:
         bits = c_int32(0)
         self.check(lib().d2_device_errors(self.h, ctypes.byref(bits)))
         return int(bits.value)
+
+    def set_phase_limit(self, max_phases):
+        """Cap the exact solver's shortest-path phases per pair (0 = default);
+        a low cap makes solves stop early and report D2_ENOCONV."""
+        self.check(lib().d2_set_phase_limit(self.h, int(max_phases)))
 
     def sweep_tuning(self, m):
         """The plan-sweep autotuner's record for plan width m: None when untuned,
@@ -479,5 +485,7 @@ def d2_assign_noalloc(bags, x, w):
     rc = lib().d2_assign_noalloc(bags.ref(), x.shape[0], x.shape[1], _ptr(x), _ptr(w), _ptr(labels), _ptr(dist),
                                  _stream())
     if rc != D2_OK:
-        raise D2Error(rc, "d2_assign_noalloc failed" + (": N * K exceeds the fixed scratch" if rc == D2_ESCRATCH else ""))
+        why = {D2_ESCRATCH: ": N * K exceeds the fixed scratch", D2_ENOTSUP: ": m + max_mk or the tableaus too large",
+               D2_EINVAL: ": invalid arguments", D2_ENOCONV: ": a solve reached the phase cap"}.get(rc, "")
+        raise D2Error(rc, "d2_assign_noalloc failed" + why)
     return labels, dist

@@ -171,6 +171,14 @@ extern "C" int d2_device_errors(d2_ctx* ctx, int32_t* bits) {
     D2_CK(ctx, cudaMemset(word, 0, sizeof(int)));
     if (bits) *bits = v;
     if (v & D2F_DEV_TIMEOUT) return d2_fail(ctx, D2_ETIMEOUT, "a bounded device-side wait expired");
+    if (v & D2F_PIVOT_LIMIT)
+        return d2_fail(ctx, D2_ENOCONV, "an exact W^2 solve reached its phase cap (its value and label are wrong)");
+    return D2_OK;
+}
+
+extern "C" int d2_set_phase_limit(d2_ctx* ctx, int32_t max_phases) {
+    if (!ctx || max_phases < 0) return D2_EINVAL;
+    ctx->phase_limit = max_phases;
     return D2_OK;
 }
 

@@ -437,28 +437,61 @@ static W2Fn w2_kernel_for(int V) {
     return nullptr;
 }
 
+// Launch shape of the pair solver for a.m + a.nmax nodes on `device`:
+// kernel, warps per block, dynamic shared memory and a grid bound (the
+// kernel is a persistent stride loop).  Returns D2_OK, or D2_ENOTSUP when the
+// per-warp tableaus exceed 200 KiB or m + max_mk exceeds 256 (then *why says
+// which), or D2_ECUDA when a runtime call fails.
+struct PairLaunch {
+    W2Fn fn;
+    int wpb;
+    size_t smem;
+    unsigned grid;
+};
+static int pair_launch_config(AssignArgs& a, int64_t max_units, int device, PairLaunch* L, const char** why,
+                              cudaError_t* cerr) {
+    a.warp_bytes = d2_assign_warp_bytes(a.m, a.nmax);
+    if (a.warp_bytes > 200 * 1024) {
+        *why = "m * max_mk too large for the per-warp tableau";
+        return D2_ENOTSUP;
+    }
+    L->fn = w2_kernel_for(a.m + a.nmax);
+    if (!L->fn) {
+        *why = "m + max_mk exceeds 256";
+        return D2_ENOTSUP;
+    }
+    L->wpb = pick_wpb(a.warp_bytes);
+    L->smem = a.warp_bytes * L->wpb;
+    cudaError_t e = cudaFuncSetAttribute(L->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
+    if (e != cudaSuccess) {
+        *why = "k_w2_pairs shared-memory attribute";
+        *cerr = e;
+        return D2_ECUDA;
+    }
+    int sms = 152, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L->fn, L->wpb * 32, L->smem);
+    per_sm = std::max(per_sm, 1);
+    const int64_t want = d2_ceil_div(std::max<int64_t>(max_units, 1), L->wpb);
+    L->grid = (unsigned)std::max<int64_t>(1, std::min(want, (int64_t)sms * per_sm * 8));
+    return D2_OK;
+}
+
+// default cap on the shortest-path phases of one pair (each phase routes
+// flow to at least one deficit sink, so a pair needs far fewer)
+static inline int default_max_phase(int m, int nmax) { return 8 * (m + nmax) + 64; }
+
 // Launch the pair solver; grid is a bound (persistent stride loop).
 int d2_launch_pairs(d2_ctx* ctx, AssignArgs a, int64_t max_units, cudaStream_t st) {
-    a.warp_bytes = d2_assign_warp_bytes(a.m, a.nmax);
-    if (a.warp_bytes > 200 * 1024)
-        return d2_fail(ctx, D2_ENOTSUP, "d2_assign: m * max_mk too large for the per-warp tableau");
-    const W2Fn fn = w2_kernel_for(a.m + a.nmax);
-    if (!fn) return d2_fail(ctx, D2_ENOTSUP, "d2_assign: m + max_mk = %d exceeds 256", a.m + a.nmax);
-    const int wpb = pick_wpb(a.warp_bytes);
-    size_t smem = a.warp_bytes * wpb;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return d2_cuda_fail(ctx, e, "k_w2_pairs smem attribute");
-    int dev_sms = 152;
-    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, smem);
-    if (per_sm < 1) per_sm = 1;
-    int64_t want = d2_ceil_div(std::max<int64_t>(max_units, 1), wpb);
-    int64_t cap = (int64_t)dev_sms * per_sm * 8;
-    unsigned grid = (unsigned)std::max<int64_t>(1, std::min(want, cap));
-    a.max_phase = 8 * (a.m + a.nmax) + 64;
+    PairLaunch L;
+    const char* why = "";
+    cudaError_t ce = cudaSuccess;
+    const int rc = pair_launch_config(a, max_units, ctx->device, &L, &why, &ce);
+    if (rc == D2_ENOTSUP) return d2_fail(ctx, D2_ENOTSUP, "d2_assign: %s (m = %d, max_mk = %d)", why, a.m, a.nmax);
+    if (rc) return d2_cuda_fail(ctx, ce, why);
+    a.max_phase = ctx->phase_limit > 0 ? ctx->phase_limit : default_max_phase(a.m, a.nmax);
     d2_time_begin(ctx, D2_KT_ASSIGN, st);
-    fn<<<grid, wpb * 32, smem, st>>>(a);
+    L.fn<<<L.grid, L.wpb * 32, L.smem, st>>>(a);
     d2_time_end(ctx, st);
     D2_LAUNCH_CK(ctx, "k_w2_pairs");
     return D2_OK;
@@ -501,7 +534,7 @@ int d2_assign_exact(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x,
     int rc = d2_ws(ctx, WS_ASSIGN, (size_t)N * K * 4, &pD);
     if (rc) return rc;
     float* D = static_cast<float*>(pD);
-    AssignArgs a = d2_assign_args(b, K, m, x, w, ctx->dev_flags, counters + 2);
+    AssignArgs a = d2_assign_args(b, K, m, x, w, ctx->dev_flags + D2_DEV_ERR_WORD, counters + 2);
     a.mode = 0;
     a.npairs = N * K;
     a.out = D;
@@ -516,7 +549,7 @@ int d2_assign_exact(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x,
 int d2_prune_solve_pairs(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w, int mode,
                          int64_t npairs, const int64_t* npairs_dev, const int32_t* cand, int r,
                          const int64_t* bag_list, float* out, int64_t* fail_count, cudaStream_t st) {
-    AssignArgs a = d2_assign_args(b, K, m, x, w, ctx->dev_flags, fail_count);
+    AssignArgs a = d2_assign_args(b, K, m, x, w, ctx->dev_flags + D2_DEV_ERR_WORD, fail_count);
     a.mode = mode;
     a.npairs = npairs;
     a.npairs_dev = npairs_dev;
@@ -541,7 +574,7 @@ extern "C" int d2_w2_pairs(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t 
     if ((rc = d2_ws(ctx, WS_SCAN, 64, &sc))) return rc;
     int64_t* counters = static_cast<int64_t*>(sc);
     D2_CK(ctx, cudaMemsetAsync(counters, 0, 3 * sizeof(int64_t), st));
-    AssignArgs a = d2_assign_args(bags, K, m, x, w, ctx->dev_flags, counters + 2);
+    AssignArgs a = d2_assign_args(bags, K, m, x, w, ctx->dev_flags + D2_DEV_ERR_WORD, counters + 2);
     a.mode = 1;
     a.npairs = npairs;
     a.pair_bag = pair_bag;
@@ -552,40 +585,33 @@ extern "C" int d2_w2_pairs(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t 
 
 // All N x K pairs into D, then argmin per bag, with caller-provided scratch
 // (D: N*K floats, flags: 1 int, fail_count: 1 int64, both already zeroed).
-// No context, no allocation.
-cudaError_t d2_assign_exact_into(const d2_bags* b, int K, int m, const float* x, const float* w, int32_t* labels,
-                                 float* dist, float* D, int* flags, int64_t* fail_count, int device,
-                                 cudaStream_t st) {
+// No context, no allocation.  Returns D2_OK, D2_ENOTSUP (the shape limits of
+// pair_launch_config) or D2_ECUDA (*cerr holds the runtime's error).
+int d2_assign_exact_into(const d2_bags* b, int K, int m, const float* x, const float* w, int32_t* labels,
+                         float* dist, float* D, int* flags, int64_t* fail_count, int device, cudaStream_t st,
+                         cudaError_t* cerr) {
     AssignArgs a = d2_assign_args(b, K, m, x, w, flags, fail_count);
     a.mode = 0;
     a.npairs = b->N * (int64_t)K;
     a.out = D;
-    a.warp_bytes = d2_assign_warp_bytes(m, b->max_mk);
-    if (a.warp_bytes > 200 * 1024) return cudaErrorInvalidValue;
-    const W2Fn fn = w2_kernel_for(m + b->max_mk);
-    if (!fn) return cudaErrorInvalidValue;
-    const int wpb = pick_wpb(a.warp_bytes);
-    const size_t smem = a.warp_bytes * wpb;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int sms = 152, per_sm = 1;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, smem);
-    per_sm = std::max(per_sm, 1);
-    const int64_t want = d2_ceil_div(std::max<int64_t>(a.npairs, 1), wpb);
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min(want, (int64_t)sms * per_sm * 8));
-    a.max_phase = 8 * (a.m + a.nmax) + 64;
-    fn<<<grid, wpb * 32, smem, st>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    PairLaunch L;
+    const char* why = "";
+    *cerr = cudaSuccess;
+    const int rc = pair_launch_config(a, a.npairs, device, &L, &why, cerr);
+    if (rc) return rc;
+    a.max_phase = default_max_phase(a.m, a.nmax);
+    L.fn<<<L.grid, L.wpb * 32, L.smem, st>>>(a);
+    if ((*cerr = cudaGetLastError()) != cudaSuccess) return D2_ECUDA;
     k_argmin_rows<<<(unsigned)d2_ceil_div(b->N, 256), 256, 0, st>>>(D, b->N, K, labels, dist);
-    return cudaGetLastError();
+    if ((*cerr = cudaGetLastError()) != cudaSuccess) return D2_ECUDA;
+    return D2_OK;
 }
 
 // explicit pair list whose length is read on the device (<= max_pairs)
 int d2_solve_pair_list(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w,
                        const int64_t* pair_bag, const int32_t* pair_cent, int64_t max_pairs,
                        const int64_t* npairs_dev, float* out, int64_t* fail_count, cudaStream_t st) {
-    AssignArgs a = d2_assign_args(b, K, m, x, w, ctx->dev_flags, fail_count);
+    AssignArgs a = d2_assign_args(b, K, m, x, w, ctx->dev_flags + D2_DEV_ERR_WORD, fail_count);
     a.mode = 1;
     a.npairs = max_pairs;
     a.npairs_dev = npairs_dev;
@@ -598,7 +624,7 @@ int d2_solve_pair_list(d2_ctx* ctx, const d2_bags* b, int K, int m, const float*
 // all N x K pairs into out (N x K), no argmin
 int d2_launch_pairs_all(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w, float* out,
                         int64_t* fail_count, cudaStream_t st) {
-    AssignArgs a = d2_assign_args(b, K, m, x, w, ctx->dev_flags, fail_count);
+    AssignArgs a = d2_assign_args(b, K, m, x, w, ctx->dev_flags + D2_DEV_ERR_WORD, fail_count);
     a.mode = 0;
     a.npairs = b->N * (int64_t)K;
     a.out = out;

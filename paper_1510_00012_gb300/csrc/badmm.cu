@@ -108,7 +108,8 @@ __device__ __forceinline__ float fast_exp2(float x) {
 
 // Weight consensus (Eq. badmmw / badmmw2) of one cluster per CTA, in FP64 and
 // a fixed order: thread (g, i) sums the members p0 + g, p0 + g + G, ... of
-// column i, the G groups are then added in order, then the m columns.
+// column i (every term converted to FP64 and added in FP64), the G groups are
+// then added in order, then the m columns.
 __global__ void __launch_bounds__(256) k_consensus(const int64_t* cofs, const float* pos_part, int m, bool r2,
                                                    float* w_next, double* w_next64) {
     __shared__ double s_acc[256 + 257];
@@ -119,19 +120,18 @@ __global__ void __launch_bounds__(256) k_consensus(const int64_t* cofs, const fl
     const int t = threadIdx.x;
     const int i = t % m, g = t / m;
     if (g < G) {
-        // blocks of 8 members are summed in FP32, the blocks in FP64 (FP64
-        // throughput is scarce on this part); eight loads are in flight
+        // eight loads in flight, added in member order
         double acc = 0.0;
         int64_t p = p0 + g;
         for (; p + 7 * G < p1; p += 8 * G) {
             float v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) v[u] = __ldcg(pos_part + (p + u * G) * m + i);
-            acc += (double)(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc += (double)v[u];
         }
-        float tail = 0.f;
-        for (; p < p1; p += G) tail += pos_part[p * m + i];
-        s_acc[g * m + i] = acc + (double)tail;
+        for (; p < p1; p += G) acc += (double)pos_part[p * m + i];
+        s_acc[g * m + i] = acc;
     }
     __syncthreads();
     if (t < m) {
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep(SweepArg
         float racc[NE];
 #pragma unroll
         for (int x = 0; x < NE; ++x) racc[x] = 0.f;
-        float objacc = 0.f;
+        double objacc = 0.0;  // <C_k, Pi^(k,1)> of this lane's entries, FP64 (objective pass only)
 
         // one row group (RPW rows) per step; the next group's loads are issued
         // before the current group is computed
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep(SweepArg
                     p1n[x] = t1[x] * scale;
                     if (rv && ok[x]) {
                         racc[x] += fmaf(p1n[x], fast_exp2(l2[x] * beta), eps);
-                        objacc = fmaf(cin[x], p1n[x], objacc);
+                        if (fl & SW_OBJ) objacc = fma((double)cin[x], (double)p1n[x], objacc);
                     }
                 }
                 if (rv) {
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep(SweepArg
                     }
             }
             if (fl & SW_OBJ) {
-                double ov = group_sum_d<32>((double)objacc);
+                double ov = group_sum_d<32>(objacc);
                 if (lane == 0) a.pos_obj[p] = ov;
             }
         }
@@ -467,7 +467,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_PIPE_MINB) k_sweep_pipe(Swee
 
     // ---- compute cursor state (per member)
     float coef[NE], wcol[NE], racc[NE];
-    float beta = 0.f, rho = 0.f, objacc = 0.f;
+    float beta = 0.f, rho = 0.f;
+    double objacc = 0.0;  // <C_k, Pi^(k,1)> of this lane's entries, FP64 (objective pass only)
     bool ldP = false;
     const float eps = a.eps;
     int slot = 0;
@@ -496,7 +497,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_PIPE_MINB) k_sweep_pipe(Swee
             }
 #pragma unroll
             for (int x = 0; x < NE; ++x) racc[x] = 0.f;
-            objacc = 0.f;
+            objacc = 0.0;
         }
         const int j = mt.base + sub;
         const bool rv = j < mt.mk;
@@ -553,7 +554,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_PIPE_MINB) k_sweep_pipe(Swee
                 p1n[x] = t1[x] * scale;
                 if (rv && okv[x / 4]) {
                     racc[x] += fmaf(p1n[x], fast_exp2(l2[x] * beta), eps);
-                    objacc = fmaf(cin[x], p1n[x], objacc);
+                    if (fl & SW_OBJ) objacc = fma((double)cin[x], (double)p1n[x], objacc);
                 }
             }
             if (rv) {
@@ -606,7 +607,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_PIPE_MINB) k_sweep_pipe(Swee
                 }
             }
             if (fl & SW_OBJ) {
-                double ov = group_sum_d<32>((double)objacc);
+                double ov = group_sum_d<32>(objacc);
                 if (lane == 0) a.pos_obj[p] = ov;
             }
         }

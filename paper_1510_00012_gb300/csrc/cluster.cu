@@ -198,6 +198,7 @@ __global__ void k_stable_scatter(const int32_t* labels, int64_t N, int K, const 
 __global__ void k_acc_counts(int64_t* total, const int64_t* call) {
     total[0] += call[0];
     total[1] += call[1];
+    total[2] += call[2];
 }
 
 __global__ void k_warm_mask(const int32_t* labels, const int32_t* prev, int64_t N, uint8_t* mask) {
@@ -269,6 +270,9 @@ static int assign_any(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, co
     if (stats) {
         D2_CK(ctx, cudaMemcpyAsync(stats, counters, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         D2_CK(ctx, cudaStreamSynchronize(st));
+        if (stats[2] > 0)
+            return d2_fail(ctx, D2_ENOCONV, "d2_assign: %lld exact W^2 solves reached the phase cap",
+                           (long long)stats[2]);
     }
     return D2_OK;
 }
@@ -427,6 +431,9 @@ extern "C" int d2_cluster(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m
     D2_CK(ctx, cudaStreamSynchronize(st));
     ctx->cluster_solves = hs[0];
     ctx->cluster_fallbacks = hs[1] + bypass_fallbacks;
+    if (hs[2] > 0)
+        return d2_fail(ctx, D2_ENOCONV, "d2_cluster: %lld exact W^2 solves reached the phase cap",
+                       (long long)hs[2]);
     return D2_OK;
 }
 

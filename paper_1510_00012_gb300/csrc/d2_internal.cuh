@@ -76,6 +76,8 @@ struct d2_ctx {
     std::vector<SweepTune> tuned;
     // testing: the next tensor-core cost build lets its first wait expire
     int expire_test = 0;
+    // cap on the exact solver's shortest-path phases per pair (0: default)
+    int phase_limit = 0;
     // split calls (D2_SPLIT_STREAMS): two child contexts, each on its own
     // stream, with the per-entry workspaces lent by this context
     d2_ctx* child[2] = {nullptr, nullptr};
@@ -93,7 +95,7 @@ void d2_time_end(d2_ctx* ctx, cudaStream_t st);
 #define D2F_BAD_WEIGHTS   0x02
 #define D2F_BAD_VOCAB     0x04
 #define D2F_BAD_MEMBER    0x08
-#define D2F_PIVOT_LIMIT   0x10
+#define D2F_PIVOT_LIMIT   0x10   // an exact W^2 solve reached its phase cap (sticky word)
 #define D2F_BAD_SIZE      0x20
 #define D2F_DEV_TIMEOUT   0x40   // a bounded device-side wait expired
 // Word of dev_flags that accumulates sticky device errors (read and cleared

@@ -16,9 +16,9 @@
 #define D2_NOALLOC_HEAD 64
 static __device__ __align__(256) float g_noalloc_scratch[D2_NOALLOC_HEAD + D2_NOALLOC_MAX_PAIRS];
 
-cudaError_t d2_assign_exact_into(const d2_bags* b, int K, int m, const float* x, const float* w, int32_t* labels,
-                                 float* dist, float* D, int* flags, int64_t* fail_count, int device,
-                                 cudaStream_t st);
+int d2_assign_exact_into(const d2_bags* b, int K, int m, const float* x, const float* w, int32_t* labels,
+                         float* dist, float* D, int* flags, int64_t* fail_count, int device, cudaStream_t st,
+                         cudaError_t* cerr);
 
 #define D2_NOALLOC_MAX_DEVICES 64
 static float* g_scratch_addr[D2_NOALLOC_MAX_DEVICES];
@@ -26,6 +26,8 @@ static std::mutex g_scratch_mu;
 
 // Device address of the scratch array on the current device, resolved once
 // per device (the symbol's name in host code is only a host-side handle).
+// The cached address is not refreshed after cudaDeviceReset (the header says
+// so: the entry point must not be used after a reset).
 static cudaError_t scratch_on(int device, float** out) {
     if (device < 0 || device >= D2_NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
@@ -56,7 +58,13 @@ extern "C" int d2_assign_noalloc(const d2_bags* bags, int32_t K, int32_t m, cons
     int* flags = reinterpret_cast<int*>(scratch);
     int64_t* fails = reinterpret_cast<int64_t*>(scratch + 2);
     float* D = scratch + D2_NOALLOC_HEAD;
-    cudaError_t e = d2_assign_exact_into(bags, K, m, x, w, labels, dist, D, flags, fails, device, st);
-    if (e == cudaErrorInvalidValue) return D2_ENOTSUP;
-    return e == cudaSuccess ? D2_OK : D2_ECUDA;
+    cudaError_t ce = cudaSuccess;
+    const int rc = d2_assign_exact_into(bags, K, m, x, w, labels, dist, D, flags, fails, device, st, &ce);
+    if (rc) return rc;
+    // a pair that reached the solver's phase cap leaves a wrong W^2 and label:
+    // read the count back (this makes the call synchronous)
+    int64_t nfail = 0;
+    if (cudaMemcpyAsync(&nfail, fails, sizeof(nfail), cudaMemcpyDeviceToHost, st) != cudaSuccess) return D2_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return D2_ECUDA;
+    return nfail > 0 ? D2_ENOCONV : D2_OK;
 }

@@ -68,4 +68,4 @@ def oracle_clusters(jobs, procs=8):
     (spawn: the parent has already initialised CUDA)."""
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(min(procs, max(1, len(jobs)))) as pool:
-        return pool.map(oracle_cluster_job, jobs)
+        return pool.map(oracle_cluster_job, jobs, chunksize=1)

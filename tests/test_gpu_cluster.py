@@ -224,3 +224,121 @@ def test_d2_cluster_with_split_streams_and_tensor_core_cost(d2, ctx):
     assert torch.equal(a[2], b[2])
     assert a[3] == b[3]
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+@pytest.fixture(scope="module")
+def doc_shape_case():
+    """Bags of the document workload's shape (d = 300 unit word vectors from a
+    50,000-word vocabulary, m_k ~ U{10..60} distinct Zipf words) against
+    m = 64 centroids: the solver then collects 8 deficit sinks per
+    shortest-path pass (m >= 64 and m + m_k > 64).  Two centroid sets, both
+    computed by the oracle: padded seeds (Eq. merge; m_k < 64, so zero-weight
+    copies) and the barycenters after one B-ADMM update of 12-bag clusters."""
+    from oracle import badmm_barycenter
+    from oracle.cluster import pad_support
+    bags = synth.document_bags(71, 48, V=50_000, d=300, mk=(10, 60))
+    K, m = 4, 64
+    seeds = [pad_support(*merge_reduce(*bags.bag(k), m), m) for k in (3, 17, 29, 41)]
+    upd = []
+    for c in range(K):
+        members = [bags.bag(k) for k in range(c * 12, (c + 1) * 12)]
+        r = badmm_barycenter(members, seeds[c][0], seeds[c][1], T=50, tau=10)
+        upd.append((r["x"], r["w"]))
+    sets = {}
+    for name, cents in (("merge", seeds), ("updated", upd)):
+        x = torch.tensor(np.array([c[0] for c in cents]), dtype=torch.float32)
+        w = torch.tensor(np.array([c[1] for c in cents]), dtype=torch.float32)
+        w = w / w.sum(1, keepdim=True)
+        ref = np.array([[w2_exact(x[c].double().numpy(), w[c].double().numpy(), *bags.bag(k))
+                         for c in range(K)] for k in range(bags.N)])
+        sets[name] = (x, w, ref)
+    return bags, sets
+
+
+@pytest.mark.parametrize("centroids", ["merge", "updated"])
+def test_w2_document_shape_eight_sinks(d2, ctx, doc_shape_case, centroids):
+    bags, sets = doc_shape_case
+    x, w, ref = sets[centroids]
+    db = d2.DeviceBags.from_synth(bags)
+    K = x.shape[0]
+    pb = torch.arange(bags.N, dtype=torch.int64).repeat_interleave(K).cuda()
+    pc = torch.arange(K, dtype=torch.int32).repeat(bags.N).cuda()
+    vals = d2.d2_w2_pairs(ctx, db, x.cuda(), w.cuda(), pb, pc).cpu().double().numpy().reshape(bags.N, K)
+    np.testing.assert_array_less(np.abs(vals - ref), 1e-4 * ref + 1e-6)
+    labels, dist, st = d2.d2_assign(ctx, db, x.cuda(), w.cuda(), want_stats=True)
+    assert st["limit_hits"] == 0
+    labels, dist = labels.cpu().numpy(), dist.cpu().double().numpy()
+    clear = 0
+    for k in range(bags.N):
+        order = np.argsort(ref[k], kind="stable")
+        best = ref[k, order[0]]
+        assert abs(dist[k] - best) <= 1e-4 * best + 1e-6
+        if ref[k, order[1]] - best > 1e-4 * best:
+            assert labels[k] == order[0]
+            clear += 1
+    assert clear >= bags.N // 2
+    print("document shape (%s centroids): max rel W^2 err %.2e, %d of %d labels with a clear margin"
+          % (centroids, float(np.max(np.abs(vals - ref) / ref)), clear, bags.N))
+
+
+def test_elkan_clustering_matches_oracle(d2, ctx):
+    """Triangle-inequality skipping (Section 5) inside the clustering loop:
+    labels and per-round objectives against the FP64 oracle's Algorithm 1 (which
+    solves every pair), and fewer exact solves than the full loop."""
+    bags = synth.gaussian_class_bags(42, 160, 4, 5, mk=(4, 12), mu_sigma=3.0, alpha=1.0)
+    db = d2.DeviceBags.from_synth(bags)
+    K, m, rounds, T = 5, 5, 4, 20
+    x, w, labels, objs = d2.d2_cluster(ctx, db, K, m, seed=21, rounds=rounds,
+                                       opts=d2.badmm_opts(iters=T, tau=10, elkan=True))
+    solves = ctx.cluster_stats()["exact_solves"]
+    members = [bags.bag(k) for k in range(bags.N)]
+    ref = oracle_cluster(members, K, m, seed=21, rounds=rounds, T=T, tau=10)
+    np.testing.assert_array_equal(labels.cpu().numpy(), ref["labels"])
+    for r in range(rounds):
+        assert abs(objs[r] - ref["obj_per_round"][r]) <= 1e-4 * ref["obj_per_round"][r]
+    np.testing.assert_allclose(w.cpu().double().numpy(), ref["w"], atol=1e-5, rtol=0)
+    np.testing.assert_allclose(x.cpu().double().numpy(), ref["x"], atol=2e-4 * (1 + np.abs(ref["x"]).max()))
+    assert solves < bags.N * K * rounds
+    print("Elkan: %d exact solves of %d" % (solves, bags.N * K * rounds))
+
+
+def test_phase_cap_is_reported_as_enoconv(d2):
+    """A solve that reaches its phase cap returns the cost of an unfinished
+    flow; every path that runs the exact solver must say so (D2_ENOCONV)
+    rather than hand back a silently wrong W^2 or label.  The cap is lowered
+    on a context of its own so that solves stop early, without any fault."""
+    bags = synth.gaussian_class_bags(81, 120, 4, 3, mk=(8, 20), mu_sigma=2.0)
+    db = d2.DeviceBags.from_synth(bags)
+    x, w = centroids(82, 3, 8, 4)
+    x, w = x.cuda(), w.cuda()
+    c = d2.Context(0)
+    ref_lab, ref_dist = d2.d2_assign(c, db, x, w)
+    assert c.device_errors() == 0
+    c.set_phase_limit(1)
+    with pytest.raises(d2.D2Error) as e:
+        d2.d2_assign(c, db, x, w, want_stats=True)
+    assert e.value.code == d2.D2_ENOCONV
+    with pytest.raises(d2.D2Error) as e:
+        d2.d2_assign(c, db, x, w, want_stats=True, bounded=True)
+    assert e.value.code == d2.D2_ENOCONV
+    with pytest.raises(d2.D2Error) as e:
+        c.device_errors()
+    assert e.value.code == d2.D2_ENOCONV
+    # asynchronous calls leave the sticky bit for d2_device_errors
+    d2.d2_assign(c, db, x, w)
+    pb = torch.arange(bags.N, dtype=torch.int64, device="cuda")
+    d2.d2_w2_pairs(c, db, x, w, pb, torch.zeros(bags.N, dtype=torch.int32, device="cuda"))
+    with pytest.raises(d2.D2Error) as e:
+        c.device_errors()
+    assert e.value.code == d2.D2_ENOCONV
+    assert c.device_errors() == 0                      # read and cleared
+    with pytest.raises(d2.D2Error) as e:
+        d2.d2_cluster(c, db, 3, 8, seed=1, rounds=2, opts=d2.badmm_opts(iters=5))
+    assert e.value.code == d2.D2_ENOCONV
+    with pytest.raises(d2.D2Error):
+        c.device_errors()
+    # the default cap again: the same context gives the reference result
+    c.set_phase_limit(0)
+    lab, dist, st = d2.d2_assign(c, db, x, w, want_stats=True)
+    assert st["limit_hits"] == 0 and c.device_errors() == 0
+    assert torch.equal(lab, ref_lab) and torch.equal(dist, ref_dist)

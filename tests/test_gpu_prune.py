@@ -267,3 +267,59 @@ def test_full_size_learned_pruning(d2, ctx):
     la, da, sa = d2.d2_assign(ctx, db, x, w, prune=pr, want_stats=True)
     assert torch.equal(la[:ev], lp)
     assert sa["exact_solves"] <= bags.N * K // 10
+
+
+def test_loss_and_gradient_elementwise(d2, ctx):
+    """Element-wise check of the embedding, the loss and every gradient entry.
+    Parameters and support points are made FP16-representable first, so the
+    only differences from the FP64 oracle are the kernels' FP16 roundings of
+    intermediate values (centred points, first hidden layer, pooled vector;
+    each 2^-11 relative) and FP32 accumulation: every entry must lie within
+    3e-3 of its block's largest entry.  The same check must reject an oracle
+    gradient that leaves out one pair's centroid-side contribution."""
+    bags, x, w = small_problem(12, N=48, d=8, K=6, m=5)
+    bags.supp = bags.supp.half().float()
+    x = x.half().float()
+    db = d2.DeviceBags.from_synth(bags)
+    p = d2.Pruner(ctx, bags.d, hidden=32, embed=16, seed=13)
+    p.set_params(p.params().half().float())
+    params = {k: v.double().numpy() for k, v in p.unpack(p.params()).items()}
+    members = [bags.bag(k) for k in range(bags.N)]
+    K = x.shape[0]
+    cents = [(x[q].double().numpy(), w[q].double().numpy()) for q in range(K)]
+    # embeddings
+    ids = torch.arange(bags.N, dtype=torch.int64, device="cuda")
+    emb, _ = p.embed(db, ids)
+    emb = emb.cpu().double().numpy()
+    ref_emb = np.array([mlp.embed(params, *members[k]) for k in range(bags.N)])
+    scale = np.abs(ref_emb).max()
+    emb_err = float(np.abs(emb - ref_emb).max() / scale)
+    assert emb_err <= 3e-3, emb_err
+    # loss and gradient over 24 pairs
+    pairs = [(a, (a * 5 + 1) % K) for a in range(0, bags.N, 2)]
+    targets = [w2_exact(cents[q][0], cents[q][1], *members[a]) for a, q in pairs]
+    L, g = mlp.pair_loss_and_grad(params, members, cents, pairs, targets)
+    pb = torch.tensor([a for a, _ in pairs], dtype=torch.int64, device="cuda")
+    pc = torch.tensor([q for _, q in pairs], dtype=torch.int32, device="cuda")
+    tg = torch.tensor(targets, dtype=torch.float32, device="cuda")
+    loss, grad = p.loss_grad(db, x.cuda(), w.cuda(), pb, pc, tg)
+    assert abs(float(loss) - L) <= 3e-3 * L, (float(loss), L)
+    gg = {k: v.double().numpy() for k, v in p.unpack(grad.cpu()).items()}
+    worst = {}
+    for name in mlp.PARAM_NAMES:
+        tol = 3e-3 * np.abs(g[name]).max()
+        err = np.abs(gg[name] - g[name])
+        worst[name] = float(err.max() / np.abs(g[name]).max())
+        assert (err <= tol).all(), (name, worst[name])
+    # power: drop the centroid-side term of the first pair from the oracle
+    a0, q0 = pairs[0]
+    fa = mlp.embed(params, *members[a0])
+    fq, cache = mlp.embed(params, *cents[q0], want_cache=True)
+    mu2 = float(np.sum((mlp.mean_of(*members[a0]) - mlp.mean_of(*cents[q0])) ** 2))
+    res = float((fa - fq) @ (fa - fq)) - (targets[0] - mu2)
+    gq = mlp.embed_backward(params, cache, -(2.0 * res / len(pairs)) * 2.0 * (fa - fq))
+    caught = [name for name in mlp.PARAM_NAMES
+              if (np.abs((g[name] - gq[name]) - g[name]) > 3e-3 * np.abs(g[name]).max()).any()]
+    assert caught, "the element-wise check cannot see a missing pair term"
+    print("MLP element-wise: embedding %.2e, gradient blocks %s (relative to the block max)"
+          % (emb_err, {k: "%.1e" % v for k, v in worst.items()}))

@@ -178,3 +178,100 @@ def test_init_pick_falls_back_to_the_largest():
         assert len(set(q)) == 3 and all(sizes[k] >= 6 for k in q)
     # the fallback threshold equals m when exactly K bags qualify
     assert sorted(init_pick(sizes, 3, 9, 1)) == [1, 3, 9]
+
+
+def test_pad_support_golden():
+    """Padding reading (Section 5 assumes m_k >= m): hand-derived golden values,
+    and padding leaves the distribution unchanged (W^2 to the seed is 0)."""
+    from oracle.cluster import pad_support
+    g = json.load(open(os.path.join(GOLD, "pad_support.json")))
+    x, w = pad_support(np.array(g["x"]), np.array(g["w"]), g["m"])
+    np.testing.assert_array_equal(x, np.array(g["x_out"]))
+    np.testing.assert_array_equal(w, np.array(g["w_out"]))
+    np.testing.assert_allclose(w @ x, np.array(g["mean"]), atol=1e-15)
+    assert w2_exact(x, w, np.array(g["x"]), np.array(g["w"])) <= 1e-12
+    # a seed that already has m points (or more) is returned as it is
+    x2, w2 = pad_support(np.array(g["x"]), np.array(g["w"]), 2)
+    np.testing.assert_array_equal(x2, np.array(g["x"]))
+    np.testing.assert_array_equal(w2, np.array(g["w"]))
+
+
+def test_d2_cluster_pads_small_seeds():
+    """With m above every m_k each seed is the (unmerged) bag plus zero-weight
+    copies of its last point: the first round's W^2 to that seed's own bag is 0."""
+    rng = np.random.default_rng(8)
+    bags = [(rng.normal(size=(int(rng.integers(2, 5)), 2)), None) for _ in range(7)]
+    bags = [(y, rng.dirichlet(np.ones(len(y)))) for y, _ in bags]
+    K, m = 2, 6
+    res = d2_cluster(bags, K, m, seed=4, rounds=1, T=5, tau=10)
+    picks = res["picks"]
+    from oracle.cluster import d2_assign as oracle_assign
+    # recompute the round-1 distances to the padded seeds directly
+    seeds = []
+    for k in picks:
+        y, wy = bags[k]
+        q = y.shape[0]
+        seeds.append((np.vstack([y] + [y[-1:]] * (m - q)), np.concatenate([wy, np.zeros(m - q)])))
+    _, dists, D = oracle_assign(bags, seeds)
+    for i, k in enumerate(picks):
+        assert D[k, i] <= 1e-12
+    assert abs(res["obj_per_round"][0] - dists.mean()) <= 1e-12
+
+
+def test_d2_cluster_warm_start_selection(monkeypatch):
+    """Section 5, warm start: in round r > 0 a member starts from its cached
+    Pi^(k,2) exactly when its label equals its label of round r - 1 (the most
+    recent assignment); every other member, and every member in round 0,
+    starts from w_i w_j^(k).  Labels are teacher-forced so that the expected
+    sequence of barycenter calls can be written out by hand:
+
+      labels  round 0: 0 0 0 1 1 1
+              round 1: 0 1 0 1 0 1   (members 1 and 4 move)
+              round 2: 1 1 0 1 0 1   (member 0 moves; 1 and 4 stay where round 1 put them)
+
+      round 0: cluster 0 <- [0, 1, 2] all cold;  cluster 1 <- [3, 4, 5] all cold
+      round 1: cluster 0 <- [0, 2, 4] warm T T F; cluster 1 <- [1, 3, 5] warm F T T
+      round 2: cluster 0 <- [2, 4]    warm T T;   cluster 1 <- [0, 1, 3, 5] warm F T T T
+
+    and a warm member's plan0 is the Pi^(k,2) that its previous round's call
+    returned for it (member 1's in round 2 comes from round 1's cluster 1
+    call, not from round 0)."""
+    import oracle.cluster as oc
+    rng = np.random.default_rng(12)
+    bags = [(rng.normal(size=(3 + (k % 3), 2)) + (k // 3) * 3.0, None) for k in range(6)]
+    bags = [(y, rng.dirichlet(np.ones(len(y)))) for y, _ in bags]
+    ids_of = {id(b[0]): k for k, b in enumerate(bags)}
+    calls = []
+    real = oc.badmm_barycenter
+
+    def recorder(members, x0, w0, **kw):
+        res = real(members, x0, w0, **kw)
+        ids = [ids_of[id(y)] for y, _ in members]
+        warm = kw.get("warm")
+        plan0 = kw.get("plan0")
+        calls.append(dict(ids=ids, warm=[bool(v) for v in warm],
+                          plan0={k: (None if p is None else p.copy()) for k, p in zip(ids, plan0)},
+                          P2={k: res["P2"][t].copy() for t, k in enumerate(ids)}))
+        return res
+
+    monkeypatch.setattr(oc, "badmm_barycenter", recorder)
+    L = [[0, 0, 0, 1, 1, 1], [0, 1, 0, 1, 0, 1], [1, 1, 0, 1, 0, 1]]
+    oc.d2_cluster(bags, 2, 2, seed=1, rounds=3, T=4, tau=10, labels_in=L)
+    expect = [([0, 1, 2], [False] * 3), ([3, 4, 5], [False] * 3),
+              ([0, 2, 4], [True, True, False]), ([1, 3, 5], [False, True, True]),
+              ([2, 4], [True, True]), ([0, 1, 3, 5], [False, True, True, True])]
+    assert [(c["ids"], c["warm"]) for c in calls] == expect
+    # plan0 of each warm member is what the previous round returned for it
+    r0 = {**calls[0]["P2"], **calls[1]["P2"]}
+    r1 = {**calls[2]["P2"], **calls[3]["P2"]}
+    for k in (0, 2):
+        np.testing.assert_array_equal(calls[2]["plan0"][k], r0[k])
+    for k in (3, 5):
+        np.testing.assert_array_equal(calls[3]["plan0"][k], r0[k])
+    for k in (2, 4):
+        np.testing.assert_array_equal(calls[4]["plan0"][k], r1[k])
+    for k in (1, 3, 5):
+        np.testing.assert_array_equal(calls[5]["plan0"][k], r1[k])
+    # member 1's round-0 plan (cluster 0) differs from its round-1 plan: the
+    # check above really distinguishes the two rounds' caches
+    assert r0[1].shape == r1[1].shape and not np.array_equal(r0[1], r1[1])

@@ -54,3 +54,23 @@ def test_rejects_problems_beyond_the_scratch(d2):
     with pytest.raises(d2.D2Error) as e:
         d2.d2_assign_noalloc(db, x, w)
     assert e.value.code == d2.D2_ESCRATCH
+
+
+def test_rejects_unsupported_and_invalid_shapes(d2):
+    """Both rejections happen on the host before any kernel runs: m + max_mk
+    above the solver's 256 nodes (D2_ENOTSUP), and bags with neither a
+    support matrix nor a vocabulary (D2_EINVAL)."""
+    bags, _, _ = problem(4, 40, 1, 4, 3)
+    db = d2.DeviceBags.from_synth(bags)
+    m = 257 - db.max_mk
+    x = torch.zeros(1, m, 3, device="cuda")
+    w = torch.full((1, m), 1.0 / m, device="cuda")
+    with pytest.raises(d2.D2Error) as e:
+        d2.d2_assign_noalloc(db, x, w)
+    assert e.value.code == d2.D2_ENOTSUP
+    bare = d2.DeviceBags(db.offsets, db.wt, db.d, supp=None, max_mk=db.max_mk)
+    x = torch.zeros(1, 4, 3, device="cuda")
+    w = torch.full((1, 4), 0.25, device="cuda")
+    with pytest.raises(d2.D2Error) as e:
+        d2.d2_assign_noalloc(bare, x, w)
+    assert e.value.code == d2.D2_EINVAL
