@@ -267,8 +267,101 @@ def _d2_round_comparison(d2, ctx, dev, seed):
     out.update({"bounded_s_per_round": te / R, "obj_bounded": oe,
                 "labels_equal_bounded_vs_batched": bool(torch.equal(le, lb)),
                 "speedup_bounded_vs_plain": out["plain_s_per_round"] / (te / R)})
+    # Elkan's triangle-inequality skipping (Section 5), exact
+    eopts = d2.badmm_opts(iters=W["iters"], tau=W["tau"], elkan=True)
+    d2.d2_cluster(ctx, db, K, m, 11, 1, eopts)
+    (xk, wk, lk, ok), tk = timed(lambda: d2.d2_cluster(ctx, db, K, m, 11, R, eopts))
+    out.update({"elkan_s_per_round": tk / R, "elkan_exact_solves": ctx.cluster_stats()["exact_solves"],
+                "labels_equal_elkan_vs_batched": bool(torch.equal(lk, lb))})
+    out["plain_form"] = ("this library one cluster per badmm_barycenter call with the register-prefetch "
+                         "sweep (FP32, fused iterations) and the exact full-K assignment: a conservative "
+                         "plain form")
     out["speedup_batched_vs_plain"] = out["plain_s_per_round"] / out["batched_s_per_round"]
     out["speedup_pruned_vs_plain"] = out["plain_s_per_round"] / out["pruned_s_per_round"]
+    return out
+
+
+PILOT_WORKLOAD = dict(N=64, d=2, mk=(4, 16), m=8, iters=200, tau=10,
+                      desc="single barycenter: N=64 distributions in d=2, m_k~U{4..16} from a 3-component "
+                           "Gaussian mixture (sigma=1, means on a radius-5 circle), Dirichlet(1) weights, "
+                           "m=8, rho0=2, T=200, tau=10")
+RHO0_SWEEP = (0.5, 1.0, 2.0, 4.0, 8.0, 16.0)
+
+
+def pilot_and_rho_study(d2, ctx, dev, seed, reps=20):
+    """The small single-barycenter workload (latency-bound: 5e3 plan entries):
+    plan-entry updates/s of one badmm_barycenter call, and the objective after
+    T iterations for rho0 in {0.5, ..., 16} under rules R1 and R2 (the
+    robustness study of Section 7.1 and the R1/R2 comparison of Table 1), on
+    this workload and on the K=10 Gaussian-class clusters at their true labels
+    (one update of T=100 iterations of all ten clusters)."""
+    W = PILOT_WORKLOAD
+    bags = synth.circle_mixture_bags(seed, N=W["N"], d=W["d"], mk=W["mk"])
+    co = torch.tensor([0, bags.N], dtype=torch.int64)
+    mem = torch.arange(bags.N, dtype=torch.int64)
+    x0, w0 = synth.sample_initial_barycenters(seed + 1, bags, co, mem, W["m"])
+    bags = bags.to(dev)
+    db = d2.DeviceBags(bags.offsets, bags.wt, bags.d, supp=bags.supp)
+    co, mem, x0, w0 = co.to(dev), mem.to(dev), x0.to(dev), w0.to(dev)
+    T, m = W["iters"], W["m"]
+    x, w = x0.clone(), w0.clone()
+    plan = torch.empty(bags.n, m, dtype=torch.float32, device=dev)
+    obj = torch.empty(1, dtype=torch.float64, device=dev)
+    side = torch.cuda.Stream(device=dev)   # graph replay needs a non-default stream
+    out = {"workload": W["desc"], "plan_entries": m * bags.n}
+    with torch.cuda.stream(side):
+        opts = d2.badmm_opts(iters=T, tau=W["tau"])
+        for _ in range(3):
+            x.copy_(x0)
+            w.copy_(w0)
+            d2.badmm_barycenter(ctx, db, co, mem, x, w, plan, None, opts, obj)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        for _ in range(reps):
+            x.copy_(x0)
+            w.copy_(w0)
+            d2.badmm_barycenter(ctx, db, co, mem, x, w, plan, None, opts, obj)
+        e1.record(side)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out.update({"ms_per_call": ms, "value": m * bags.n * T / (ms * 1e-3), "unit": UNIT,
+                    "note": "latency-bound (about 135 launches of a few microseconds, one CUDA graph)"})
+        study = {}
+        for rule in ("R1", "R2"):
+            row = {}
+            for r0 in RHO0_SWEEP:
+                x.copy_(x0)
+                w.copy_(w0)
+                d2.badmm_barycenter(ctx, db, co, mem, x, w, plan, None,
+                                    d2.badmm_opts(iters=T, tau=W["tau"], rho0=r0, rule=rule), obj)
+                row[str(r0)] = float(obj.item())
+            study[rule] = row
+        out["objective_after_T"] = study
+        # the K=10 Gaussian classes at their true labels
+        D = D2_WORKLOAD
+        gb = synth.gaussian_class_bags(seed + 2, D["N"], D["d"], D["K"], mk=D["mk"], device=dev)
+        gdb = d2.DeviceBags(gb.offsets, gb.wt, gb.d, supp=gb.supp)
+        order = torch.sort(gb.labels, stable=True).indices.contiguous()
+        gco = torch.zeros(D["K"] + 1, dtype=torch.int64, device=dev)
+        gco[1:] = torch.cumsum(torch.bincount(gb.labels, minlength=D["K"]), 0)
+        gx0, gw0 = synth.sample_initial_barycenters(seed + 3, gb, gco, order, D["m"])
+        nc = (gco[1:] - gco[:-1]).double()
+        gobj = torch.empty(D["K"], dtype=torch.float64, device=dev)
+        gstudy = {}
+        for rule in ("R1", "R2"):
+            row = {}
+            for r0 in RHO0_SWEEP:
+                gx, gw = gx0.clone(), gw0.clone()
+                d2.badmm_barycenter(ctx, gdb, gco, order, gx, gw, None, None,
+                                    d2.badmm_opts(iters=D["iters"], tau=D["tau"], rho0=r0, rule=rule), gobj)
+                row[str(r0)] = float((gobj * nc).sum().item() / gb.N)
+            gstudy[rule] = row
+        torch.cuda.synchronize()
+    out["gaussian_classes_objective_after_T"] = {
+        "workload": "K=10 Gaussian classes of the D2-clustering workload at their true labels, one update "
+                    "of T=%d iterations; objective = (1/N) sum_c N_c F_c" % D["iters"], **gstudy}
+    allv = [v for r in study.values() for v in r.values()]
+    out["objective_spread_rel"] = (max(allv) - min(allv)) / min(allv)
     return out
 
 
@@ -331,6 +424,26 @@ def pruning_at_scale(d2, ctx, dev, seed, steps=1500):
     (lp, _, st), t_pruned = timed(lambda: d2.d2_assign(ctx, dsub, x, w, prune=pr, want_stats=True))
     (la, _, st_all), t_all = timed(lambda: d2.d2_assign(ctx, db, x, w, prune=pr, want_stats=True))
     mis = float((lp != le).float().mean())
+    # the non-learned alternatives on the same evaluation bags: the exact mean
+    # term alone as the margin (delta = infinity), the certified lower bounds
+    # (Eq. primal relaxations and the mean term; exact), and the learned
+    # candidates followed by the certified bounds (exact)
+    pr.set_margin(r, 1e30)
+    (lm, _, stm), t_mean = timed(lambda: d2.d2_assign(ctx, dsub, x, w, prune=pr, want_stats=True))
+    pr.set_margin(r, delta)
+    (lb, _, stb), t_bnd = timed(lambda: d2.d2_assign(ctx, dsub, x, w, want_stats=True, bounded=True))
+    (lbp, _, stbp), t_bndp = timed(lambda: d2.d2_assign(ctx, dsub, x, w, prune=pr, want_stats=True, bounded=True))
+    out["alternatives"] = {
+        "mean_term_only": {"s": t_mean, "exact_solves": stm["exact_solves"], "fallbacks": stm["fallbacks"],
+                           "misassignment_vs_exact": float((lm != le).float().mean())},
+        "certified_bounds": {"s": t_bnd, "exact_solves": stb["exact_solves"],
+                             "misassignment_vs_exact": float((lb != le).float().mean())},
+        "learned_then_certified_bounds": {"s": t_bndp, "exact_solves": stbp["exact_solves"],
+                                          "misassignment_vs_exact": float((lbp != le).float().mean())},
+        "elkan": "applies across rounds only (its bounds come from the previous round's centroids); "
+                 "compared in d2_round",
+        "learned_speedup_vs_certified_bounds": t_bnd / t_pruned,
+        "learned_speedup_vs_mean_term_only": t_mean / t_pruned}
     out.update({"train_pairs": npairs, "target_w2_s": t_tg, "train_steps": steps, "train_s": t_train,
                 "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:])),
                 "r": r, "delta": delta, "eval_bags": ev,
@@ -451,6 +564,55 @@ def docs_clustering(d2, ctx, dev, seed, n_docs=None):
                                    "labels_equal_full_K": bool(torch.equal(lbd, le))},
                 # (against the merge-initialised centroids; later rounds' LPs take longer)
                 "full_K_assign_s_initial_centroids_est": bags.N * K / (ns * K / t_ex)})
+    return out
+
+
+def docs_rounds(d2, ctx, dev, seed, rounds=2):
+    """The document workload at full size, a short run: D2-clustering rounds
+    (Algorithm 1) with the exact assignment by certified bounds and the
+    split-BF16 tensor-core cost build, timed as one d2_cluster call with
+    per-launch CUDA events: seconds per round, the exact solver's pair rate,
+    the B-ADMM update's share and the fused plan sweep's HBM roofline."""
+    W = DOCS_WORKLOAD
+    K, m = W["K"], W["m"]
+    t0 = time.perf_counter()
+    bags = synth.document_bags(seed, W["N"], V=W["V"], d=W["d"], mk=W["mk"], device=dev)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    db = d2.DeviceBags(bags.offsets, bags.wt, bags.d, vocab_idx=bags.vocab_idx, vocab=bags.vocab)
+    opts = d2.badmm_opts(iters=W["iters"], tau=W["tau"], cost="bf16x3", assign_bounded=True)
+    ctx.timing(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, w, lab, objs = d2.d2_cluster(ctx, db, K, m, 11, rounds, opts)
+    torch.cuda.synchronize()
+    t_cl = time.perf_counter() - t0
+    kt = ctx.timing_read()
+    ctx.timing(False)
+    cs = ctx.cluster_stats()
+    out = {"workload": W["desc"].replace("5 rounds", "%d rounds" % rounds), "N": bags.N,
+           "support_rows": bags.n, "generate_s": t_gen, "rounds": rounds,
+           "s_per_round": t_cl / rounds, "obj_per_round": objs,
+           "assignment": "exact (certified lower bounds skip LPs; labels equal to the full N x K solve)",
+           "exact_solves": cs["exact_solves"], "full_K_pairs": bags.N * K * rounds,
+           "kernel_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in kt.items() if v[1]}}
+    a_ms, a_n = kt["assign"]
+    if a_n:
+        out["exact_pairs_per_s"] = cs["exact_solves"] / (a_ms * 1e-3)
+    f_ms, f_n = kt["sweep_fused"]
+    if f_n:
+        peak, peak_kind = load_peaks()
+        sbytes = BYTES_PER_ENTRY * m * bags.n
+        ach = sbytes / (f_ms / f_n * 1e-3) / 1e9
+        out["sweep_roofline"] = {"bound": "hbm", "kernel": "k_sweep_pipe (fused B+A pass)", "achieved": ach,
+                                 "peak": peak, "peak_source": peak_kind, "unit": "GB/s", "frac": ach / peak,
+                                 "algorithmic_bytes_per_launch": sbytes, "avg_launch_ms": f_ms / f_n,
+                                 "launches": f_n}
+    upd = sum(kt[k][0] for k in ("sweep_fused", "sweep_half", "cost", "support"))
+    out["badmm_update_ms_per_round"] = upd / rounds
+    out["badmm_updates_per_s"] = m * bags.n * W["iters"] * rounds / max(upd * 1e-3, 1e-12)
+    del bags, db
+    torch.cuda.empty_cache()
     return out
 
 
@@ -739,7 +901,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-d2", action="store_true", help="skip the D2-clustering s/round comparison")
-    ap.add_argument("--pruning", action="store_true", help="also run the learned-pruning assignment at scale")
+    ap.add_argument("--no-pruning", action="store_true", help="skip the learned-pruning assignment at scale")
+    ap.add_argument("--no-pilot", action="store_true", help="skip the N=64 pilot and the rho0 / R1-R2 study")
+    ap.add_argument("--no-docs-rounds", action="store_true", help="skip the two document-workload rounds")
     ap.add_argument("--docs-n", type=int, default=None, help="document count of --docs (default 200,000)")
     ap.add_argument("--docs", action="store_true",
                     help="also run D2-clustering of the 200k document-like bags (d=300, K=64, m=64)")
@@ -912,8 +1076,22 @@ def main():
         except Exception as exc:  # reported, never hides the main metric
             d2cmp = {"error": repr(exc)}
 
+    pilot = None
+    if rank == 0 and not args.no_pilot:
+        try:
+            pilot = pilot_and_rho_study(d2, ctx, dev, args.seed + 23)
+        except Exception as exc:
+            pilot = {"error": repr(exc)}
+
+    docs_short = None
+    if rank == 0 and not args.no_docs_rounds and not args.docs:
+        try:
+            docs_short = docs_rounds(d2, ctx, dev, args.seed + 41)
+        except Exception as exc:
+            docs_short = {"error": repr(exc)}
+
     prune_res = None
-    if rank == 0 and args.pruning:
+    if rank == 0 and not args.no_pruning:
         try:
             prune_res = pruning_at_scale(d2, ctx, dev, args.seed + 31)
         except Exception as exc:
@@ -952,6 +1130,10 @@ def main():
                 "kernel_breakdown_ms_per_step": breakdown, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "d2_round": d2cmp,
                 "cpu_baseline_all_cores": cpu_all}
+        if pilot is not None:
+            line["pilot"] = pilot
+        if docs_short is not None:
+            line["docs_rounds"] = docs_short
         if prune_res is not None:
             line["pruning"] = prune_res
         if docs_res is not None:

@@ -194,6 +194,17 @@ int d2_device_errors(d2_ctx* ctx, int32_t* bits);
  * report D2_ENOCONV.  Returns D2_EINVAL for a negative cap. */
 int d2_set_phase_limit(d2_ctx* ctx, int32_t max_phases);
 
+/* Flow store of the exact W^2 solver on this context (no counterpart in the
+ * paper; the LP of Eq. primal is the same either way).  store = 0 (default):
+ * per size class of bags, the store that keeps more warps resident per SM;
+ * 1: dense flow tableaus; 2: sparse (per-point bitmasks and a pool of nonzero
+ * flows).  A pair whose sparse pool overflows is solved again with the dense
+ * store in the same call (up to 65,536 pairs per call; beyond that a pair is
+ * reported like a phase-cap hit, D2_ENOCONV).  pool_cap > 0 caps the pool's
+ * entries below its default 2 (m + m_k), to exercise that path in tests.
+ * Returns D2_EINVAL for a store outside 0..2 or a negative cap. */
+int d2_set_flow_store(d2_ctx* ctx, int32_t store, int32_t pool_cap);
+
 /* Validate a bag set on the device (synchronous): offsets non-decreasing with
  * offsets[N] == n and every m_k in [1, max_mk]; weights finite, >= 0 and each
  * bag's sum within 1e-5 of 1 (Section 2: w in the simplex); vocabulary indices

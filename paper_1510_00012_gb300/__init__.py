@@ -64,6 +64,7 @@ _SIGS = {
     "d2_launch_count": (c_int64, [c_void_p]),
     "d2_device_errors": (c_int, [c_void_p, c_void_p]),
     "d2_set_phase_limit": (c_int, [c_void_p, c_int32]),
+    "d2_set_flow_store": (c_int, [c_void_p, c_int32, c_int32]),
     "d2_sweep_tuning": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "d2_cluster_stats": (c_int, [c_void_p, c_void_p]),
     "d2_cost": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32,
@@ -195,6 +196,12 @@ class Context:
         """Cap the exact solver's shortest-path phases per pair (0 = default);
         a low cap makes solves stop early and report D2_ENOCONV."""
         self.check(lib().d2_set_phase_limit(self.h, int(max_phases)))
+
+    def set_flow_store(self, store="auto", pool_cap=0):
+        """Exact solver's flow store: "auto", "dense" or "sparse"; pool_cap > 0
+        caps the sparse pool (overflowed pairs are solved again densely)."""
+        code = {"auto": 0, "dense": 1, "sparse": 2}[store]
+        self.check(lib().d2_set_flow_store(self.h, code, int(pool_cap)))
 
     def sweep_tuning(self, m):
         """The plan-sweep autotuner's record for plan width m: None when untuned,

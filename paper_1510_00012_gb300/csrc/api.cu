@@ -176,6 +176,13 @@ extern "C" int d2_device_errors(d2_ctx* ctx, int32_t* bits) {
     return D2_OK;
 }
 
+extern "C" int d2_set_flow_store(d2_ctx* ctx, int32_t store, int32_t pool_cap) {
+    if (!ctx || store < 0 || store > 2 || pool_cap < 0) return D2_EINVAL;
+    ctx->flow_store = store;
+    ctx->pool_cap = pool_cap;
+    return D2_OK;
+}
+
 extern "C" int d2_set_phase_limit(d2_ctx* ctx, int32_t max_phases) {
     if (!ctx || max_phases < 0) return D2_EINVAL;
     ctx->phase_limit = max_phases;

@@ -15,6 +15,18 @@
 // pot_i = 0, pot_j = min_i C_ij and every sink sends what it can to its
 // cheapest source (those arcs have zero reduced cost).  Costs, flows and
 // potentials are FP32; the final cost sum_ij f_ij C_ij is accumulated in FP64.
+//
+// Flow storage.  Only the cost tableau needs dense random access: the
+// shortest-path passes read whole cost rows and columns but ask of the flow
+// only whether a backward arc exists.  The sparse store keeps, per bag point
+// j, a bitmask of the centroid points with flow above tol into it, and the
+// nonzero flows themselves in a small pool of entries linked per bag point
+// (lane 0 alone edits it, during the greedy start and the augmentations).  A
+// transportation flow built along shortest paths has about m + m_k - 1
+// nonzeros; degenerate costs can add cycles, so a pair whose pool overflows
+// is put on a list and solved again by the dense store afterwards.  Both
+// stores do the same arithmetic in the same order, so a pair's flow does not
+// depend on the store; only the order of the final FP64 sum differs.
 #include <algorithm>
 #include <cstring>
 
@@ -38,9 +50,11 @@ struct AssignArgs {
     const float* x;    // K x m x d
     const float* w;    // K x m
     int m, K, nmax;
+    int nlo;                   // this launch solves only bags with nlo < m_k <= nmax
     // pair enumeration
     int mode;                  // 0: all N*K pairs; 1: explicit list; 2: all K for listed bags;
-                               // 3: r candidates per bag (bag p / r, centroid cand[p])
+                               // 3: r candidates per bag (bag p / r, centroid cand[p]);
+                               // 4: explicit list with output slots (re-solves)
     int64_t npairs;            // mode 0/1 host count (mode 1: upper bound if npairs_dev)
     const int64_t* npairs_dev; // mode 1/2: device count (pairs, or bags for mode 2)
     const int64_t* pair_bag;   // mode 1
@@ -48,29 +62,131 @@ struct AssignArgs {
     const int64_t* bag_list;   // mode 2
     const int32_t* cand;       // mode 3
     int r;                     // mode 3
-    float* out;                // mode 0/2: out[bag*K + cent]; mode 1: out[pair]
+    float* out;                // mode 0/2: out[bag*K + cent]; mode 1: out[pair]; mode 4: out[pair_slot[p]]
+    const int64_t* pair_slot;  // mode 4 (with pair_bag, pair_cent, npairs_dev)
+    // pairs whose sparse flow pool overflowed, solved again by the dense store
+    int64_t* ovf_bag;
+    int32_t* ovf_cent;
+    int64_t* ovf_slot;
+    int64_t* ovf_cnt;
+    int64_t ovf_cap;
+    int pool_cap;              // > 0: fewer sparse pool entries than the layout's (testing)
     int* flags;
     int64_t* pivot_fail;       // count of pairs that hit the phase limit
     int max_phase;
     size_t warp_bytes;
 };
 
-// the cost-build staging (AS_DC x (m + n) floats) lives in the flow tableau,
-// which is only cleared after the cost is built, whenever it fits there
-__host__ __device__ static inline bool staging_in_flows(int m, int nmax) { return AS_DC * (m + nmax) <= m * nmax; }
-
-// Per-warp shared memory: the cost and flow tableaus, the initial potentials
-// and excesses (moved to registers once the greedy start is done), the
-// predecessor of every node, and the cost-build staging.
-struct WarpMem {
-    float* C;      // m x n
-    float* F;      // m x n
-    float* pot;    // V
-    float* exc;    // V
-    short* pred;   // V
-    float* xs;     // AS_DC x m
-    float* ys;     // AS_DC x n
+// Per-warp shared memory (byte offsets from the warp's slice), for bags of
+// at most ncap points: the cost tableau (m x ns floats, ns = ncap | 1); the
+// flow store (dense: an m x ns tableau; sparse: E pool flows, the per-point
+// bitmasks (ncap x MW words), the pool list heads and links); the initial
+// potentials and excesses (moved to registers once the greedy start is done);
+// the predecessor of every node; the cost-build staging (AS_DC x (m + ncap)
+// floats), which shares the flow store's space when it fits there, since the
+// flows are initialised only after the cost is built.
+struct WarpLayout {
+    size_t c, f, ef, mask, head, enext, esrc, pot, exc, pred, xs, ys, bytes;
+    int E, MW;
 };
+__host__ __device__ inline size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
+__host__ __device__ inline WarpLayout warp_layout(int m, int ncap, bool sparse) {
+    WarpLayout L;
+    const int ns = ncap | 1, V = m + ncap;
+    L.MW = (m + 31) / 32;
+    L.E = sparse ? 2 * V : 0;
+    L.c = 0;
+    size_t o = al16((size_t)m * ns * 4);
+    L.f = L.ef = L.mask = L.head = L.enext = L.esrc = o;
+    size_t store;
+    if (!sparse) {
+        store = (size_t)m * ns * 4;
+    } else {
+        L.ef = o;
+        L.mask = L.ef + (size_t)L.E * 4;
+        L.head = L.mask + (size_t)ncap * L.MW * 4;
+        L.enext = L.head + (size_t)ncap * 2;
+        L.esrc = L.enext + (size_t)L.E * 2;
+        store = L.esrc + (size_t)L.E * 2 - o;
+    }
+    const size_t stage = (size_t)AS_DC * V * 4;
+    const bool stage_inside = stage <= store;
+    o = al16(o + store);
+    L.pot = o;
+    L.exc = L.pot + (size_t)V * 4;
+    L.pred = L.exc + (size_t)V * 4;
+    o = al16(L.pred + (size_t)V * 2);
+    if (stage_inside) {
+        L.xs = L.f;
+    } else {
+        L.xs = o;
+        o = al16(o + stage);
+    }
+    L.ys = L.xs + (size_t)AS_DC * m * 4;
+    L.bytes = o;
+    return L;
+}
+
+// Per-warp shared memory views (see WarpLayout).
+struct WarpMem {
+    float* C;        // m x ns
+    float* F;        // dense store: m x ns
+    float* ef;       // sparse store: E flows
+    unsigned* mask;  // sparse store: ncap x MW words; bit i of word (j, i / 32): flow (i, j) > tol
+    short* head;     // sparse store: ncap list heads (-1: no entry)
+    short* enext;    // sparse store: E links (also the free list)
+    short* esrc;     // sparse store: E centroid points
+    int E, MW;
+    float* pot;      // V
+    float* exc;      // V
+    short* pred;     // V
+    float* xs;       // AS_DC x m
+    float* ys;       // AS_DC x n
+};
+
+// ---- sparse flow store (lane 0 only) ------------------------------------
+// pool entry holding flow (i, j), or -1; *prev receives its predecessor in
+// the list of j (-1: the head).  Walks are bounded by the pool size.
+__device__ __forceinline__ int pool_find(const WarpMem& s, int i, int j, int* prev) {
+    int pv = -1, k = s.head[j];
+    for (int g = 0; g < s.E && (unsigned)k < (unsigned)s.E; ++g) {
+        if (s.esrc[k] == i) {
+            *prev = pv;
+            return k;
+        }
+        pv = k;
+        k = s.enext[k];
+    }
+    *prev = -1;
+    return -1;
+}
+__device__ __forceinline__ void pool_bit(const WarpMem& s, int i, int j, bool on) {
+    unsigned* wd = s.mask + j * s.MW + (i >> 5);
+    const unsigned b = 1u << (i & 31);
+    *wd = on ? (*wd | b) : (*wd & ~b);
+}
+// new entry (i, j) with flow 0 at the head of j's list, or -1 when the pool is full
+__device__ __forceinline__ int pool_new(const WarpMem& s, int i, int j, int& fbump, int& ffree) {
+    int k = -1;
+    if (ffree >= 0) {
+        k = ffree;
+        ffree = s.enext[k];
+    } else if (fbump < s.E) {
+        k = fbump++;
+    }
+    if (k < 0) return -1;
+    s.esrc[k] = (short)i;
+    s.ef[k] = 0.f;
+    s.enext[k] = s.head[j];
+    s.head[j] = (short)k;
+    return k;
+}
+__device__ __forceinline__ void pool_free(const WarpMem& s, int j, int k, int prev, int& ffree) {
+    if (prev < 0) s.head[j] = s.enext[k];
+    else s.enext[prev] = s.enext[k];
+    s.enext[k] = (short)ffree;
+    ffree = k;
+}
 
 __device__ __forceinline__ void warp_argmin(float& v, int& idx) {
 #pragma unroll
@@ -96,9 +212,12 @@ __device__ __forceinline__ float node_bcast(const float (&r)[TV], int v) {
     return __shfl_sync(0xffffffffu, x, v & 31);
 }
 
-// Solve one pair; returns W^2 (all lanes).  TV >= (m + n) / 32 node slots per lane.
-template <int TV>
-__device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int cent, bool& hit_limit) {
+// Solve one pair; returns W^2 (all lanes).  TV >= (m + n) / 32 node slots per
+// lane; SP selects the sparse flow store, whose pool overflow sets `overflow`
+// (the result is then invalid and the pair must be solved again densely).
+template <int TV, bool SP>
+__device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int cent, bool& hit_limit,
+                             bool& overflow) {
     const int lane = threadIdx.x & 31;
     const int m = a.m, d = a.d;
     const int64_t r0 = a.offsets[bag];
@@ -134,7 +253,15 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
         }
     }
     // ---- initial state
-    for (int e = lane; e < m * ns; e += 32) s.F[e] = 0.f;
+    int fbump = 0, ffree = -1;  // sparse pool allocator (lane 0)
+    overflow = false;
+    __syncwarp();  // the cost build's staging may share the flow store's space
+    if (SP) {
+        for (int e = lane; e < n * s.MW; e += 32) s.mask[e] = 0u;
+        for (int j = lane; j < n; j += 32) s.head[j] = -1;
+    } else {
+        for (int e = lane; e < m * ns; e += 32) s.F[e] = 0.f;
+    }
     for (int v = lane; v < V; v += 32) {
         s.exc[v] = (v < m) ? a.w[(int64_t)cent * m + v] : a.wt[r0 + (v - m)];
         s.pot[v] = 0.f;
@@ -155,12 +282,23 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
         s.pred[m + j] = (short)am;
     }
     __syncwarp();
+    bool gov = false;  // sparse pool full during the greedy start (only under a test cap)
     if (lane == 0) {
         for (int j = 0; j < n; ++j) {
             int i = s.pred[m + j];
             float f = fminf(s.exc[m + j], s.exc[i]);
             if (f > 0.f) {
-                s.F[i * ns + j] += f;
+                if (SP) {
+                    const int k = pool_new(s, i, j, fbump, ffree);
+                    if (k < 0) {
+                        gov = true;
+                        break;
+                    }
+                    s.ef[k] += f;
+                    if (s.ef[k] > 1e-9f) pool_bit(s, i, j, true);  // the tol below
+                } else {
+                    s.F[i * ns + j] += f;
+                }
                 s.exc[m + j] -= f;
                 s.exc[i] -= f;
             }
@@ -169,6 +307,10 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
     __syncwarp();
     const float tol = 1e-9f;
     hit_limit = false;
+    if (SP && __shfl_sync(0xffffffffu, (int)gov, 0)) {
+        overflow = true;
+        return 0.0;
+    }
     // node state in registers: node v is owned by lane v mod 32, slot v / 32
     float pot[TV], exc[TV], dist[TV];
 #pragma unroll
@@ -250,7 +392,9 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
 #pragma unroll
                 for (int t = 0; t < TV; ++t) {
                     const int i = lane + 32 * t;
-                    if (i < m && !((vis >> t) & 1u) && s.F[i * ns + j] > tol) {
+                    const bool arc = SP ? (i < m && ((s.mask[j * s.MW + t] >> lane) & 1u))
+                                        : (i < m && s.F[i * ns + j] > tol);
+                    if (arc && !((vis >> t) & 1u)) {
                         const float rc = fmaxf(-s.C[i * ns + j] + pu - pot[t], 0.f);
                         const float nd = du + rc;
                         if (nd < dist[t]) {
@@ -286,7 +430,17 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
                         src_node = v;
                         break;
                     }
-                    if (v < m) dflow = fminf(dflow, s.F[v * ns + (p - m)]);  // backward arc (v, p - m)
+                    if (v < m) {  // backward arc (v, p - m)
+                        float fv;
+                        if (SP) {
+                            int pv;
+                            const int k = pool_find(s, v, p - m, &pv);
+                            fv = k >= 0 ? s.ef[k] : 0.f;
+                        } else {
+                            fv = s.F[v * ns + (p - m)];
+                        }
+                        dflow = fminf(dflow, fv);
+                    }
                     v = p;
                 }
             }
@@ -294,19 +448,48 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
             dflow = __shfl_sync(0xffffffffu, dflow, 0);
             const float delta = fminf(fminf(dflow, node_bcast<TV>(exc, target)), node_bcast<TV>(exc, src_node));
             if (!(delta > 0.f)) continue;
+            bool ovf = false;
             if (lane == 0) {
                 int v = target;
                 for (int guard = 0; guard <= V; ++guard) {
                     const int p = s.pred[v];
                     if (p < 0) break;
-                    if (v >= m) {  // forward arc p -> v
-                        s.F[p * ns + (v - m)] += delta;
-                    } else {       // backward arc: flow on (v, p - m) decreases
-                        const float f = s.F[v * ns + (p - m)] - delta;
-                        s.F[v * ns + (p - m)] = f > 0.f ? f : 0.f;
+                    if (SP) {
+                        if (v >= m) {  // forward arc p -> v
+                            int pv;
+                            int k = pool_find(s, p, v - m, &pv);
+                            if (k < 0) k = pool_new(s, p, v - m, fbump, ffree);
+                            if (k < 0) {
+                                ovf = true;
+                                break;
+                            }
+                            s.ef[k] += delta;
+                            pool_bit(s, p, v - m, s.ef[k] > tol);
+                        } else {       // backward arc: flow on (v, p - m) decreases
+                            int pv;
+                            const int k = pool_find(s, v, p - m, &pv);
+                            if (k >= 0) {
+                                float f = s.ef[k] - delta;
+                                f = f > 0.f ? f : 0.f;
+                                if (f == 0.f) pool_free(s, p - m, k, pv, ffree);
+                                else s.ef[k] = f;
+                                pool_bit(s, v, p - m, f > tol);
+                            }
+                        }
+                    } else {
+                        if (v >= m) {  // forward arc p -> v
+                            s.F[p * ns + (v - m)] += delta;
+                        } else {       // backward arc: flow on (v, p - m) decreases
+                            const float f = s.F[v * ns + (p - m)] - delta;
+                            s.F[v * ns + (p - m)] = f > 0.f ? f : 0.f;
+                        }
                     }
                     v = p;
                 }
+            }
+            if (SP && __shfl_sync(0xffffffffu, (int)ovf, 0)) {
+                overflow = true;
+                break;
             }
 #pragma unroll
             for (int t = 0; t < TV; ++t) {
@@ -316,39 +499,53 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
             }
             __syncwarp();
         }
+        if (overflow) break;
     }
     // ---- cost of the flow, FP64
     double acc = 0.0;
-    for (int e = lane; e < m * ns; e += 32) acc += (double)s.F[e] * (double)s.C[e];  // padding: F = 0, C = 0
+    if (SP) {
+        __syncwarp();
+        for (int j = lane; j < n; j += 32) {
+            int k = s.head[j];
+            for (int g = 0; g < s.E && (unsigned)k < (unsigned)s.E; ++g) {
+                acc += (double)s.ef[k] * (double)s.C[s.esrc[k] * ns + j];
+                k = s.enext[k];
+            }
+        }
+    } else {
+        for (int e = lane; e < m * ns; e += 32) acc += (double)s.F[e] * (double)s.C[e];  // padding: F = 0, C = 0
+    }
     acc = group_sum_d<32>(acc);
     return acc;
 }
 
-template <int TV>
+template <int TV, bool SP>
 __global__ void k_w2_pairs(AssignArgs a) {
     extern __shared__ float4 dyn4[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     char* base = reinterpret_cast<char*>(dyn4) + (size_t)wib * a.warp_bytes;
-    const int m = a.m, n = a.nmax, V = m + n;
+    const int m = a.m, n = a.nmax;
+    const WarpLayout L = warp_layout(m, n, SP);
     WarpMem s;
-    s.C = reinterpret_cast<float*>(base);
-    s.F = s.C + m * (n | 1);
-    s.pot = s.F + m * (n | 1);
-    s.exc = s.pot + V;
-    if (staging_in_flows(m, n)) {
-        s.xs = s.F;
-        s.ys = s.F + AS_DC * m;
-        s.pred = reinterpret_cast<short*>(s.exc + V);
-    } else {
-        s.xs = s.exc + V;
-        s.ys = s.xs + AS_DC * m;
-        s.pred = reinterpret_cast<short*>(s.ys + AS_DC * n);
-    }
+    s.C = reinterpret_cast<float*>(base + L.c);
+    s.F = reinterpret_cast<float*>(base + L.f);
+    s.ef = reinterpret_cast<float*>(base + L.ef);
+    s.mask = reinterpret_cast<unsigned*>(base + L.mask);
+    s.head = reinterpret_cast<short*>(base + L.head);
+    s.enext = reinterpret_cast<short*>(base + L.enext);
+    s.esrc = reinterpret_cast<short*>(base + L.esrc);
+    s.E = (a.pool_cap > 0 && a.pool_cap < L.E) ? a.pool_cap : L.E;
+    s.MW = L.MW;
+    s.pot = reinterpret_cast<float*>(base + L.pot);
+    s.exc = reinterpret_cast<float*>(base + L.exc);
+    s.pred = reinterpret_cast<short*>(base + L.pred);
+    s.xs = reinterpret_cast<float*>(base + L.xs);
+    s.ys = reinterpret_cast<float*>(base + L.ys);
 
     int64_t total;
     if (a.mode == 0) total = a.npairs;
-    else if (a.mode == 1) total = a.npairs_dev ? min(*a.npairs_dev, a.npairs) : a.npairs;
+    else if (a.mode == 1 || a.mode == 4) total = a.npairs_dev ? min(*a.npairs_dev, a.npairs) : a.npairs;
     else if (a.mode == 2) total = (*a.npairs_dev) * a.K;
     else total = a.npairs;
     const int64_t nwarps = (int64_t)gridDim.x * wpb;
@@ -369,18 +566,39 @@ __global__ void k_w2_pairs(AssignArgs a) {
             cent = (int)(p - b * a.K);
             bag = a.bag_list[b];
             slot = bag * a.K + cent;
-        } else {
+        } else if (a.mode == 3) {
             bag = p / a.r;
             cent = a.cand[p];
             slot = p;
+        } else {
+            bag = a.pair_bag[p];
+            cent = a.pair_cent[p];
+            slot = a.pair_slot[p];
         }
-        bool lim = false;
-        double v = solve_pair<TV>(a, s, bag, cent, lim);
+        // size class of this launch (the per-warp tableaus are sized for nmax)
+        const int64_t mk = a.offsets[bag + 1] - a.offsets[bag];
+        if (mk <= a.nlo || mk > a.nmax) continue;
+        bool lim = false, ovf = false;
+        double v = solve_pair<TV, SP>(a, s, bag, cent, lim, ovf);
         if (lane == 0) {
-            a.out[slot] = (float)v;
-            if (lim) {
-                atomicOr(a.flags, D2F_PIVOT_LIMIT);
-                atomicAdd(reinterpret_cast<unsigned long long*>(a.pivot_fail), 1ull);
+            if (SP && ovf) {
+                // solved again by the dense store after this launch
+                const int64_t q = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(a.ovf_cnt), 1ull);
+                if (q < a.ovf_cap) {
+                    a.ovf_bag[q] = bag;
+                    a.ovf_cent[q] = cent;
+                    a.ovf_slot[q] = slot;
+                } else {  // the list is full: report the pair as unsolved
+                    a.out[slot] = (float)v;
+                    atomicOr(a.flags, D2F_PIVOT_LIMIT);
+                    atomicAdd(reinterpret_cast<unsigned long long*>(a.pivot_fail), 1ull);
+                }
+            } else {
+                a.out[slot] = (float)v;
+                if (lim) {
+                    atomicOr(a.flags, D2F_PIVOT_LIMIT);
+                    atomicAdd(reinterpret_cast<unsigned long long*>(a.pivot_fail), 1ull);
+                }
             }
         }
         __syncwarp();
@@ -406,12 +624,7 @@ __global__ void k_argmin_rows(const float* D, int64_t N, int K, int32_t* labels,
 }
 
 
-size_t d2_assign_warp_bytes(int m, int nmax) {
-    const int V = m + nmax;
-    const int stage = staging_in_flows(m, nmax) ? 0 : AS_DC * (m + nmax);
-    size_t b = (size_t)(2 * m * (nmax | 1) + 2 * V + stage) * 4 + (size_t)V * 2;
-    return (b + 15) & ~(size_t)15;
-}
+size_t d2_assign_warp_bytes(int m, int nmax) { return warp_layout(m, nmax, false).bytes; }
 
 // warps per block that maximise resident warps per SM for this footprint
 static int pick_wpb(size_t warp_bytes) {
@@ -428,34 +641,37 @@ static int pick_wpb(size_t warp_bytes) {
     return best;
 }
 
-// Solver instance for m + nmax nodes (node slots per lane), or null past 256.
+// Solver instance for m + nmax nodes (node slots per lane) and flow store,
+// or null past 256 nodes.
 typedef void (*W2Fn)(AssignArgs);
-static W2Fn w2_kernel_for(int V) {
-    if (V <= 64) return k_w2_pairs<2>;
-    if (V <= 128) return k_w2_pairs<4>;
-    if (V <= 256) return k_w2_pairs<8>;
+static W2Fn w2_kernel_for(int V, bool sparse) {
+    if (V <= 64) return sparse ? k_w2_pairs<2, true> : k_w2_pairs<2, false>;
+    if (V <= 128) return sparse ? k_w2_pairs<4, true> : k_w2_pairs<4, false>;
+    if (V <= 256) return sparse ? k_w2_pairs<8, true> : k_w2_pairs<8, false>;
     return nullptr;
 }
 
-// Launch shape of the pair solver for a.m + a.nmax nodes on `device`:
-// kernel, warps per block, dynamic shared memory and a grid bound (the
-// kernel is a persistent stride loop).  Returns D2_OK, or D2_ENOTSUP when the
-// per-warp tableaus exceed 200 KiB or m + max_mk exceeds 256 (then *why says
-// which), or D2_ECUDA when a runtime call fails.
+// Launch shape of the pair solver for a.m + a.nmax nodes on `device` with
+// the given flow store: kernel, warps per block, dynamic shared memory and a
+// grid bound (the kernel is a persistent stride loop; `resident` = warps per
+// SM).  Returns D2_OK, or D2_ENOTSUP when the per-warp memory exceeds 200 KiB
+// or m + max_mk exceeds 256 (then *why says which), or D2_ECUDA when a
+// runtime call fails.
 struct PairLaunch {
     W2Fn fn;
     int wpb;
     size_t smem;
     unsigned grid;
+    int resident;
 };
-static int pair_launch_config(AssignArgs& a, int64_t max_units, int device, PairLaunch* L, const char** why,
-                              cudaError_t* cerr) {
-    a.warp_bytes = d2_assign_warp_bytes(a.m, a.nmax);
+static int pair_launch_config(AssignArgs& a, int64_t max_units, int device, bool sparse, PairLaunch* L,
+                              const char** why, cudaError_t* cerr) {
+    a.warp_bytes = warp_layout(a.m, a.nmax, sparse).bytes;
     if (a.warp_bytes > 200 * 1024) {
         *why = "m * max_mk too large for the per-warp tableau";
         return D2_ENOTSUP;
     }
-    L->fn = w2_kernel_for(a.m + a.nmax);
+    L->fn = w2_kernel_for(a.m + a.nmax, sparse);
     if (!L->fn) {
         *why = "m + max_mk exceeds 256";
         return D2_ENOTSUP;
@@ -472,6 +688,7 @@ static int pair_launch_config(AssignArgs& a, int64_t max_units, int device, Pair
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L->fn, L->wpb * 32, L->smem);
     per_sm = std::max(per_sm, 1);
+    L->resident = per_sm * L->wpb;
     const int64_t want = d2_ceil_div(std::max<int64_t>(max_units, 1), L->wpb);
     L->grid = (unsigned)std::max<int64_t>(1, std::min(want, (int64_t)sms * per_sm * 8));
     return D2_OK;
@@ -481,19 +698,88 @@ static int pair_launch_config(AssignArgs& a, int64_t max_units, int device, Pair
 // flow to at least one deficit sink, so a pair needs far fewer)
 static inline int default_max_phase(int m, int nmax) { return 8 * (m + nmax) + 64; }
 
-// Launch the pair solver; grid is a bound (persistent stride loop).
+// Bags per size class of the solver's launches: one launch per class of
+// AS_CLASS support points, each with per-warp tableaus sized for its largest
+// bag, so that smaller bags fit more warps per SM.  A launch skips the pairs
+// of other classes; a pair's arithmetic does not depend on its launch.
+#define AS_CLASS 16
+
+// Pairs of one call whose sparse flow pool may overflow and be solved again
+// by the dense store (list capacity; beyond it a pair is reported as
+// unsolved through the phase-cap flag and count).
+#define AS_OVF_CAP 65536
+
+// Launch the pair solver, one launch per size class of bags; grid is a bound
+// (persistent stride loop).  Each class uses the flow store that keeps more
+// warps resident per SM (the dense one on ties); when any class used the
+// sparse store, a last launch re-solves its overflowed pairs densely.
 int d2_launch_pairs(d2_ctx* ctx, AssignArgs a, int64_t max_units, cudaStream_t st) {
-    PairLaunch L;
+    PairLaunch L, Ls;
     const char* why = "";
     cudaError_t ce = cudaSuccess;
-    const int rc = pair_launch_config(a, max_units, ctx->device, &L, &why, &ce);
+    const int nmax = a.nmax;
+    int rc = pair_launch_config(a, max_units, ctx->device, false, &L, &why, &ce);
     if (rc == D2_ENOTSUP) return d2_fail(ctx, D2_ENOTSUP, "d2_assign: %s (m = %d, max_mk = %d)", why, a.m, a.nmax);
     if (rc) return d2_cuda_fail(ctx, ce, why);
-    a.max_phase = ctx->phase_limit > 0 ? ctx->phase_limit : default_max_phase(a.m, a.nmax);
-    d2_time_begin(ctx, D2_KT_ASSIGN, st);
-    L.fn<<<L.grid, L.wpb * 32, L.smem, st>>>(a);
-    d2_time_end(ctx, st);
-    D2_LAUNCH_CK(ctx, "k_w2_pairs");
+    a.max_phase = ctx->phase_limit > 0 ? ctx->phase_limit : default_max_phase(a.m, nmax);
+    bool any_sparse = false;
+    for (int lo = 0; lo < nmax; lo += AS_CLASS) {
+        AssignArgs b = a;
+        b.nlo = lo;
+        b.nmax = std::min(nmax, lo + AS_CLASS);
+        AssignArgs bs = b;
+        if ((rc = pair_launch_config(b, max_units, ctx->device, false, &L, &why, &ce)))
+            return d2_cuda_fail(ctx, ce, why);
+        const bool sparse_ok = ctx->flow_store != 1 &&
+                               pair_launch_config(bs, max_units, ctx->device, true, &Ls, &why, &ce) == D2_OK;
+        if (sparse_ok && (ctx->flow_store == 2 || Ls.resident > L.resident)) {
+            bs.pool_cap = ctx->pool_cap;
+            if (!any_sparse) {
+                void* ov = nullptr;
+                const size_t cap = AS_OVF_CAP;
+                if ((rc = d2_ws(ctx, WS_ASSIGN_OVF, 64 + cap * (8 + 4 + 8), &ov))) return rc;
+                char* ob = static_cast<char*>(ov);
+                a.ovf_cnt = reinterpret_cast<int64_t*>(ob);
+                a.ovf_bag = reinterpret_cast<int64_t*>(ob + 64);
+                a.ovf_slot = reinterpret_cast<int64_t*>(ob + 64 + cap * 8);
+                a.ovf_cent = reinterpret_cast<int32_t*>(ob + 64 + cap * 16);
+                a.ovf_cap = (int64_t)cap;
+                D2_CK(ctx, cudaMemsetAsync(a.ovf_cnt, 0, sizeof(int64_t), st));
+                any_sparse = true;
+            }
+            bs.ovf_cnt = a.ovf_cnt;
+            bs.ovf_bag = a.ovf_bag;
+            bs.ovf_slot = a.ovf_slot;
+            bs.ovf_cent = a.ovf_cent;
+            bs.ovf_cap = a.ovf_cap;
+            b = bs;
+            L = Ls;
+        }
+        d2_time_begin(ctx, D2_KT_ASSIGN, st);
+        L.fn<<<L.grid, L.wpb * 32, L.smem, st>>>(b);
+        d2_time_end(ctx, st);
+        D2_LAUNCH_CK(ctx, "k_w2_pairs");
+    }
+    if (any_sparse) {
+        // the overflow list, densely, all size classes in one launch
+        AssignArgs r = a;
+        r.mode = 4;
+        r.npairs = a.ovf_cap;
+        r.npairs_dev = a.ovf_cnt;
+        r.pair_bag = a.ovf_bag;
+        r.pair_cent = a.ovf_cent;
+        r.pair_slot = a.ovf_slot;
+        r.nlo = 0;
+        r.nmax = nmax;
+        if ((rc = pair_launch_config(r, 1, ctx->device, false, &L, &why, &ce))) return d2_cuda_fail(ctx, ce, why);
+        int sms = 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+        L.grid = (unsigned)(sms * std::max(1, L.resident / L.wpb));
+        d2_time_begin(ctx, D2_KT_ASSIGN, st);
+        L.fn<<<L.grid, L.wpb * 32, L.smem, st>>>(r);
+        d2_time_end(ctx, st);
+        D2_LAUNCH_CK(ctx, "k_w2_pairs (overflow re-solve)");
+    }
     return D2_OK;
 }
 
@@ -597,11 +883,18 @@ int d2_assign_exact_into(const d2_bags* b, int K, int m, const float* x, const f
     PairLaunch L;
     const char* why = "";
     *cerr = cudaSuccess;
-    const int rc = pair_launch_config(a, a.npairs, device, &L, &why, cerr);
+    const int nmax = a.nmax;
+    int rc = pair_launch_config(a, a.npairs, device, false, &L, &why, cerr);
     if (rc) return rc;
-    a.max_phase = default_max_phase(a.m, a.nmax);
-    L.fn<<<L.grid, L.wpb * 32, L.smem, st>>>(a);
-    if ((*cerr = cudaGetLastError()) != cudaSuccess) return D2_ECUDA;
+    a.max_phase = default_max_phase(a.m, nmax);
+    for (int lo = 0; lo < nmax; lo += AS_CLASS) {
+        AssignArgs c = a;
+        c.nlo = lo;
+        c.nmax = std::min(nmax, lo + AS_CLASS);
+        if ((rc = pair_launch_config(c, c.npairs, device, false, &L, &why, cerr))) return rc;
+        L.fn<<<L.grid, L.wpb * 32, L.smem, st>>>(c);
+        if ((*cerr = cudaGetLastError()) != cudaSuccess) return D2_ECUDA;
+    }
     k_argmin_rows<<<(unsigned)d2_ceil_div(b->N, 256), 256, 0, st>>>(D, b->N, K, labels, dist);
     if ((*cerr = cudaGetLastError()) != cudaSuccess) return D2_ECUDA;
     return D2_OK;

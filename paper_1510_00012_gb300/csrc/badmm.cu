@@ -106,10 +106,30 @@ __device__ __forceinline__ float fast_exp2(float x) {
     return y;
 }
 
+// Double-float accumulation: a running sum held as an unevaluated pair
+// hi + lo of FP32 numbers, updated by error-free transformations (Knuth's
+// TwoSum; the product's rounding error by one FMA), so it carries about 48
+// significant bits, like an FP64 running sum, with FP32 instructions only
+// (FP64 throughput on this part is a small fraction of FP32).  The _rn
+// intrinsics keep the compiler from contracting the steps into FMAs.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float v) {
+    const float s = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+__device__ __forceinline__ void df_add_prod(float& hi, float& lo, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);  // a b = p + pe exactly
+    df_add(hi, lo, p);
+    lo = __fadd_rn(lo, pe);
+}
+
 // Weight consensus (Eq. badmmw / badmmw2) of one cluster per CTA, in FP64 and
 // a fixed order: thread (g, i) sums the members p0 + g, p0 + g + G, ... of
-// column i (every term converted to FP64 and added in FP64), the G groups are
-// then added in order, then the m columns.
+// column i in double-float (every term added exactly up to ~2^-48 of the
+// sum), the G groups are then added in order in FP64, then the m columns.
 __global__ void __launch_bounds__(256) k_consensus(const int64_t* cofs, const float* pos_part, int m, bool r2,
                                                    float* w_next, double* w_next64) {
     __shared__ double s_acc[256 + 257];
@@ -121,17 +141,17 @@ __global__ void __launch_bounds__(256) k_consensus(const int64_t* cofs, const fl
     const int i = t % m, g = t / m;
     if (g < G) {
         // eight loads in flight, added in member order
-        double acc = 0.0;
+        float hi = 0.f, lo = 0.f;
         int64_t p = p0 + g;
         for (; p + 7 * G < p1; p += 8 * G) {
             float v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) v[u] = __ldcg(pos_part + (p + u * G) * m + i);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) acc += (double)v[u];
+            for (int u = 0; u < 8; ++u) df_add(hi, lo, v[u]);
         }
-        for (; p < p1; p += G) acc += (double)pos_part[p * m + i];
-        s_acc[g * m + i] = acc;
+        for (; p < p1; p += G) df_add(hi, lo, pos_part[p * m + i]);
+        s_acc[g * m + i] = (double)hi + (double)lo;
     }
     __syncthreads();
     if (t < m) {
@@ -194,7 +214,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep(SweepArg
         float racc[NE];
 #pragma unroll
         for (int x = 0; x < NE; ++x) racc[x] = 0.f;
-        double objacc = 0.0;  // <C_k, Pi^(k,1)> of this lane's entries, FP64 (objective pass only)
+        float objhi = 0.f, objlo = 0.f;  // <C_k, Pi^(k,1)> of this lane's entries, double-float (objective pass)
 
         // one row group (RPW rows) per step; the next group's loads are issued
         // before the current group is computed
@@ -263,10 +283,12 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep(SweepArg
 #pragma unroll
                 for (int x = 0; x < NE; ++x) {
                     p1n[x] = t1[x] * scale;
-                    if (rv && ok[x]) {
-                        racc[x] += fmaf(p1n[x], fast_exp2(l2[x] * beta), eps);
-                        if (fl & SW_OBJ) objacc = fma((double)cin[x], (double)p1n[x], objacc);
-                    }
+                    if (rv && ok[x]) racc[x] += fmaf(p1n[x], fast_exp2(l2[x] * beta), eps);
+                }
+                if (fl & SW_OBJ) {  // objective pass only
+#pragma unroll
+                    for (int x = 0; x < NE; ++x)
+                        if (rv && ok[x]) df_add_prod(objhi, objlo, cin[x], p1n[x]);
                 }
                 if (rv) {
 #pragma unroll
@@ -322,7 +344,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep(SweepArg
                     }
             }
             if (fl & SW_OBJ) {
-                double ov = group_sum_d<32>(objacc);
+                double ov = group_sum_d<32>((double)objhi + (double)objlo);
                 if (lane == 0) a.pos_obj[p] = ov;
             }
         }
@@ -468,7 +490,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_PIPE_MINB) k_sweep_pipe(Swee
     // ---- compute cursor state (per member)
     float coef[NE], wcol[NE], racc[NE];
     float beta = 0.f, rho = 0.f;
-    double objacc = 0.0;  // <C_k, Pi^(k,1)> of this lane's entries, FP64 (objective pass only)
+    float objhi = 0.f, objlo = 0.f;  // <C_k, Pi^(k,1)> of this lane's entries, double-float (objective pass)
     bool ldP = false;
     const float eps = a.eps;
     int slot = 0;
@@ -497,7 +519,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_PIPE_MINB) k_sweep_pipe(Swee
             }
 #pragma unroll
             for (int x = 0; x < NE; ++x) racc[x] = 0.f;
-            objacc = 0.0;
+            objhi = objlo = 0.f;
         }
         const int j = mt.base + sub;
         const bool rv = j < mt.mk;
@@ -552,10 +574,12 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_PIPE_MINB) k_sweep_pipe(Swee
 #pragma unroll
             for (int x = 0; x < NE; ++x) {
                 p1n[x] = t1[x] * scale;
-                if (rv && okv[x / 4]) {
-                    racc[x] += fmaf(p1n[x], fast_exp2(l2[x] * beta), eps);
-                    if (fl & SW_OBJ) objacc = fma((double)cin[x], (double)p1n[x], objacc);
-                }
+                if (rv && okv[x / 4]) racc[x] += fmaf(p1n[x], fast_exp2(l2[x] * beta), eps);
+            }
+            if (fl & SW_OBJ) {  // objective pass only
+#pragma unroll
+                for (int x = 0; x < NE; ++x)
+                    if (rv && okv[x / 4]) df_add_prod(objhi, objlo, cin[x], p1n[x]);
             }
             if (rv) {
 #pragma unroll
@@ -607,7 +631,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, D2_PIPE_MINB) k_sweep_pipe(Swee
                 }
             }
             if (fl & SW_OBJ) {
-                double ov = group_sum_d<32>(objacc);
+                double ov = group_sum_d<32>((double)objhi + (double)objlo);
                 if (lane == 0) a.pos_obj[p] = ov;
             }
         }

@@ -33,6 +33,7 @@ enum WsSlot {
     WS_SPLIT,        // rebased cluster offsets of the second half of a split call
     WS_VOCAB,        // vocabulary cost table: word flags, slots, pseudo-members, chunks
     WS_VOCAB_T,      // vocabulary cost table rows (<= min(n, K V) x m floats)
+    WS_ASSIGN_OVF,   // exact solver: pairs whose sparse flow pool overflowed
     WS_NSLOTS
 };
 
@@ -78,6 +79,10 @@ struct d2_ctx {
     int expire_test = 0;
     // cap on the exact solver's shortest-path phases per pair (0: default)
     int phase_limit = 0;
+    // exact solver's flow store: 0 automatic, 1 dense, 2 sparse; and a cap on
+    // the sparse pool's entries (0: none) -- testing and tuning
+    int flow_store = 0;
+    int pool_cap = 0;
     // split calls (D2_SPLIT_STREAMS): two child contexts, each on its own
     // stream, with the per-entry workspaces lent by this context
     d2_ctx* child[2] = {nullptr, nullptr};

@@ -278,7 +278,7 @@ def test_w2_document_shape_eight_sinks(d2, ctx, doc_shape_case, centroids):
             clear += 1
     assert clear >= bags.N // 2
     print("document shape (%s centroids): max rel W^2 err %.2e, %d of %d labels with a clear margin"
-          % (centroids, float(np.max(np.abs(vals - ref) / ref)), clear, bags.N))
+          % (centroids, float(np.max(np.abs(vals - ref) / np.maximum(ref, 1e-6))), clear, bags.N))
 
 
 def test_elkan_clustering_matches_oracle(d2, ctx):
@@ -342,3 +342,62 @@ def test_phase_cap_is_reported_as_enoconv(d2):
     lab, dist, st = d2.d2_assign(c, db, x, w, want_stats=True)
     assert st["limit_hits"] == 0 and c.device_errors() == 0
     assert torch.equal(lab, ref_lab) and torch.equal(dist, ref_dist)
+
+
+@pytest.mark.parametrize("case", ["d16_m16", "d300_m64_vocab", "d32_m32", "d4_m5"])
+def test_sparse_and_dense_flow_stores_agree(d2, case):
+    """The exact solver's two flow stores run the same arithmetic: W^2 of every
+    pair equal up to the order of the final FP64 sum; a sparse pool capped so
+    that most pairs overflow hands them to the dense re-solve with the same
+    result; and against the exact LP on a sample."""
+    if case == "d300_m64_vocab":
+        bags = synth.document_bags(91, 60, V=4000, d=300, mk=(10, 60))
+        x, w = centroids(92, 3, 64, 300, scale=0.08)
+    else:
+        d, m = {"d16_m16": (16, 16), "d32_m32": (32, 32), "d4_m5": (4, 5)}[case]
+        bags = synth.gaussian_class_bags(93 + m, 120, d, 4, mk=(1, 60), mu_sigma=2.0)
+        x, w = centroids(94 + m, 4, m, d)
+    db = d2.DeviceBags.from_synth(bags)
+    x, w = x.cuda(), w.cuda()
+    K = x.shape[0]
+    pb = torch.arange(bags.N, dtype=torch.int64).repeat_interleave(K).cuda()
+    pc = torch.arange(K, dtype=torch.int32).repeat(bags.N).cuda()
+    c = d2.Context(0)
+    vals = {}
+    for store, cap in (("dense", 0), ("sparse", 0), ("sparse", 4), ("auto", 0)):
+        c.set_flow_store(store, cap)
+        vals[(store, cap)] = d2.d2_w2_pairs(c, db, x, w, pb, pc).cpu().double().numpy()
+        assert c.device_errors() == 0
+    ref = vals[("dense", 0)]
+    for key, v in vals.items():
+        np.testing.assert_allclose(v, ref, rtol=2e-7, atol=1e-12, err_msg=str(key))
+    for t in range(0, bags.N * K, max(1, bags.N * K // 24)):
+        k, ci = t // K, t % K
+        e = w2_exact(x[ci].double().cpu().numpy(), w[ci].double().cpu().numpy(), *bags.bag(k))
+        assert abs(ref[t] - e) <= 1e-4 * e + 1e-6, (t, ref[t], e)
+    # the assignment through both stores gives the same labels
+    c.set_flow_store("dense")
+    ld, dd = d2.d2_assign(c, db, x, w)
+    c.set_flow_store("sparse")
+    ls, ds = d2.d2_assign(c, db, x, w)
+    assert torch.equal(ld, ls)
+    np.testing.assert_allclose(ds.cpu().numpy(), dd.cpu().numpy(), rtol=2e-7)
+
+
+def test_overflow_list_beyond_capacity_reports_enoconv(d2):
+    """More overflowed pairs than the re-solve list holds (65,536): the ones
+    beyond it are reported (D2_ENOCONV), never returned silently."""
+    bags = synth.gaussian_class_bags(95, 2400, 3, 4, mk=(4, 12), mu_sigma=2.0)
+    db = d2.DeviceBags.from_synth(bags)
+    x, w = centroids(96, 32, 4, 3)
+    c = d2.Context(0)
+    c.set_flow_store("sparse", 1)   # one pool entry: every pair with more than one flow overflows
+    with pytest.raises(d2.D2Error) as e:
+        d2.d2_assign(c, db, x.cuda(), w.cuda(), want_stats=True)
+    assert e.value.code == d2.D2_ENOCONV
+    with pytest.raises(d2.D2Error) as e:     # the sticky bit, read and cleared
+        c.device_errors()
+    assert e.value.code == d2.D2_ENOCONV
+    c.set_flow_store("auto")
+    _, _, st = d2.d2_assign(c, db, x.cuda(), w.cuda(), want_stats=True)
+    assert st["limit_hits"] == 0 and c.device_errors() == 0
