@@ -100,6 +100,14 @@ extern "C" {
  * the j-major rows; the result is bitwise that of building every row.  This
  * flag builds every support row directly instead. */
 #define D2_COST_ROWS 0x1000
+/* Support update (Eq. updatex) on the tensor cores: with a tensor-core cost
+ * precision, d >= 32, d % 4 == 0, m % 4 == 0 and m <= 64, the partial sums
+ * sum_j pi_ij^(k,2) (y_j - mu_c) run as tcgen05 MMAs with split-BF16 operands
+ * (hi + lo, three products; hi + mid + lo with D2_COST_BF16X6) and an FP32
+ * accumulator in tensor memory, on coordinates centred at the cluster centre
+ * mu_c.  Off by default: measured slower than the FP32 CUDA-core partials
+ * on the shapes tested (the operands must be transposed and split). */
+#define D2_SUPPORT_TC 0x2000
 /* Testing only (d2_cost): the tensor-core build issues no MMA for each CTA's
  * first tile, so that CTA's bounded wait expires (about 2 s); the CTA then
  * stops, the call's output is undefined and d2_device_errors reports
@@ -134,7 +142,7 @@ typedef struct {
     int32_t rule;      /* D2_RULE_R1 (default) or D2_RULE_R2                            */
     int32_t flags;     /* D2_FIX_X | D2_FIX_W | D2_VALIDATE | D2_NO_GRAPH | D2_NO_PIPE |
                           D2_ELKAN | D2_AUTOTUNE | D2_SPLIT_STREAMS |
-                          D2_ASSIGN_BOUNDED | D2_PRUNE_RECALIBRATE | D2_COST_ROWS |
+                          D2_ASSIGN_BOUNDED | D2_PRUNE_RECALIBRATE | D2_COST_ROWS | D2_SUPPORT_TC |
                           one of D2_COST_BF16, _BF16X3, _BF16X6                        */
 } d2_badmm_opts;
 

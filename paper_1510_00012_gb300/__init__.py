@@ -28,6 +28,7 @@ D2_ASSIGN_BOUNDED = 0x200
 D2_SPLIT_STREAMS = 0x400
 D2_PRUNE_RECALIBRATE = 0x800
 D2_COST_ROWS = 0x1000
+D2_SUPPORT_TC = 0x2000
 D2_TEST_EXPIRE_WAIT = 0x8000
 D2_TUNE_MAX = 16
 COST_PRECISION = {"fp32": 0, "bf16": D2_COST_BF16, "bf16x3": D2_COST_BF16X3, "bf16x6": D2_COST_BF16X6}
@@ -263,7 +264,7 @@ def _cost_flag(precision):
 
 def badmm_opts(rho0=2.0, iters=100, tau=10, eps=1e-16, rule="R1", fix_x=False, fix_w=False,
                validate=False, rho=0.0, graph=True, elkan=False, cost="fp32", autotune=False,
-               assign_bounded=False, split_streams=False, recalibrate=False, cost_rows=False):
+               assign_bounded=False, split_streams=False, recalibrate=False, cost_rows=False, support_tc=False):
     """d2_badmm_opts; cost = "fp32" | "bf16" | "bf16x3" | "bf16x6" selects the cost build."""
     o = _Opts()
     lib().d2_badmm_opts_default(ctypes.byref(o))
@@ -273,7 +274,7 @@ def badmm_opts(rho0=2.0, iters=100, tau=10, eps=1e-16, rule="R1", fix_x=False, f
                | (0 if graph else D2_NO_GRAPH) | (D2_ELKAN if elkan else 0) | _cost_flag(cost)
                | (D2_AUTOTUNE if autotune else 0) | (D2_ASSIGN_BOUNDED if assign_bounded else 0)
                | (D2_SPLIT_STREAMS if split_streams else 0) | (D2_PRUNE_RECALIBRATE if recalibrate else 0)
-               | (D2_COST_ROWS if cost_rows else 0))
+               | (D2_COST_ROWS if cost_rows else 0) | (D2_SUPPORT_TC if support_tc else 0))
     return o
 
 

@@ -130,13 +130,14 @@ __device__ __forceinline__ void df_add_prod(float& hi, float& lo, float a, float
 // a fixed order: thread (g, i) sums the members p0 + g, p0 + g + G, ... of
 // column i in double-float (every term added exactly up to ~2^-48 of the
 // sum), the G groups are then added in order in FP64, then the m columns.
-__global__ void __launch_bounds__(256) k_consensus(const int64_t* cofs, const float* pos_part, int m, bool r2,
-                                                   float* w_next, double* w_next64) {
-    __shared__ double s_acc[256 + 257];
+#define CONS_THREADS 1024
+__global__ void __launch_bounds__(CONS_THREADS) k_consensus(const int64_t* cofs, const float* pos_part, int m,
+                                                            bool r2, float* w_next, double* w_next64) {
+    __shared__ double s_acc[CONS_THREADS + 257];
     const int c = blockIdx.x;
     const int64_t p0 = cofs[c], p1 = cofs[c + 1];
     if (p1 == p0) return;  // empty cluster: weights unchanged
-    const int G = 256 / m;
+    const int G = CONS_THREADS / m;
     const int t = threadIdx.x;
     const int i = t % m, g = t / m;
     if (g < G) {
@@ -157,17 +158,17 @@ __global__ void __launch_bounds__(256) k_consensus(const int64_t* cofs, const fl
     if (t < m) {
         double sv = 0.0;
         for (int h = 0; h < G; ++h) sv += s_acc[h * m + t];
-        s_acc[256 + t] = r2 ? sv * sv : sv;
+        s_acc[CONS_THREADS + t] = r2 ? sv * sv : sv;
     }
     __syncthreads();
     if (t == 0) {
         double tot = 0.0;
-        for (int h = 0; h < m; ++h) tot += s_acc[256 + h];
-        s_acc[256 + 256] = tot;
+        for (int h = 0; h < m; ++h) tot += s_acc[CONS_THREADS + h];
+        s_acc[CONS_THREADS + 256] = tot;
     }
     __syncthreads();
     if (t < m) {
-        const double wv = s_acc[256 + t] / s_acc[256 + 256];
+        const double wv = s_acc[CONS_THREADS + t] / s_acc[CONS_THREADS + 256];
         w_next64[(int64_t)c * m + t] = wv;
         w_next[(int64_t)c * m + t] = (float)wv;
     }
@@ -1024,8 +1025,11 @@ __global__ void __launch_bounds__(128) k_xpartial_pipe(const int64_t* members, c
     }
 }
 
+// x_i = (mu_c if the partials are of centred coordinates) + sum of the chunk
+// partials / (N_c w_i), the chunks added in order; a point of zero mass keeps
+// its position
 __global__ void k_xfinal(int m, int d, const int64_t* cofs, const int64_t* chunk_first, const float* xpart,
-                         const float* w, float* x) {
+                         const float* w, const float* mu, float* x) {
     const int c = blockIdx.x;
     const int64_t Nc = cofs[c + 1] - cofs[c];
     if (Nc == 0) return;
@@ -1035,7 +1039,7 @@ __global__ void k_xfinal(int m, int d, const int64_t* cofs, const int64_t* chunk
         float s = 0.f;
         for (int64_t q = q0; q < q1; ++q) s += xpart[q * (int64_t)m * d + idx];
         const float mass = (float)Nc * w[(int64_t)c * m + i];
-        if (mass > 0.f) x[(int64_t)c * m * d + idx] = s / mass;
+        if (mass > 0.f) x[(int64_t)c * m * d + idx] = mu ? mu[(int64_t)c * d + (idx - i * d)] + s / mass : s / mass;
     }
 }
 
@@ -1259,6 +1263,11 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
     rc = d2_cluster_ws(ctx, K, m, d, P, &cw);
     if (rc) return rc;
     if ((rc = d2_cost_prepare(ctx, bags, m, cost_prec))) return rc;
+    // the support update on the tensor cores only when asked for: measured
+    // slower than the FP32 CUDA-core partials (its transposing BF16-piece
+    // conversion issues more instructions per row than the FMAs it replaces)
+    const bool xp_tc = !fix_x && (opts.flags & D2_SUPPORT_TC) && d2_support_tc_applies(bags, m, cost_prec);
+    if (xp_tc && (rc = d2_support_tc_prepare(ctx, bags, m, cost_prec))) return rc;
     int32_t* pos_cluster = static_cast<int32_t*>(vpc);
     double* chunk_sum = need_sums ? static_cast<double*>(vcs) : nullptr;
     int64_t* chunk_rows = need_sums ? reinterpret_cast<int64_t*>(static_cast<char*>(vcs) + (size_t)maxch * 8) : nullptr;
@@ -1369,7 +1378,7 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
         D2_LAUNCH_CK(ctx, "k_sweep");
         if ((flags & SW_A) && s.w_next) {
             d2_time_begin(ctx, D2_KT_OTHER, st);
-            k_consensus<<<K, 256, 0, st>>>(cluster_offsets, sa.pos_part, m, rflag != 0, s.w_next, cw.w64);
+            k_consensus<<<K, CONS_THREADS, 0, st>>>(cluster_offsets, sa.pos_part, m, rflag != 0, s.w_next, cw.w64);
             d2_time_end(ctx, st);
             D2_LAUNCH_CK(ctx, "k_consensus");
         }
@@ -1390,7 +1399,11 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
             // Eq. (updatex) with Pi2^n and w^n, then the new cost
             dim3 g((unsigned)maxch, (unsigned)d2_ceil_div(d, XU_DT), (unsigned)d2_ceil_div(m, XU_MT));
             d2_time_begin(ctx, D2_KT_SUPPORT, st);
-            if (xp_pipe) {
+            if (xp_tc) {
+                if ((rc = d2_support_tc(ctx, bags, members, maxch, m, cost_prec, plan, cw, static_cast<float*>(vxp),
+                                        st)))
+                    return rc;
+            } else if (xp_pipe) {
                 dim3 g2((unsigned)maxch, (unsigned)d2_ceil_div(d, 64), (unsigned)d2_ceil_div(m, 32));
                 k_xpartial_pipe<<<g2, 128, 0, st>>>(members, bags->offsets, bags->supp, bags->vocab_idx, bags->vocab,
                                                     d, m, plan, cw.chunks, cw.nchunks, static_cast<float*>(vxp));
@@ -1401,7 +1414,7 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
             }
             D2_LAUNCH_CK(ctx, "k_xpartial");
             k_xfinal<<<K, 256, 0, st>>>(m, d, cluster_offsets, cw.chunk_first, static_cast<float*>(vxp),
-                                        wbuf(it), x);
+                                        wbuf(it), xp_tc ? cw.mu : nullptr, x);
             d2_time_end(ctx, st);
             D2_LAUNCH_CK(ctx, "k_xfinal");
             if ((rc = d2_prep_x(ctx, x, K, m, d, cw, st))) return rc;

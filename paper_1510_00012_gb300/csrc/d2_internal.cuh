@@ -222,6 +222,14 @@ int d2_cost_tc_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64
                     const ClusterWs& cw, float* C, double* chunk_sum, int64_t* chunk_rows, cudaStream_t st,
                     bool* used);
 
+// Tensor-core support partials (support_tc.cu): applies with a tensor-core
+// cost precision, d >= 32 and m <= 128; partial sums of the centred support
+// per chunk into xpart (chunk x m x d).
+bool d2_support_tc_applies(const d2_bags* b, int m, int prec);
+int d2_support_tc_prepare(d2_ctx* ctx, const d2_bags* b, int m, int prec);
+int d2_support_tc(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t maxch, int m, int prec,
+                  const float* plan, const ClusterWs& cw, float* xpart, cudaStream_t st);
+
 // Builds the chunk table of a cluster-offsets array (no position map).
 int d2_build_chunks(d2_ctx* ctx, const int64_t* cofs, int K, const ClusterWs& cw, cudaStream_t st);
 

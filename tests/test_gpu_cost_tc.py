@@ -217,3 +217,31 @@ def test_badmm_tensor_core_cost_shapes(d2, ctx, d, m):
     gx, gw, gplan, gobj = run_gpu_badmm(d2, ctx, bags, co, mem, x0, w0, iters=21, tau=10, cost="bf16x3")
     assert ctx.device_errors() == 0
     _check_badmm(bags, co, mem, x0, w0, gx, gw, gplan, gobj, "bf16x3", 21, 10)
+
+
+@pytest.mark.parametrize("case", ["d64_m32_x3", "d300_m64_vocab_x3", "d124_m20_x3", "d32_m64_x6", "d64_m32_bf16"])
+def test_badmm_tensor_core_support_update(d2, ctx, case):
+    """The opt-in tensor-core support update (Eq. updatex as tcgen05 MMAs on
+    split-BF16 pieces of the centred support and the plan): plans, w, the
+    objective and x against the FP64 oracle with the tolerances of the
+    split-BF16 cost build; several row tiles per chunk, support dimensions in
+    several 64-wide blocks with a ragged last block (d = 124, 300), N padded
+    to 16 (m = 20), three pieces (x6), and single-product BF16 costs (the
+    support update then still uses two pieces)."""
+    prec = {"d64_m32_x3": "bf16x3", "d300_m64_vocab_x3": "bf16x3", "d124_m20_x3": "bf16x3",
+            "d32_m64_x6": "bf16x6", "d64_m32_bf16": "bf16"}[case]
+    if case == "d300_m64_vocab_x3":
+        bags = synth.document_bags(47, 80, V=500, d=300, mk=(10, 60))
+        K, m = 3, 64
+        co, mem = split_clusters(torch.arange(bags.N) % K, K)
+    else:
+        d, m = {"d64_m32_x3": (64, 32), "d124_m20_x3": (124, 20), "d32_m64_x6": (32, 64),
+                "d64_m32_bf16": (64, 32)}[case]
+        K = 4
+        bags = synth.gaussian_class_bags(48 + d + m, 140, d, K, mk=(1, 64), mu_sigma=3.0)
+        co, mem = split_clusters(bags.labels, K)
+    x0, w0 = synth.sample_initial_barycenters(49, bags, co, mem, m)
+    gx, gw, gplan, gobj = run_gpu_badmm(d2, ctx, bags, co, mem, x0, w0, iters=31, tau=10, cost=prec,
+                                        support_tc=True)
+    assert ctx.device_errors() == 0
+    _check_badmm(bags, co, mem, x0, w0, gx, gw, gplan, gobj, prec, 31, 10)
