@@ -430,6 +430,17 @@ def pruning_at_scale(d2, ctx, dev, seed, steps=1500):
     # candidates followed by the certified bounds (exact)
     pr.set_margin(r, 1e30)
     (lm, _, stm), t_mean = timed(lambda: d2.d2_assign(ctx, dsub, x, w, prune=pr, want_stats=True))
+    # candidate counts: the exact solves per bag are what a pruned assignment costs
+    r_sweep = {}
+    for rr in (1, 2, 4, 8):
+        pr.set_margin(rr, delta)
+        d2.d2_assign(ctx, dsub, x, w, prune=pr)
+        (lr_, _, str_), t_r = timed(lambda: d2.d2_assign(ctx, dsub, x, w, prune=pr, want_stats=True))
+        (lrb, _, strb), t_rb = timed(lambda: d2.d2_assign(ctx, dsub, x, w, prune=pr, want_stats=True, bounded=True))
+        r_sweep[str(rr)] = {"s": t_r, "exact_solves": str_["exact_solves"], "fallbacks": str_["fallbacks"],
+                            "misassignment_vs_exact": float((lr_ != le).float().mean()),
+                            "then_certified_bounds_s": t_rb, "then_certified_bounds_solves": strb["exact_solves"],
+                            "then_certified_bounds_misassignment": float((lrb != le).float().mean())}
     pr.set_margin(r, delta)
     (lb, _, stb), t_bnd = timed(lambda: d2.d2_assign(ctx, dsub, x, w, want_stats=True, bounded=True))
     (lbp, _, stbp), t_bndp = timed(lambda: d2.d2_assign(ctx, dsub, x, w, prune=pr, want_stats=True, bounded=True))
@@ -443,7 +454,10 @@ def pruning_at_scale(d2, ctx, dev, seed, steps=1500):
         "elkan": "applies across rounds only (its bounds come from the previous round's centroids); "
                  "compared in d2_round",
         "learned_speedup_vs_certified_bounds": t_bnd / t_pruned,
-        "learned_speedup_vs_mean_term_only": t_mean / t_pruned}
+        "learned_speedup_vs_mean_term_only": t_mean / t_pruned,
+        "learned_r_sweep": r_sweep,
+        "best_learned_s": min(v["s"] for v in r_sweep.values()),
+        "best_learned_speedup_vs_certified_bounds": t_bnd / min(v["s"] for v in r_sweep.values())}
     out.update({"train_pairs": npairs, "target_w2_s": t_tg, "train_steps": steps, "train_s": t_train,
                 "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:])),
                 "r": r, "delta": delta, "eval_bags": ev,

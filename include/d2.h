@@ -117,8 +117,12 @@ extern "C" {
 typedef struct d2_ctx d2_ctx;
 
 /* A set of N discrete distributions (Section 2).  Supports are either dense
- * (`supp`, n x d) or indices into a shared table (`vocab_idx` into `vocab`,
- * V x d): the grid/symbolic storage of Section 5. */
+ * (`supp`, n x d), or indices into a shared table of points (`vocab_idx`
+ * into `vocab`, V x d: the grid storage of Section 5), or symbols of a
+ * symbolic set with a given symbol-to-symbol dissimilarity (`vocab_idx`
+ * holds symbol ids in [0, V), `symcost` the V x V dissimilarities; supp and
+ * vocab NULL, d = 1): the symbolic data of Sections 2 and 5, used only by the
+ * *_sym entry points (the others return D2_EINVAL for them). */
 typedef struct {
     int64_t        N;          /* number of distributions                         */
     int64_t        n;          /* total support rows = offsets[N] (host copy)     */
@@ -130,6 +134,7 @@ typedef struct {
     const float*   vocab;      /* device, V x d row-major, or NULL                */
     int64_t        V;          /* vocabulary rows                                 */
     const float*   wt;         /* device, n; each bag's weights >= 0, sum 1       */
+    const float*   symcost;    /* device, V x V row-major, or NULL (see above)    */
 } d2_bags;
 
 /* Options of Algorithm badmm (Section 3.3). */
@@ -423,6 +428,50 @@ int d2_w2_pairs(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,
 #define D2_NOALLOC_MAX_PAIRS (1 << 20)
 int d2_assign_noalloc(const d2_bags* bags, int32_t K, int32_t m, const float* x, const float* w,
                       int32_t* labels, float* dist, void* stream);
+
+/* ---- symbolic supports (Sections 2 and 5) ---------------------------------
+ * Distributions over a symbolic set with a given symbol-to-symbol
+ * dissimilarity c(s, t) = symcost[s V + t] (any nonnegative values; squared
+ * distances for D2-clustering).  The centroids' supports are symbols too and
+ * never move ("the step of updating the support vectors can be skipped since
+ * the set of symbols is fixed", Section 5): a centroid is m symbols
+ * csym[c m .. c m + m - 1] and their weights. */
+
+/* Cost matrices C_k[j, i] = c(csym_c,i, symbol of row j) of every listed
+ * member, j-major like d2_cost (cluster_offsets, members, P, K, m as there;
+ * csym: device, K x m symbol ids in [0, V)). */
+int d2_sym_cost(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_offsets, const int64_t* members,
+                int64_t P, int32_t K, int32_t m, const int32_t* csym, float* C_out, void* stream);
+
+/* Algorithm badmm (Section 3.3) with fixed symbolic supports: the plans and
+ * the weights w (device, K x m, in/out) of every cluster, the costs taken
+ * from the table, rho by Eq. (rho), Eq. (updatex) skipped.  Other arguments
+ * and results as for badmm_barycenter (D2_FIX_X is implied; D2_SPLIT_STREAMS
+ * and the cost precision flags are ignored). */
+int badmm_barycenter_sym(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_offsets,
+                         const int64_t* members, int64_t P, int32_t K, int32_t m, const int32_t* csym,
+                         float* w, float* plan, const uint8_t* warm_mask, const d2_badmm_opts* opts,
+                         double* obj, void* stream);
+
+/* Assignment step of Algorithm 1 with symbolic supports: labels[k] =
+ * argmin_i W^2(Q_i, P^(k)) by the exact solver of d2_assign on the table's
+ * costs (ties -> lowest i); stats and D2_ENOCONV as for d2_assign. */
+int d2_assign_sym(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, const int32_t* csym,
+                  const float* w, int32_t* labels, float* dist, int64_t* stats, void* stream);
+
+/* D2-clustering (Algorithm 1) of symbolic distributions, every centroid
+ * supported on the same m symbols sym (device, m ids).  Initialisation: K
+ * distinct bags drawn by a partial Fisher-Yates shuffle of all bag ids driven
+ * by SplitMix64(seed); centroid c's weight on sym_i is the mass of the c-th
+ * bag's symbols whose nearest centroid symbol (smallest c(sym_i, t), first
+ * minimum) is sym_i.  Rounds as in d2_cluster: exact assignment, then
+ * badmm_barycenter_sym over all K clusters with the plans of unchanged
+ * members warm-started (Section 5).  w_out: device K x m; labels_out: device
+ * N; obj_per_round: host, rounds doubles.  Synchronous; D2_ENOCONV as for
+ * d2_cluster. */
+int d2_cluster_sym(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, const int32_t* sym, uint64_t seed,
+                   int32_t rounds, const d2_badmm_opts* opts, float* w_out, int32_t* labels_out,
+                   double* obj_per_round, void* stream);
 
 /* Greedy merge of Eq. (merge) (Section 5): reduce bag ids[c] to m support
  * points for c = 0..cnt-1 -> x (device cnt x m x d), w (device cnt x m).

@@ -49,7 +49,7 @@ def consensus_weights(wtil, rule):
 
 
 def badmm_barycenter(members, x0, w0, *, rho0=2.0, T=100, tau=10, eps=1e-16, rule="R1",
-                     plan0=None, warm=None, fix_w=False, fix_x=False, rho=None):
+                     plan0=None, warm=None, fix_w=False, fix_x=False, rho=None, costs=None):
     """Run T iterations of Algorithm badmm on one cluster.
 
     members : list of (y_k (m_k, d), w_k (m_k,)) -- the cluster's distributions P^(k)
@@ -61,16 +61,25 @@ def badmm_barycenter(members, x0, w0, *, rho0=2.0, T=100, tau=10, eps=1e-16, rul
               and w^(k); used as a test mode)
     fix_x   : never move the support (pre-fixed support track of Section 4)
     rho     : override rho (else Eq. rho with the reading above)
+    costs   : optional list of the members' cost matrices C_k (m x m_k), given
+              instead of computed from coordinates: symbolic supports with a
+              given symbol-to-symbol dissimilarity (Section 5), whose support
+              is fixed; members' y and x0 are then unused (x0 may be None)
     Returns dict(x, w, P1, P2, Lam, obj, rho).
     """
     N = len(members)
-    x = np.array(x0, dtype=np.float64, copy=True)
     w = np.array(w0, dtype=np.float64, copy=True)
-    m = x.shape[0]
-    Y = [np.asarray(y, dtype=np.float64) for y, _ in members]
+    m = w.shape[0]
     Wk = [np.asarray(wk, dtype=np.float64) for _, wk in members]
-
-    C = [cost_matrix(x, Y[k]) for k in range(N)]
+    if costs is not None:
+        fix_x = True
+        x = None if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+        C = [np.asarray(Ck, dtype=np.float64) for Ck in costs]
+        Y = [np.zeros((Ck.shape[1], 0)) for Ck in C]
+    else:
+        x = np.array(x0, dtype=np.float64, copy=True)
+        Y = [np.asarray(y, dtype=np.float64) for y, _ in members]
+        C = [cost_matrix(x, Y[k]) for k in range(N)]
     if rho is None:
         # Eq. rho: rho0 times the average transport cost over all m*m_k entries
         total = sum(float(Ck.sum()) for Ck in C)

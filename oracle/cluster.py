@@ -82,24 +82,20 @@ def d2_assign(bags_list, cents):
     return labels, D[np.arange(N), labels], D
 
 
-def d2_cluster(bags_list, K, m, seed, rounds, *, rho0=2.0, T=100, tau=10, eps=1e-16,
-               rule="R1", labels_in=None):
-    """Algorithm 1 with the Section 5 choices.
-
-    labels_in: optional list of per-round label arrays; when given, round r uses
-    labels_in[r] instead of its own assignment (teacher forcing, so a single
-    near-tie flip does not make later rounds incomparable).
-    Returns dict(x (K,m,d), w (K,m), labels, obj_per_round, dists).
-    """
-    sizes = [y.shape[0] for y, _ in bags_list]
-    picks = init_pick(sizes, K, m, seed)
-    cents = [pad_support(*merge_reduce(bags_list[k][0], bags_list[k][1], m), m) for k in picks]
-    N = len(bags_list)
+def cluster_rounds(N, cents, rounds, assign, update, labels_in=None):
+    """The rounds of Algorithm 1 with the Section 5 warm start, for any kind of
+    centroid: assign(cents) -> (labels, dists); update(i, ids, cent, plan0,
+    warm) -> (new centroid, that call's Pi^(k,2) list).  A member starts from
+    its cached Pi^(k,2) exactly when its label equals its label at the
+    previous round's assignment; an empty cluster keeps its centroid.
+    labels_in: optional per-round labels used instead of the assignment
+    (teacher forcing).  Returns (cents, labels, objs, labels_per_round)."""
+    K = len(cents)
     prev_labels = None
     cache = [None] * N
     objs, all_labels = [], []
     for r in range(rounds):
-        labels, dists, _ = d2_assign(bags_list, cents)
+        labels, dists = assign(cents)
         objs.append(float(np.mean(dists)))
         if labels_in is not None:
             labels = np.asarray(labels_in[r])
@@ -112,14 +108,38 @@ def d2_cluster(bags_list, K, m, seed, rounds, *, rho0=2.0, T=100, tau=10, eps=1e
                 continue
             warm = [prev_labels is not None and prev_labels[k] == i and cache[k] is not None
                     for k in ids]
-            res = badmm_barycenter([bags_list[k] for k in ids], cents[i][0], cents[i][1],
-                                   rho0=rho0, T=T, tau=tau, eps=eps, rule=rule,
-                                   plan0=[cache[k] for k in ids], warm=warm)
+            cent, P2 = update(i, ids, cents[i], [cache[k] for k in ids], warm)
             for t, k in enumerate(ids):
-                cache[k] = res["P2"][t]
-            new_cents.append((res["x"], res["w"]))
+                cache[k] = P2[t]
+            new_cents.append(cent)
         cents = new_cents
         prev_labels = labels
+    return cents, prev_labels, objs, all_labels
+
+
+def d2_cluster(bags_list, K, m, seed, rounds, *, rho0=2.0, T=100, tau=10, eps=1e-16,
+               rule="R1", labels_in=None):
+    """Algorithm 1 with the Section 5 choices.
+
+    labels_in: optional list of per-round label arrays; when given, round r uses
+    labels_in[r] instead of its own assignment (teacher forcing, so a single
+    near-tie flip does not make later rounds incomparable).
+    Returns dict(x (K,m,d), w (K,m), labels, obj_per_round, dists).
+    """
+    sizes = [y.shape[0] for y, _ in bags_list]
+    picks = init_pick(sizes, K, m, seed)
+    cents = [pad_support(*merge_reduce(bags_list[k][0], bags_list[k][1], m), m) for k in picks]
+
+    def assign(cs):
+        labels, dists, _ = d2_assign(bags_list, cs)
+        return labels, dists
+
+    def update(i, ids, cent, plan0, warm):
+        res = badmm_barycenter([bags_list[k] for k in ids], cent[0], cent[1], rho0=rho0, T=T, tau=tau,
+                               eps=eps, rule=rule, plan0=plan0, warm=warm)
+        return (res["x"], res["w"]), res["P2"]
+
+    cents, labels, objs, all_labels = cluster_rounds(len(bags_list), cents, rounds, assign, update, labels_in)
     return dict(x=np.array([c[0] for c in cents]), w=np.array([c[1] for c in cents]),
-                labels=prev_labels, obj_per_round=objs, labels_per_round=all_labels,
+                labels=labels, obj_per_round=objs, labels_per_round=all_labels,
                 picks=picks)

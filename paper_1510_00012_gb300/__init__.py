@@ -45,7 +45,7 @@ class D2Error(RuntimeError):
 class _Bags(ctypes.Structure):
     _fields_ = [("N", c_int64), ("n", c_int64), ("d", c_int32), ("max_mk", c_int32),
                 ("offsets", c_void_p), ("supp", c_void_p), ("vocab_idx", c_void_p),
-                ("vocab", c_void_p), ("V", c_int64), ("wt", c_void_p)]
+                ("vocab", c_void_p), ("V", c_int64), ("wt", c_void_p), ("symcost", c_void_p)]
 
 
 class _Opts(ctypes.Structure):
@@ -79,6 +79,14 @@ _SIGS = {
     "d2_assign_noalloc": (c_int, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "d2_w2_pairs": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                             c_int64, c_void_p, c_void_p]),
+    "d2_sym_cost": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_void_p,
+                            c_void_p, c_void_p]),
+    "badmm_barycenter_sym": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32,
+                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "d2_assign_sym": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                              c_void_p, c_void_p]),
+    "d2_cluster_sym": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_uint64, c_int32, c_void_p,
+                               c_void_p, c_void_p, c_void_p, c_void_p]),
     "d2_merge_init": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p,
                               c_void_p]),
     "d2_cluster": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_uint64, c_int32, c_void_p,
@@ -229,28 +237,31 @@ class Context:
 class DeviceBags:
     """Device-resident bag set in the layout of d2_bags (see include/d2.h)."""
 
-    def __init__(self, offsets, wt, d, supp=None, vocab_idx=None, vocab=None, max_mk=None):
+    def __init__(self, offsets, wt, d, supp=None, vocab_idx=None, vocab=None, max_mk=None, symcost=None):
+        """Coordinates (supp, or vocab_idx into vocab) or symbols (vocab_idx
+        into the V x V dissimilarity table symcost, d = 1)."""
         self.offsets = _need(offsets, torch.int64, "offsets")
         self.wt = _need(wt, torch.float32, "wt")
         self.supp = None if supp is None else _need(supp, torch.float32, "supp")
         self.vocab_idx = None if vocab_idx is None else _need(vocab_idx, torch.int32, "vocab_idx")
         self.vocab = None if vocab is None else _need(vocab, torch.float32, "vocab")
+        self.symcost = None if symcost is None else _need(symcost, torch.float32, "symcost")
         self.d = int(d)
         self.N = offsets.numel() - 1
         self.n = wt.numel()
         if max_mk is None:
             max_mk = int((offsets[1:] - offsets[:-1]).max().item()) if self.N > 0 else 1
         self.max_mk = int(max_mk)
-        self.V = 0 if vocab is None else vocab.shape[0]
+        self.V = vocab.shape[0] if vocab is not None else (symcost.shape[0] if symcost is not None else 0)
         self.c = _Bags(self.N, self.n, self.d, self.max_mk, _ptr(self.offsets), _ptr(self.supp),
-                       _ptr(self.vocab_idx), _ptr(self.vocab), self.V, _ptr(self.wt))
+                       _ptr(self.vocab_idx), _ptr(self.vocab), self.V, _ptr(self.wt), _ptr(self.symcost))
 
     @classmethod
     def from_synth(cls, b, device="cuda"):
         mv = lambda t, dt: None if t is None else t.to(device=device, dtype=dt).contiguous()
         return cls(mv(b.offsets, torch.int64), mv(b.wt, torch.float32), b.d,
                    supp=mv(b.supp, torch.float32), vocab_idx=mv(b.vocab_idx, torch.int32),
-                   vocab=mv(b.vocab, torch.float32))
+                   vocab=mv(b.vocab, torch.float32), symcost=mv(getattr(b, "symcost", None), torch.float32))
 
     def ref(self):
         return ctypes.byref(self.c)
@@ -322,6 +333,74 @@ def badmm_barycenter(ctx, bags, cluster_offsets, members, x, w, plan=None, warm_
                                      members.numel(), K, m, _ptr(x), _ptr(w), _ptr(plan),
                                      _ptr(warm_mask), ctypes.byref(opts), _ptr(obj), _stream()))
     return x, w, plan, obj
+
+
+def d2_sym_cost(ctx, bags, cluster_offsets, members, csym, C_out=None):
+    """Symbolic bags: C (n x m, j-major rows) from the table for each cluster's symbols csym (K, m) int32."""
+    _need(cluster_offsets, torch.int64, "cluster_offsets")
+    _need(members, torch.int64, "members")
+    _need(csym, torch.int32, "csym")
+    K, m = csym.shape[0], csym.shape[1]
+    if C_out is None:
+        C_out = torch.zeros(bags.n, m, dtype=torch.float32, device=csym.device)
+    _need(C_out, torch.float32, "C_out")
+    ctx.check(lib().d2_sym_cost(ctx.h, bags.ref(), _ptr(cluster_offsets), _ptr(members), members.numel(), K, m,
+                                _ptr(csym), _ptr(C_out), _stream()))
+    return C_out
+
+
+def badmm_barycenter_sym(ctx, bags, cluster_offsets, members, csym, w, plan=None, warm_mask=None, opts=None,
+                         obj=None):
+    """Algorithm badmm with fixed symbolic supports csym (K, m) int32; updates w (K, m) and plan (n, m)."""
+    _need(cluster_offsets, torch.int64, "cluster_offsets")
+    _need(members, torch.int64, "members")
+    _need(csym, torch.int32, "csym")
+    _need(w, torch.float32, "w")
+    K, m = csym.shape[0], csym.shape[1]
+    if plan is None:
+        plan = torch.empty(bags.n, m, dtype=torch.float32, device=w.device)
+    _need(plan, torch.float32, "plan")
+    if warm_mask is not None:
+        _need(warm_mask, torch.uint8, "warm_mask")
+    if obj is None:
+        obj = torch.empty(K, dtype=torch.float64, device=w.device)
+    if opts is None:
+        opts = badmm_opts()
+    ctx.check(lib().badmm_barycenter_sym(ctx.h, bags.ref(), _ptr(cluster_offsets), _ptr(members), members.numel(),
+                                         K, m, _ptr(csym), _ptr(w), _ptr(plan), _ptr(warm_mask), ctypes.byref(opts),
+                                         _ptr(obj), _stream()))
+    return w, plan, obj
+
+
+def d2_assign_sym(ctx, bags, csym, w, want_stats=False):
+    """Exact assignment of symbolic bags to centroids (csym (K, m) int32, w (K, m))."""
+    _need(csym, torch.int32, "csym")
+    _need(w, torch.float32, "w")
+    K, m = csym.shape[0], csym.shape[1]
+    labels = torch.empty(bags.N, dtype=torch.int32, device=w.device)
+    dist = torch.empty(bags.N, dtype=torch.float32, device=w.device)
+    st = (c_int64 * 3)() if want_stats else None
+    ctx.check(lib().d2_assign_sym(ctx.h, bags.ref(), K, m, _ptr(csym), _ptr(w), _ptr(labels), _ptr(dist), st,
+                                  _stream()))
+    if want_stats:
+        return labels, dist, dict(exact_solves=st[0], fallbacks=st[1], limit_hits=st[2])
+    return labels, dist
+
+
+def d2_cluster_sym(ctx, bags, K, sym, seed, rounds, opts=None):
+    """Algorithm 1 on symbolic bags, every centroid on the symbols sym (m,) int32
+    -> (w (K, m), labels (N), obj_per_round list)."""
+    _need(sym, torch.int32, "sym")
+    m = sym.numel()
+    dev = bags.offsets.device
+    w = torch.empty(K, m, dtype=torch.float32, device=dev)
+    labels = torch.empty(bags.N, dtype=torch.int32, device=dev)
+    objs = (c_double * rounds)()
+    if opts is None:
+        opts = badmm_opts()
+    ctx.check(lib().d2_cluster_sym(ctx.h, bags.ref(), K, m, _ptr(sym), c_uint64(seed), rounds, ctypes.byref(opts),
+                                   _ptr(w), _ptr(labels), objs, _stream()))
+    return w, labels, list(objs)
 
 
 def d2_merge_init(ctx, bags, ids, m):

@@ -222,6 +222,7 @@ int d2_ws(d2_ctx* ctx, int slot, size_t bytes, void** out) {
 
 int d2_check_bags_host(d2_ctx* ctx, const d2_bags* b) {
     if (!b) return d2_fail(ctx, D2_EINVAL, "bags is NULL");
+    if (b->symcost) return d2_fail(ctx, D2_EINVAL, "bags: symbolic bags need the *_sym entry points");
     if (b->N < 1 || b->n < 1 || b->d < 1 || b->max_mk < 1)
         return d2_fail(ctx, D2_EINVAL, "bags: need N, n, d, max_mk >= 1 (got %lld, %lld, %d, %d)",
                        (long long)b->N, (long long)b->n, b->d, b->max_mk);
@@ -231,6 +232,16 @@ int d2_check_bags_host(d2_ctx* ctx, const d2_bags* b) {
     if (dense == voc) return d2_fail(ctx, D2_EINVAL, "bags: give exactly one of supp or (vocab_idx, vocab, V)");
     if (dense && (reinterpret_cast<uintptr_t>(b->supp) & 15))
         return d2_fail(ctx, D2_EINVAL, "bags: supp must be 16-byte aligned");
+    return D2_OK;
+}
+
+int d2_check_sym_bags_host(d2_ctx* ctx, const d2_bags* b) {
+    if (!b) return d2_fail(ctx, D2_EINVAL, "bags is NULL");
+    if (b->N < 1 || b->n < 1 || b->max_mk < 1 || b->V < 1)
+        return d2_fail(ctx, D2_EINVAL, "symbolic bags: need N, n, max_mk, V >= 1");
+    if (!b->offsets || !b->wt || !b->vocab_idx || !b->symcost)
+        return d2_fail(ctx, D2_EINVAL, "symbolic bags: offsets, wt, vocab_idx (symbols) and symcost are required");
+    if (b->supp || b->vocab) return d2_fail(ctx, D2_EINVAL, "symbolic bags: supp and vocab must be NULL");
     return D2_OK;
 }
 
@@ -266,7 +277,7 @@ __global__ void k_check_bags(d2_bags b, int* flags) {
 
 extern "C" int d2_check_bags(d2_ctx* ctx, const d2_bags* bags, void* stream) {
     if (!ctx) return D2_EINVAL;
-    int rc = d2_check_bags_host(ctx, bags);
+    int rc = (bags && bags->symcost) ? d2_check_sym_bags_host(ctx, bags) : d2_check_bags_host(ctx, bags);
     if (rc) return rc;
     cudaStream_t st = d2_stream(stream);
     D2_CK(ctx, cudaMemsetAsync(ctx->dev_flags, 0, sizeof(int), st));

@@ -47,8 +47,12 @@ struct AssignArgs {
     const float* vocab;
     const float* wt;
     int d;
-    const float* x;    // K x m x d
+    const float* x;    // K x m x d (NULL for symbolic supports)
     const float* w;    // K x m
+    // symbolic supports (Section 5): cost C_ij = symcost[csym[cent m + i] * V + vidx[row j]]
+    const float* symcost;      // V x V, or NULL
+    const int32_t* csym;       // K x m centroid symbols
+    int64_t V;
     int m, K, nmax;
     int nlo;                   // this launch solves only bags with nlo < m_k <= nmax
     // pair enumeration
@@ -223,12 +227,19 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
     const int64_t r0 = a.offsets[bag];
     const int n = (int)(a.offsets[bag + 1] - r0);
     const int V = m + n;
-    const float* xc = a.x + (int64_t)cent * m * d;
+    const float* xc = a.x ? a.x + (int64_t)cent * m * d : nullptr;
 
-    // ---- cost C[i][j] = sum_dd (x_i - y_j)^2 by direct differences
-    // tableau rows are ns = n | 1 floats apart (odd: a column walk across
-    // rows touches distinct banks)
+    // ---- cost C[i][j] = sum_dd (x_i - y_j)^2 by direct differences, or the
+    // given symbol-to-symbol dissimilarity; tableau rows are ns = n | 1 floats
+    // apart (odd: a column walk across rows touches distinct banks)
     const int ns = n | 1;
+    if (a.symcost) {
+        const int32_t* cs = a.csym + (int64_t)cent * m;
+        for (int e = lane; e < m * ns; e += 32) {
+            const int i = e / ns, j = e - i * ns;
+            s.C[e] = j < n ? a.symcost[(int64_t)cs[i] * a.V + a.vidx[r0 + j]] : 0.f;
+        }
+    } else {
     for (int e = lane; e < m * ns; e += 32) s.C[e] = 0.f;
     for (int d0 = 0; d0 < d; d0 += AS_DC) {
         const int dc = min(AS_DC, d - d0);
@@ -251,6 +262,7 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
             }
             s.C[i * ns + j] = acc;
         }
+    }
     }
     // ---- initial state
     int fbump = 0, ffree = -1;  // sparse pool allocator (lane 0)
@@ -821,6 +833,29 @@ int d2_assign_exact(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x,
     if (rc) return rc;
     float* D = static_cast<float*>(pD);
     AssignArgs a = d2_assign_args(b, K, m, x, w, ctx->dev_flags + D2_DEV_ERR_WORD, counters + 2);
+    a.mode = 0;
+    a.npairs = N * K;
+    a.out = D;
+    if ((rc = d2_launch_pairs(ctx, a, N * K, st))) return rc;
+    k_add_i64<<<1, 1, 0, st>>>(counters, N * K);
+    D2_LAUNCH_CK(ctx, "k_add_i64");
+    return d2_argmin_rows(ctx, D, N, K, labels, dist, st);
+}
+
+// all N x K pairs with symbolic supports (costs from the bags' symbol table),
+// then argmin per bag
+int d2_assign_sym_exact(d2_ctx* ctx, const d2_bags* b, int K, int m, const int32_t* csym, const float* w,
+                        int32_t* labels, float* dist, int64_t* counters, cudaStream_t st) {
+    const int64_t N = b->N;
+    void* pD = nullptr;
+    int rc = d2_ws(ctx, WS_ASSIGN, (size_t)N * K * 4, &pD);
+    if (rc) return rc;
+    float* D = static_cast<float*>(pD);
+    AssignArgs a = d2_assign_args(b, K, m, nullptr, w, ctx->dev_flags + D2_DEV_ERR_WORD, counters + 2);
+    a.d = 1;
+    a.symcost = b->symcost;
+    a.csym = csym;
+    a.V = b->V;
     a.mode = 0;
     a.npairs = N * K;
     a.out = D;

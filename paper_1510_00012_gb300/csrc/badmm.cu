@@ -1206,6 +1206,13 @@ static int badmm_split(d2_ctx* ctx, const d2_bags* bags, const int64_t* cofs, co
 // entry point
 // ---------------------------------------------------------------------------
 
+// Algorithm badmm for coordinate supports (x, csym NULL) or fixed symbolic
+// supports (csym, x NULL: costs from the bags' symbol table, no support
+// update).
+static int badmm_impl(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_offsets, const int64_t* members,
+                      int64_t P, int32_t K, int32_t m, float* x, const int32_t* csym, float* w, float* plan,
+                      const uint8_t* warm_mask, const d2_badmm_opts* opts_in, double* obj, void* stream);
+
 extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_offsets,
                                 const int64_t* members, int64_t P, int32_t K, int32_t m, float* x,
                                 float* w, float* plan, const uint8_t* warm_mask, const d2_badmm_opts* opts_in,
@@ -1213,9 +1220,34 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
     if (!ctx) return D2_EINVAL;
     int rc = d2_check_bags_host(ctx, bags);
     if (rc) return rc;
+    if (!x) return d2_fail(ctx, D2_EINVAL, "badmm_barycenter: x is NULL");
+    return badmm_impl(ctx, bags, cluster_offsets, members, P, K, m, x, nullptr, w, plan, warm_mask, opts_in, obj,
+                      stream);
+}
+
+extern "C" int badmm_barycenter_sym(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_offsets,
+                                    const int64_t* members, int64_t P, int32_t K, int32_t m, const int32_t* csym,
+                                    float* w, float* plan, const uint8_t* warm_mask, const d2_badmm_opts* opts_in,
+                                    double* obj, void* stream) {
+    if (!ctx) return D2_EINVAL;
+    int rc = d2_check_sym_bags_host(ctx, bags);
+    if (rc) return rc;
+    if (!csym) return d2_fail(ctx, D2_EINVAL, "badmm_barycenter_sym: csym is NULL");
+    d2_badmm_opts o;
+    if (opts_in) o = *opts_in; else d2_badmm_opts_default(&o);
+    o.flags |= D2_FIX_X;
+    o.flags &= ~(D2_SPLIT_STREAMS | D2_COST_BF16X6 | D2_SUPPORT_TC | D2_COST_ROWS);
+    return badmm_impl(ctx, bags, cluster_offsets, members, P, K, m, nullptr, csym, w, plan, warm_mask, &o, obj,
+                      stream);
+}
+
+static int badmm_impl(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_offsets, const int64_t* members,
+                      int64_t P, int32_t K, int32_t m, float* x, const int32_t* csym, float* w, float* plan,
+                      const uint8_t* warm_mask, const d2_badmm_opts* opts_in, double* obj, void* stream) {
+    int rc = D2_OK;
     d2_badmm_opts opts;
     if (opts_in) opts = *opts_in; else d2_badmm_opts_default(&opts);
-    if (K < 1 || m < 1 || m > 256 || P < 0 || !cluster_offsets || (P > 0 && !members) || !x || !w || !plan)
+    if (K < 1 || m < 1 || m > 256 || P < 0 || !cluster_offsets || (P > 0 && !members) || !w || !plan)
         return d2_fail(ctx, D2_EINVAL, "badmm_barycenter: need K >= 1, 1 <= m <= 256 and non-NULL arrays");
     if (opts.iters < 1 || opts.tau < 1 || !(opts.eps >= 0.0) || !(opts.rho0 > 0.0) ||
         (opts.rule != D2_RULE_R1 && opts.rule != D2_RULE_R2))
@@ -1234,7 +1266,7 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
         if (rc || done) return rc;
         opts.flags &= ~D2_SPLIT_STREAMS;
     }
-    const int d = bags->d;
+    const int d = csym ? 1 : bags->d;
     const int64_t n = bags->n;
 
     // workspaces
@@ -1256,13 +1288,13 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
     void *vpc = nullptr, *vcs = nullptr;
     if ((rc = d2_ws(ctx, WS_POS_CLUSTER, (size_t)P * 4, &vpc))) return rc;
     if (need_sums && (rc = d2_ws(ctx, WS_CHUNK_SUM, (size_t)maxch * 16, &vcs))) return rc;
-    const int cost_prec = d2_cost_prec(opts.flags);
-    const bool use_vt = d2_vocab_table_applies(bags, K, m, cost_prec, opts.flags);
+    const int cost_prec = csym ? 0 : d2_cost_prec(opts.flags);
+    const bool use_vt = !csym && d2_vocab_table_applies(bags, K, m, cost_prec, opts.flags);
     if (use_vt && (rc = d2_vocab_reserve(ctx, bags, K, m, cw))) return rc;
     // the cluster workspace may have moved while growing the others
     rc = d2_cluster_ws(ctx, K, m, d, P, &cw);
     if (rc) return rc;
-    if ((rc = d2_cost_prepare(ctx, bags, m, cost_prec))) return rc;
+    if (!csym && (rc = d2_cost_prepare(ctx, bags, m, cost_prec))) return rc;
     // the support update on the tensor cores only when asked for: measured
     // slower than the FP32 CUDA-core partials (its transposing BF16-piece
     // conversion issues more instructions per row than the FMAs it replaces)
@@ -1343,10 +1375,14 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
     D2_CK(ctx, cudaMemsetAsync(cw.counters, 0, (size_t)K * 4, st));
     D2_CK(ctx, cudaMemcpyAsync(cw.wb[0], w, (size_t)K * m * 4, cudaMemcpyDeviceToDevice, st));
     // initial cost and rho (Eq. rho)
-    if ((rc = d2_prep_x(ctx, x, K, m, d, cw, st))) return rc;
-    if ((rc = d2_cost_rows(ctx, bags, members, P, K, m, cw, cost, need_sums, cost_prec,
-                           use_vt ? D2_VT_SETUP : D2_VT_OFF, st)))
-        return rc;
+    if (csym) {
+        if ((rc = d2_sym_cost_rows(ctx, bags, members, P, K, m, csym, cw, cost, chunk_sum, chunk_rows, st))) return rc;
+    } else {
+        if ((rc = d2_prep_x(ctx, x, K, m, d, cw, st))) return rc;
+        if ((rc = d2_cost_rows(ctx, bags, members, P, K, m, cw, cost, need_sums, cost_prec,
+                               use_vt ? D2_VT_SETUP : D2_VT_OFF, st)))
+            return rc;
+    }
     k_rho<<<(unsigned)d2_ceil_div(K, 128), 128, 0, st>>>(K, m, cw.chunk_first, chunk_sum, chunk_rows,
                                                         opts.rho0, opts.rho, cw.rho, cw.beta, cw.nrows);
     D2_LAUNCH_CK(ctx, "k_rho");
@@ -1461,7 +1497,8 @@ extern "C" int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t*
     const std::vector<uint64_t> key = {
         (uint64_t)ctx->generation, (uint64_t)bags->N, (uint64_t)bags->n, (uint64_t)bags->d, (uint64_t)bags->max_mk,
         u(bags->offsets), u(bags->supp), u(bags->vocab_idx), u(bags->vocab), (uint64_t)bags->V, u(bags->wt),
-        u(cluster_offsets), u(members), (uint64_t)P, (uint64_t)K, (uint64_t)m, u(x), u(w), u(plan),
+        u(cluster_offsets), u(members), (uint64_t)P, (uint64_t)K, (uint64_t)m, u(x), u(csym), u(bags->symcost),
+        u(w), u(plan),
         u(warm_mask), u(obj), rho_bits, rho0_bits, eps_bits, (uint64_t)opts.iters, (uint64_t)opts.tau,
         (uint64_t)opts.rule, (uint64_t)opts.flags, u(reinterpret_cast<const void*>(sweep)), (uint64_t)per_sm};
     if (ctx->graph_exec && ctx->graph_key == key) {

@@ -437,6 +437,147 @@ extern "C" int d2_cluster(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m
     return D2_OK;
 }
 
+// ---------------------------------------------------------------------------
+// d2_cluster_sym: symbolic supports
+// ---------------------------------------------------------------------------
+
+// Initial centroid weights from the picked bags: the mass of each bag symbol
+// goes to its nearest centroid symbol (smallest dissimilarity, first
+// minimum); one thread per centroid, FP64 sums in row order.
+__global__ void k_sym_project(const int64_t* ids, int K, const int64_t* offsets, const int32_t* bsym,
+                              const float* bw, const float* symcost, int64_t V, const int32_t* sym, int m,
+                              float* w_out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= K) return;
+    const int64_t k = ids[c];
+    float* wc = w_out + (int64_t)c * m;
+    double acc[256];
+    for (int i = 0; i < m; ++i) acc[i] = 0.0;
+    double tot = 0.0;
+    for (int64_t r = offsets[k]; r < offsets[k + 1]; ++r) {
+        const float* col = symcost + bsym[r];  // c(s, t) for t = bsym[r] at col[s * V]
+        int best = 0;
+        float bv = col[(int64_t)sym[0] * V];
+        for (int i = 1; i < m; ++i) {
+            const float v = col[(int64_t)sym[i] * V];
+            if (v < bv) {
+                bv = v;
+                best = i;
+            }
+        }
+        acc[best] += (double)bw[r];
+        tot += (double)bw[r];
+    }
+    for (int i = 0; i < m; ++i) wc[i] = tot > 0.0 ? (float)(acc[i] / tot) : 1.0f / (float)m;
+}
+
+__global__ void k_tile_sym(const int32_t* sym, int K, int m, int32_t* csym) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < (int64_t)K * m) csym[e] = sym[e % m];
+}
+
+extern "C" int d2_cluster_sym(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, const int32_t* sym,
+                              uint64_t seed, int32_t rounds, const d2_badmm_opts* opts, float* w_out,
+                              int32_t* labels_out, double* obj_per_round, void* stream) {
+    if (!ctx) return D2_EINVAL;
+    int rc = d2_check_sym_bags_host(ctx, bags);
+    if (rc) return rc;
+    if (K < 1 || m < 1 || m > 256 || rounds < 1 || !sym || !w_out || !labels_out)
+        return d2_fail(ctx, D2_EINVAL, "d2_cluster_sym: need K >= 1, 1 <= m <= 256, rounds >= 1, non-NULL arrays");
+    const int64_t N = bags->N, n = bags->n;
+    if (K > N) return d2_fail(ctx, D2_EINVAL, "d2_cluster_sym: K = %d exceeds N = %lld", K, (long long)N);
+    cudaStream_t st = d2_stream(stream);
+    // seeded pick: partial Fisher-Yates over all bag ids (no size condition:
+    // a symbolic centroid is not merged from its seed)
+    std::vector<int64_t> elig(N);
+    for (int64_t k = 0; k < N; ++k) elig[k] = k;
+    uint64_t state = seed;
+    for (int t = 0; t < K; ++t) {
+        const uint64_t z = splitmix64_next(state);
+        const uint64_t j = t + z % (uint64_t)(N - t);
+        std::swap(elig[t], elig[j]);
+    }
+    const size_t o_lab = 0;
+    const size_t o_prev = o_lab + ((N * 4 + 255) & ~255ull);
+    const size_t o_dist = o_prev + ((N * 4 + 255) & ~255ull);
+    const size_t o_mask = o_dist + ((N * 4 + 255) & ~255ull);
+    const size_t o_mem = o_mask + ((N + 255) & ~255ull);
+    const size_t o_co = o_mem + ((N * 8 + 255) & ~255ull);
+    const size_t o_cnt = o_co + (((K + 1) * 8 + 255) & ~255ull);
+    const size_t o_cur = o_cnt + ((K * 8 + 255) & ~255ull);
+    const size_t o_ids = o_cur + ((K * 8 + 255) & ~255ull);
+    const size_t o_obj = o_ids + ((K * 8 + 255) & ~255ull);
+    const size_t o_bobj = o_obj + 256;
+    const size_t o_csym = o_bobj + ((K * 8 + 255) & ~255ull);
+    const size_t o_cnt2 = o_csym + (((size_t)K * m * 4 + 255) & ~255ull);
+    const size_t o_plan = o_cnt2 + 256;
+    const size_t total = o_plan + (size_t)n * m * 4;
+    void* base = nullptr;
+    if ((rc = d2_ws(ctx, WS_CLUSTER_LOOP, total, &base))) return rc;
+    char* b = static_cast<char*>(base);
+    int32_t* lab = reinterpret_cast<int32_t*>(b + o_lab);
+    int32_t* prev = reinterpret_cast<int32_t*>(b + o_prev);
+    float* dist = reinterpret_cast<float*>(b + o_dist);
+    uint8_t* mask = reinterpret_cast<uint8_t*>(b + o_mask);
+    int64_t* members = reinterpret_cast<int64_t*>(b + o_mem);
+    int64_t* co = reinterpret_cast<int64_t*>(b + o_co);
+    int64_t* counts = reinterpret_cast<int64_t*>(b + o_cnt);
+    int64_t* cursor = reinterpret_cast<int64_t*>(b + o_cur);
+    int64_t* ids = reinterpret_cast<int64_t*>(b + o_ids);
+    double* dobj = reinterpret_cast<double*>(b + o_obj);
+    double* bobj = reinterpret_cast<double*>(b + o_bobj);
+    int32_t* csym = reinterpret_cast<int32_t*>(b + o_csym);
+    int64_t* solves = reinterpret_cast<int64_t*>(b + o_cnt2);  // [0] exact solves, [1] fall-backs, [2] limit
+    float* plan = reinterpret_cast<float*>(b + o_plan);
+
+    D2_CK(ctx, cudaMemcpyAsync(ids, elig.data(), K * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    k_tile_sym<<<(unsigned)d2_ceil_div((int64_t)K * m, 256), 256, 0, st>>>(sym, K, m, csym);
+    D2_LAUNCH_CK(ctx, "k_tile_sym");
+    k_sym_project<<<(unsigned)d2_ceil_div(K, 64), 64, 0, st>>>(ids, K, bags->offsets, bags->vocab_idx, bags->wt,
+                                                               bags->symcost, bags->V, sym, m, w_out);
+    D2_LAUNCH_CK(ctx, "k_sym_project");
+    D2_CK(ctx, cudaMemsetAsync(prev, 0xff, N * 4, st));
+    D2_CK(ctx, cudaMemsetAsync(solves, 0, 3 * sizeof(int64_t), st));
+    void* scnt = nullptr;
+    if ((rc = d2_ws(ctx, WS_SCAN, 64, &scnt))) return rc;
+    int64_t* acounters = static_cast<int64_t*>(scnt);
+    d2_badmm_opts o;
+    if (opts) o = *opts; else d2_badmm_opts_default(&o);
+    o.flags &= ~D2_VALIDATE;
+    const unsigned gN = (unsigned)d2_ceil_div(N, 256);
+    for (int r = 0; r < rounds; ++r) {
+        if ((rc = d2_assign_sym_impl(ctx, bags, K, m, csym, w_out, lab, dist, acounters, st))) return rc;
+        k_acc_counts<<<1, 1, 0, st>>>(solves, acounters);
+        D2_LAUNCH_CK(ctx, "k_acc_counts");
+        k_mean_dist<<<1, 1024, 0, st>>>(dist, N, dobj);
+        D2_LAUNCH_CK(ctx, "k_mean_dist");
+        if (obj_per_round)
+            D2_CK(ctx, cudaMemcpyAsync(&obj_per_round[r], dobj, sizeof(double), cudaMemcpyDeviceToHost, st));
+        k_warm_mask<<<gN, 256, 0, st>>>(lab, prev, N, mask);
+        D2_LAUNCH_CK(ctx, "k_warm_mask");
+        D2_CK(ctx, cudaMemsetAsync(counts, 0, K * 8, st));
+        k_label_hist<<<gN, 256, 0, st>>>(lab, N, K, counts);
+        D2_LAUNCH_CK(ctx, "k_label_hist");
+        k_excl_scan<<<1, 1024, 0, st>>>(counts, K, co);
+        D2_LAUNCH_CK(ctx, "k_excl_scan");
+        k_stable_scatter<<<1, 1024, 0, st>>>(lab, N, K, co, cursor, members);
+        D2_LAUNCH_CK(ctx, "k_stable_scatter");
+        if ((rc = badmm_barycenter_sym(ctx, bags, co, members, N, K, m, csym, w_out, plan, mask, &o, bobj, stream)))
+            return rc;
+        D2_CK(ctx, cudaMemcpyAsync(prev, lab, N * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    D2_CK(ctx, cudaMemcpyAsync(labels_out, lab, N * 4, cudaMemcpyDeviceToDevice, st));
+    int64_t hs[3] = {0, 0, 0};
+    D2_CK(ctx, cudaMemcpyAsync(hs, solves, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    D2_CK(ctx, cudaStreamSynchronize(st));
+    ctx->cluster_solves = hs[0];
+    ctx->cluster_fallbacks = 0;
+    if (hs[2] > 0)
+        return d2_fail(ctx, D2_ENOCONV, "d2_cluster_sym: %lld exact W^2 solves reached the phase cap",
+                       (long long)hs[2]);
+    return D2_OK;
+}
+
 extern "C" int d2_cluster_stats(const d2_ctx* ctx, int64_t* stats) {
     if (!ctx || !stats) return D2_EINVAL;
     stats[0] = ctx->cluster_solves;

@@ -129,8 +129,10 @@ static inline cudaStream_t d2_stream(void* s) { return reinterpret_cast<cudaStre
 
 static inline int64_t d2_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Host-side validation of a bag descriptor (pointers and sizes only).
+// Host-side validation of a bag descriptor (pointers and sizes only):
+// coordinate bags (dense or through a point table), or symbolic bags.
 int d2_check_bags_host(d2_ctx* ctx, const d2_bags* b);
+int d2_check_sym_bags_host(d2_ctx* ctx, const d2_bags* b);
 
 // ---------------------------------------------------------------------------
 // Device helpers
@@ -229,6 +231,16 @@ bool d2_support_tc_applies(const d2_bags* b, int m, int prec);
 int d2_support_tc_prepare(d2_ctx* ctx, const d2_bags* b, int m, int prec);
 int d2_support_tc(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t maxch, int m, int prec,
                   const float* plan, const ClusterWs& cw, float* xpart, cudaStream_t st);
+
+// Symbolic supports (symbolic.cu): cost rows gathered from the bags' symbol
+// table for the centroid symbols csym (K x m), with the FP64 chunk sums of
+// Eq. rho when chunk_sum is given; the exact assignment on those costs
+// (counters: solves, fall-backs, phase-cap hits; cleared here).
+int d2_sym_cost_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int64_t P, int K, int m,
+                     const int32_t* csym, const ClusterWs& cw, float* C, double* chunk_sum, int64_t* chunk_rows,
+                     cudaStream_t st);
+int d2_assign_sym_impl(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, const int32_t* csym,
+                       const float* w, int32_t* labels, float* dist, int64_t* counters, cudaStream_t st);
 
 // Builds the chunk table of a cluster-offsets array (no position map).
 int d2_build_chunks(d2_ctx* ctx, const int64_t* cofs, int K, const ClusterWs& cw, cudaStream_t st);

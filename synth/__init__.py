@@ -36,6 +36,7 @@ class Bags:
     vocab: Optional[torch.Tensor] = None      # float32 (V, d)
     labels: Optional[torch.Tensor] = None     # int64 (N) ground-truth class
     meta: dict = field(default_factory=dict)
+    symcost: Optional[torch.Tensor] = None    # float32 (V, V): symbolic bags (vocab_idx = symbols)
 
     @property
     def N(self) -> int:
@@ -51,7 +52,13 @@ class Bags:
     def to(self, device) -> "Bags":
         mv = lambda t: None if t is None else t.to(device)
         return Bags(mv(self.offsets), mv(self.wt), self.d, mv(self.supp),
-                    mv(self.vocab_idx), mv(self.vocab), mv(self.labels), dict(self.meta))
+                    mv(self.vocab_idx), mv(self.vocab), mv(self.labels), dict(self.meta), mv(self.symcost))
+
+    def symbols(self, k: int):
+        """(symbol ids (int64 numpy), weights (float64 numpy)) of symbolic bag k."""
+        a, b = int(self.offsets[k]), int(self.offsets[k + 1])
+        return (self.vocab_idx[a:b].detach().cpu().long().numpy(),
+                self.wt[a:b].detach().cpu().double().numpy())
 
     def points(self) -> torch.Tensor:
         """(n, d) support points, gathering from the vocabulary if needed."""
@@ -263,6 +270,38 @@ def document_bags(seed: int, N: int, V: int = 50_000, d: int = 300, mk=(10, 60),
     wt = (counts / tot[owner]).float()
     return Bags(offsets, wt, d, vocab_idx=vocab_idx, vocab=vocab,
                 meta=dict(recipe="document", seed=seed, V=V))
+
+
+def symbolic_bags(seed: int, N: int, V: int = 20, n_classes: int = 4, mk=(4, 16), q: int = 5,
+                  alpha: float = 1.0, device="cpu") -> Bags:
+    """Symbolic workload (stand-in for the paper's symbolic data, e.g. amino-acid
+    histograms over V = 20 symbols): the symbol-to-symbol dissimilarity is the
+    squared Euclidean distance between hidden embeddings of the symbols (N(0, I)
+    in R^q); each class c has a symbol distribution pi_c ~ Dirichlet(1) over the
+    V symbols; a bag of class c draws m_k ~ U{mk} distinct symbols from pi_c
+    (sampling without replacement) with weights Dirichlet(alpha).  Supports are
+    stored as symbol ids (vocab_idx) with the V x V table in symcost; d = 1."""
+    g = _gen(seed, device)
+    emb = torch.randn(V, q, generator=g, dtype=torch.float64, device=device)
+    table = ((emb[:, None, :] - emb[None, :, :]) ** 2).sum(-1).float()
+    pis = _gamma_ge1(g, torch.ones(n_classes * V, dtype=torch.float64, device=device), device).reshape(n_classes, V)
+    pis = pis / pis.sum(1, keepdim=True)
+    labels = torch.randint(0, n_classes, (N,), generator=g, device=device)
+    sizes = torch.randint(mk[0], min(mk[1], V) + 1, (N,), generator=g, device=device)
+    offsets = _ragged(sizes)
+    n = int(offsets[-1])
+    sym = torch.empty(n, dtype=torch.int32, device=device)
+    # distinct symbols per bag: the first m_k of the class's weighted random order
+    # (Efraimidis-Spirakis keys u^(1/pi))
+    u = torch.rand(N, V, generator=g, dtype=torch.float64, device=device).clamp_min(1e-300)
+    keys = u.log() / pis[labels]
+    order = torch.argsort(keys, dim=1, descending=True)
+    owner = _row_owner(offsets)
+    pos = torch.arange(n, device=device) - offsets[:-1][owner]
+    sym[:] = order[owner, pos].to(torch.int32)
+    wt = _dirichlet_rows(g, offsets, alpha, device)
+    return Bags(offsets, wt, 1, vocab_idx=sym, labels=labels, symcost=table,
+                meta=dict(recipe="symbolic", seed=seed, V=V))
 
 
 def sample_initial_barycenters(seed: int, bags: Bags, cluster_offsets: torch.Tensor,
