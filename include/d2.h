@@ -270,6 +270,29 @@ int badmm_barycenter(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_of
                      float* x, float* w, float* plan, const uint8_t* warm_mask,
                      const d2_badmm_opts* opts, double* obj, void* stream);
 
+/* ---- member-parallel trunks (the parallel implementation of Section 5) ----
+ * Every cross-member sum of Algorithm badmm (the weight consensus of every
+ * iteration, the support partials of every support update, the cost sum of
+ * Eq. rho, the objective, the member counts) is an exact sum of 64-bit
+ * fixed-point integers, whose result does not depend on the order of its
+ * terms.  A caller that splits the members of every cluster over several
+ * processes (each calling badmm_barycenter with its own members, in whole
+ * groups of 64 consecutive members of a cluster as one process would order
+ * them, so that every per-group partial sum is the same) installs a reducer
+ * that sums (or takes the maximum of) an int64 buffer element-wise across the
+ * processes, in place, ordered on the given stream -- an NCCL all-reduce, or
+ * host code.  The results (x, w, the plans of each process's members, the
+ * objective) are then bitwise those of one process holding every member.
+ * The library calls the reducer while it enqueues work (about one call per
+ * iteration, two per support update); with a reducer installed it launches
+ * kernels directly (no CUDA graph, no D2_SPLIT_STREAMS).  fn returns 0 on
+ * success; anything else makes the call fail with D2_ECUDA.  fn = NULL
+ * removes it.  No counterpart in the paper beyond the trunks themselves. */
+#define D2_REDUCE_SUM 0
+#define D2_REDUCE_MAX 1
+typedef int (*d2_reducer_fn)(void* user, int32_t op, int64_t* buf, int64_t count, void* stream);
+int d2_set_reducer(d2_ctx* ctx, d2_reducer_fn fn, void* user);
+
 /* Plan-sweep autotuner (no counterpart in the paper; Algorithm badmm fixes
  * what is computed, not how it is laid out on a GPU).  The first
  * badmm_barycenter call on a context with D2_AUTOTUNE in opts->flags and plan

@@ -31,6 +31,9 @@ D2_COST_ROWS = 0x1000
 D2_SUPPORT_TC = 0x2000
 D2_TEST_EXPIRE_WAIT = 0x8000
 D2_TUNE_MAX = 16
+D2_REDUCE_SUM, D2_REDUCE_MAX = 0, 1
+# int reducer(void* user, int32 op, int64* buf, int64 count, void* stream)
+REDUCER_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_int32, c_void_p, c_int64, c_void_p)
 COST_PRECISION = {"fp32": 0, "bf16": D2_COST_BF16, "bf16x3": D2_COST_BF16X3, "bf16x6": D2_COST_BF16X6}
 KT_NAMES = ("sweep_fused", "sweep_half", "cost", "support", "assign", "prune", "other")
 KT_COUNT = len(KT_NAMES)
@@ -66,6 +69,7 @@ _SIGS = {
     "d2_device_errors": (c_int, [c_void_p, c_void_p]),
     "d2_set_phase_limit": (c_int, [c_void_p, c_int32]),
     "d2_set_flow_store": (c_int, [c_void_p, c_int32, c_int32]),
+    "d2_set_reducer": (c_int, [c_void_p, c_void_p, c_void_p]),
     "d2_sweep_tuning": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "d2_cluster_stats": (c_int, [c_void_p, c_void_p]),
     "d2_cost": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32,
@@ -205,6 +209,25 @@ class Context:
         """Cap the exact solver's shortest-path phases per pair (0 = default);
         a low cap makes solves stop early and report D2_ENOCONV."""
         self.check(lib().d2_set_phase_limit(self.h, int(max_phases)))
+
+    def set_reducer(self, fn):
+        """Install fn(op, ptr, count, stream) -> int as the cross-process reducer
+        of badmm_barycenter's exact sums (D2_REDUCE_SUM / D2_REDUCE_MAX of an
+        int64 buffer of `count` elements at device address `ptr`, in place,
+        ordered on the CUDA stream `stream`); None removes it."""
+        if fn is None:
+            self._reducer = None
+            self.check(lib().d2_set_reducer(self.h, None, None))
+            return
+
+        def tramp(user, op, ptr, count, stream):
+            try:
+                return int(fn(int(op), int(ptr), int(count), int(stream or 0)))
+            except Exception:  # no exception may cross the C boundary
+                return 1
+
+        self._reducer = REDUCER_FN(tramp)
+        self.check(lib().d2_set_reducer(self.h, ctypes.cast(self._reducer, c_void_p), None))
 
     def set_flow_store(self, store="auto", pool_cap=0):
         """Exact solver's flow store: "auto", "dense" or "sparse"; pool_cap > 0

@@ -176,6 +176,13 @@ extern "C" int d2_device_errors(d2_ctx* ctx, int32_t* bits) {
     return D2_OK;
 }
 
+extern "C" int d2_set_reducer(d2_ctx* ctx, d2_reducer_fn fn, void* user) {
+    if (!ctx) return D2_EINVAL;
+    ctx->reducer = fn;
+    ctx->reducer_user = fn ? user : nullptr;
+    return D2_OK;
+}
+
 extern "C" int d2_set_flow_store(d2_ctx* ctx, int32_t store, int32_t pool_cap) {
     if (!ctx || store < 0 || store > 2 || pool_cap < 0) return D2_EINVAL;
     ctx->flow_store = store;

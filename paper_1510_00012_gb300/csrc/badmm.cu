@@ -126,54 +126,6 @@ __device__ __forceinline__ void df_add_prod(float& hi, float& lo, float a, float
     lo = __fadd_rn(lo, pe);
 }
 
-// Weight consensus (Eq. badmmw / badmmw2) of one cluster per CTA, in FP64 and
-// a fixed order: thread (g, i) sums the members p0 + g, p0 + g + G, ... of
-// column i in double-float (every term added exactly up to ~2^-48 of the
-// sum), the G groups are then added in order in FP64, then the m columns.
-#define CONS_THREADS 1024
-__global__ void __launch_bounds__(CONS_THREADS) k_consensus(const int64_t* cofs, const float* pos_part, int m,
-                                                            bool r2, float* w_next, double* w_next64) {
-    __shared__ double s_acc[CONS_THREADS + 257];
-    const int c = blockIdx.x;
-    const int64_t p0 = cofs[c], p1 = cofs[c + 1];
-    if (p1 == p0) return;  // empty cluster: weights unchanged
-    const int G = CONS_THREADS / m;
-    const int t = threadIdx.x;
-    const int i = t % m, g = t / m;
-    if (g < G) {
-        // eight loads in flight, added in member order
-        float hi = 0.f, lo = 0.f;
-        int64_t p = p0 + g;
-        for (; p + 7 * G < p1; p += 8 * G) {
-            float v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = __ldcg(pos_part + (p + u * G) * m + i);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) df_add(hi, lo, v[u]);
-        }
-        for (; p < p1; p += G) df_add(hi, lo, pos_part[p * m + i]);
-        s_acc[g * m + i] = (double)hi + (double)lo;
-    }
-    __syncthreads();
-    if (t < m) {
-        double sv = 0.0;
-        for (int h = 0; h < G; ++h) sv += s_acc[h * m + t];
-        s_acc[CONS_THREADS + t] = r2 ? sv * sv : sv;
-    }
-    __syncthreads();
-    if (t == 0) {
-        double tot = 0.0;
-        for (int h = 0; h < m; ++h) tot += s_acc[CONS_THREADS + h];
-        s_acc[CONS_THREADS + 256] = tot;
-    }
-    __syncthreads();
-    if (t < m) {
-        const double wv = s_acc[CONS_THREADS + t] / s_acc[CONS_THREADS + 256];
-        w_next64[(int64_t)c * m + t] = wv;
-        w_next[(int64_t)c * m + t] = (float)wv;
-    }
-}
-
 template <int VEC, int LPR, int NV>
 __global__ void __launch_bounds__(SWEEP_THREADS, D2_SWEEP_MINB) k_sweep(SweepArgs a) {
     constexpr int RPW = 32 / LPR;   // rows per warp step
@@ -782,33 +734,8 @@ extern "C" int d2_sweep_tuning(const d2_ctx* ctx, int32_t m, int32_t* ncand, int
 }
 
 // ---------------------------------------------------------------------------
-// rho per cluster (Eq. rho, rho0 x mean cost) from the per-chunk FP64 sums
-// ---------------------------------------------------------------------------
-__global__ void k_rho(int K, int m, const int64_t* chunk_first, const double* chunk_sum,
-                      const int64_t* chunk_rows, double rho0, double rho_fixed, float* rho, float* beta,
-                      int64_t* nrows) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= K) return;
-    double s = 0.0;
-    int64_t r = 0;
-    if (chunk_sum) {
-        for (int64_t q = chunk_first[c]; q < chunk_first[c + 1]; ++q) {
-            s += chunk_sum[q];
-            r += chunk_rows[q];
-        }
-    }
-    double v;
-    if (rho_fixed > 0.0) v = rho_fixed;
-    else v = (r > 0) ? rho0 * s / ((double)m * (double)r) : 1.0;
-    if (!(v > 0.0) || !isfinite(v)) v = 1.0;   // all costs zero: any rho gives the same plans
-    rho[c] = (float)v;
-    beta[c] = (float)(D2_LOG2E / v);
-    nrows[c] = r;
-}
-
-// ---------------------------------------------------------------------------
-// support update (Eq. updatex): per-chunk partial sums of Pi2^T Y, then a
-// fixed-order combine per cluster and the division by N_c w_i
+// support update (Eq. updatex): per-chunk partial sums of Pi2^T Y (their
+// exact sum per cluster and the division by N_c w_i are in reduce.cu)
 // ---------------------------------------------------------------------------
 #define XU_THREADS 256
 #define XU_ROWS 32
@@ -1025,42 +952,7 @@ __global__ void __launch_bounds__(128) k_xpartial_pipe(const int64_t* members, c
     }
 }
 
-// x_i = (mu_c if the partials are of centred coordinates) + sum of the chunk
-// partials / (N_c w_i), the chunks added in order; a point of zero mass keeps
-// its position
-__global__ void k_xfinal(int m, int d, const int64_t* cofs, const int64_t* chunk_first, const float* xpart,
-                         const float* w, const float* mu, float* x) {
-    const int c = blockIdx.x;
-    const int64_t Nc = cofs[c + 1] - cofs[c];
-    if (Nc == 0) return;
-    const int64_t q0 = chunk_first[c], q1 = chunk_first[c + 1];
-    for (int idx = threadIdx.x; idx < m * d; idx += blockDim.x) {
-        const int i = idx / d;
-        float s = 0.f;
-        for (int64_t q = q0; q < q1; ++q) s += xpart[q * (int64_t)m * d + idx];
-        const float mass = (float)Nc * w[(int64_t)c * m + i];
-        if (mass > 0.f) x[(int64_t)c * m * d + idx] = mu ? mu[(int64_t)c * d + (idx - i * d)] + s / mass : s / mass;
-    }
-}
 
-// objective (1/N_c) sum_k <C_k, Pi^(k,1)> in fixed member order; final weights out
-__global__ void k_finish(int K, int m, const int64_t* cofs, const double* pos_obj, const float* wfin,
-                         float* w_out, double* obj, bool want_obj) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= K) return;
-    const int64_t p0 = cofs[c], p1 = cofs[c + 1];
-    if (p1 == p0) {
-        if (obj) obj[c] = 0.0;
-        return;
-    }
-    if (want_obj && obj) {
-        double s = 0.0;
-        for (int64_t p = p0; p < p1; ++p) s += pos_obj[p];
-        obj[c] = s / (double)(p1 - p0);
-    }
-    if (wfin != w_out)
-        for (int i = 0; i < m; ++i) w_out[(int64_t)c * m + i] = wfin[(int64_t)c * m + i];
-}
 
 // Reads the autotuner's event pairs (synchronises the stream), averages them
 // per candidate and keeps the fastest launch shape in the context.
@@ -1259,7 +1151,12 @@ static int badmm_impl(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_o
         rc = d2_check_bags(ctx, bags, stream);
         if (rc) return rc;
     }
-    if (P == 0) return D2_OK;
+    if (P == 0) {
+        if (ctx->reducer)  // the other processes would wait in the reductions
+            return d2_fail(ctx, D2_EINVAL, "badmm_barycenter: with a reducer every process needs members");
+        return D2_OK;
+    }
+    if (ctx->reducer) opts.flags &= ~D2_SPLIT_STREAMS;  // one call on one stream per process
     if (opts.flags & D2_SPLIT_STREAMS) {
         bool done = false;
         rc = badmm_split(ctx, bags, cluster_offsets, members, P, K, m, x, w, plan, warm_mask, opts, obj, st, &done);
@@ -1285,8 +1182,13 @@ static int badmm_impl(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_o
         if ((rc = d2_ws(ctx, WS_XPART, (size_t)maxch * m * d * 4, &vxp))) return rc;
     }
     const bool need_sums = !(opts.rho > 0.0);
+    // exact reductions: global member counts (K + 1), consensus sums (K m),
+    // scratch for the rho / support / objective sums
+    const size_t fx_scratch = std::max<size_t>((size_t)3 * K, fix_x ? 0 : (size_t)K + (size_t)K * m * d);
+    void* vfx = nullptr;
+    if ((rc = d2_ws(ctx, WS_FIXED, ((size_t)K + 1 + (size_t)K * m + fx_scratch) * 8, &vfx))) return rc;
     void *vpc = nullptr, *vcs = nullptr;
-    if ((rc = d2_ws(ctx, WS_POS_CLUSTER, (size_t)P * 4, &vpc))) return rc;
+    if ((rc = d2_ws(ctx, WS_POS_CLUSTER, (size_t)std::max<int64_t>(P, 1) * 4, &vpc))) return rc;
     if (need_sums && (rc = d2_ws(ctx, WS_CHUNK_SUM, (size_t)maxch * 16, &vcs))) return rc;
     const int cost_prec = csym ? 0 : d2_cost_prec(opts.flags);
     const bool use_vt = !csym && d2_vocab_table_applies(bags, K, m, cost_prec, opts.flags);
@@ -1305,6 +1207,9 @@ static int badmm_impl(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_o
     int64_t* chunk_rows = need_sums ? reinterpret_cast<int64_t*>(static_cast<char*>(vcs) + (size_t)maxch * 8) : nullptr;
     float* lam = static_cast<float*>(vlam);
     float* cost = static_cast<float*>(vcost);
+    int64_t* gcount = static_cast<int64_t*>(vfx);
+    long long* cons_sum = reinterpret_cast<long long*>(gcount + K + 1);
+    long long* fx = cons_sum + (size_t)K * m;
 
     SweepArgs sa;
     sa.members = members;
@@ -1372,6 +1277,7 @@ static int badmm_impl(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_o
   auto enqueue = [&]() -> int {
     int rc = D2_OK;
     if ((rc = d2_setup_clusters(ctx, cluster_offsets, P, K, &pos_cluster, &cw, st))) return rc;
+    if ((rc = d2_fx_counts(ctx, K, cluster_offsets, gcount, st))) return rc;
     D2_CK(ctx, cudaMemsetAsync(cw.counters, 0, (size_t)K * 4, st));
     D2_CK(ctx, cudaMemcpyAsync(cw.wb[0], w, (size_t)K * m * 4, cudaMemcpyDeviceToDevice, st));
     // initial cost and rho (Eq. rho)
@@ -1383,9 +1289,9 @@ static int badmm_impl(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_o
                                use_vt ? D2_VT_SETUP : D2_VT_OFF, st)))
             return rc;
     }
-    k_rho<<<(unsigned)d2_ceil_div(K, 128), 128, 0, st>>>(K, m, cw.chunk_first, chunk_sum, chunk_rows,
-                                                        opts.rho0, opts.rho, cw.rho, cw.beta, cw.nrows);
-    D2_LAUNCH_CK(ctx, "k_rho");
+    if ((rc = d2_fx_rho(ctx, K, m, cw.chunk_first, chunk_sum, chunk_rows, gcount, opts.rho0, opts.rho, cw.rho,
+                        cw.beta, cw.nrows, fx, st)))
+        return rc;
 
     auto launch = [&](int flags, const float* wcur, float* wnext) -> int {
         SweepArgs s = sa;
@@ -1414,9 +1320,10 @@ static int badmm_impl(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_o
         D2_LAUNCH_CK(ctx, "k_sweep");
         if ((flags & SW_A) && s.w_next) {
             d2_time_begin(ctx, D2_KT_OTHER, st);
-            k_consensus<<<K, CONS_THREADS, 0, st>>>(cluster_offsets, sa.pos_part, m, rflag != 0, s.w_next, cw.w64);
+            const int crc = d2_fx_consensus(ctx, K, m, cluster_offsets, sa.pos_part, rflag != 0, gcount, cons_sum,
+                                            s.w_next, cw.w64, st);
             d2_time_end(ctx, st);
-            D2_LAUNCH_CK(ctx, "k_consensus");
+            if (crc) return crc;
         }
         return D2_OK;
     };
@@ -1449,10 +1356,10 @@ static int badmm_impl(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_o
                                                       static_cast<float*>(vxp));
             }
             D2_LAUNCH_CK(ctx, "k_xpartial");
-            k_xfinal<<<K, 256, 0, st>>>(m, d, cluster_offsets, cw.chunk_first, static_cast<float*>(vxp),
-                                        wbuf(it), xp_tc ? cw.mu : nullptr, x);
+            rc = d2_fx_support(ctx, K, m, d, cw.chunk_first, static_cast<float*>(vxp), gcount, wbuf(it),
+                               xp_tc ? cw.mu : nullptr, x, fx, st);
             d2_time_end(ctx, st);
-            D2_LAUNCH_CK(ctx, "k_xfinal");
+            if (rc) return rc;
             if ((rc = d2_prep_x(ctx, x, K, m, d, cw, st))) return rc;
             if ((rc = d2_cost_rows(ctx, bags, members, P, K, m, cw, cost, false, cost_prec,
                                    use_vt ? D2_VT_REUSE : D2_VT_OFF, st)))
@@ -1466,10 +1373,7 @@ static int badmm_impl(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_o
     }
     // final B step: Pi2^T into the plan buffer (Lambda^T is not needed)
     if ((rc = launch(SW_B | (lam_valid ? 0 : SW_LAM_ZERO), wbuf(T), nullptr))) return rc;
-    k_finish<<<(unsigned)d2_ceil_div(K, 128), 128, 0, st>>>(K, m, cluster_offsets, sa.pos_obj, wbuf(T), w,
-                                                            obj, true);
-    D2_LAUNCH_CK(ctx, "k_finish");
-    return D2_OK;
+    return d2_fx_finish(ctx, K, m, cluster_offsets, sa.pos_obj, gcount, wbuf(T), w, obj, fx, st);
   };
 
     // Replay the whole launch sequence as one CUDA graph when possible: on a
@@ -1482,7 +1386,7 @@ static int badmm_impl(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_o
         for (auto e : tev) cudaEventDestroy(e);
         return rc;
     }
-    const bool want_graph = !(opts.flags & D2_NO_GRAPH) && !ctx->timing && st != nullptr;
+    const bool want_graph = !(opts.flags & D2_NO_GRAPH) && !ctx->timing && st != nullptr && !ctx->reducer;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (want_graph && cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
         cudaGetLastError();

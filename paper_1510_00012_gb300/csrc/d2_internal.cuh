@@ -34,6 +34,7 @@ enum WsSlot {
     WS_VOCAB,        // vocabulary cost table: word flags, slots, pseudo-members, chunks
     WS_VOCAB_T,      // vocabulary cost table rows (<= min(n, K V) x m floats)
     WS_ASSIGN_OVF,   // exact solver: pairs whose sparse flow pool overflowed
+    WS_FIXED,        // exact fixed-point reductions: counts, consensus sums, scratch
     WS_NSLOTS
 };
 
@@ -79,6 +80,9 @@ struct d2_ctx {
     int expire_test = 0;
     // cap on the exact solver's shortest-path phases per pair (0: default)
     int phase_limit = 0;
+    // member-parallel trunks: sum / max of int64 buffers across processes
+    d2_reducer_fn reducer = nullptr;
+    void* reducer_user = nullptr;
     // exact solver's flow store: 0 automatic, 1 dense, 2 sparse; and a cap on
     // the sparse pool's entries (0: none) -- testing and tuning
     int flow_store = 0;
@@ -241,6 +245,21 @@ int d2_sym_cost_rows(d2_ctx* ctx, const d2_bags* b, const int64_t* members, int6
                      cudaStream_t st);
 int d2_assign_sym_impl(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, const int32_t* csym,
                        const float* w, int32_t* labels, float* dist, int64_t* counters, cudaStream_t st);
+
+// Exact fixed-point cross-member reductions (reduce.cu), reduced across
+// processes by the installed reducer.  gcount: K + 1 int64 (member counts
+// per cluster over every process, then their total).
+int d2_reduce(d2_ctx* ctx, int op, int64_t* buf, int64_t count, cudaStream_t st);
+int d2_fx_counts(d2_ctx* ctx, int K, const int64_t* cofs, int64_t* gcount, cudaStream_t st);
+int d2_fx_consensus(d2_ctx* ctx, int K, int m, const int64_t* cofs, const float* pos_part, bool r2,
+                    const int64_t* gcount, long long* S, float* w_next, double* w_next64, cudaStream_t st);
+int d2_fx_rho(d2_ctx* ctx, int K, int m, const int64_t* chunk_first, const double* chunk_sum,
+              const int64_t* chunk_rows, const int64_t* gcount, double rho0, double rho_fixed, float* rho,
+              float* beta, int64_t* nrows, long long* fx, cudaStream_t st);
+int d2_fx_support(d2_ctx* ctx, int K, int m, int d, const int64_t* chunk_first, const float* xpart,
+                  const int64_t* gcount, const float* w, const float* mu, float* x, long long* fx, cudaStream_t st);
+int d2_fx_finish(d2_ctx* ctx, int K, int m, const int64_t* cofs, const double* pos_obj, const int64_t* gcount,
+                 const float* wfin, float* w_out, double* obj, long long* fx, cudaStream_t st);
 
 // Builds the chunk table of a cluster-offsets array (no position map).
 int d2_build_chunks(d2_ctx* ctx, const int64_t* cofs, int K, const ClusterWs& cw, cudaStream_t st);
