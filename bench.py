@@ -900,6 +900,57 @@ def run_reference(args):
     return 0
 
 
+def run_probe(args):
+    """Small single-kernel cases for profiling (ncu captures of one launch):
+    assign_docs : exact W^2 of 4,000 document bags (d = 300, Zipf words from a
+                  50,000-word vocabulary) against K = 64 merge-initialised
+                  centroids of m = 64 points, solved once warm and once timed;
+    support_tc  : one badmm_barycenter call (T = 11, tau = 10: one support
+                  update) on 256 clusters of the ragged recipe with the
+                  split-BF16 cost and the tensor-core support update.
+    Prints one JSON line with the timing."""
+    import paper_1510_00012_gb300 as d2
+    from paper_1510_00012_gb300 import build
+    build.build()
+    dev = torch.device("cuda", 0)
+    ctx = d2.Context(0)
+    out = {"probe": args.probe}
+    if args.probe == "assign_docs":
+        N = args.probe_n or 4000
+        bags = synth.document_bags(5, N, V=50000, d=300, mk=(10, 60), device=dev)
+        db = d2.DeviceBags(bags.offsets, bags.wt, bags.d, vocab_idx=bags.vocab_idx, vocab=bags.vocab)
+        ctx.set_flow_store(args.probe_store)
+        ids = torch.arange(0, 64 * 37, 37, device=dev) % N
+        x, w = d2.d2_merge_init(ctx, db, ids, 64)
+        d2.d2_assign(ctx, db, x, w)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, st = d2.d2_assign(ctx, db, x, w, want_stats=True)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        out.update({"pairs": N * 64, "s": t, "pairs_per_s": N * 64 / t, "flow_store": args.probe_store,
+                    "limit_hits": st["limit_hits"]})
+    elif args.probe == "support_tc":
+        bags, co, mem = synth.ragged_cluster_bags(7, args.probe_n or 256, device=dev)
+        x0, w0 = synth.sample_initial_barycenters(8, bags, co, mem, 32)
+        db = d2.DeviceBags(bags.offsets, bags.wt, bags.d, supp=bags.supp)
+        opts = d2.badmm_opts(iters=11, tau=10, cost="bf16x3", graph=False, support_tc=True)
+        x, w = x0.clone(), w0.clone()
+        d2.badmm_barycenter(ctx, db, co, mem, x, w, None, None, opts)
+        torch.cuda.synchronize()
+        ctx.timing(True)
+        x, w = x0.clone(), w0.clone()
+        d2.badmm_barycenter(ctx, db, co, mem, x, w, None, None, opts)
+        torch.cuda.synchronize()
+        kt = ctx.timing_read()
+        s_ms, s_n = kt["support"]
+        out.update({"rows": bags.n, "support_ms": s_ms / s_n,
+                    "support_gbs_384B_per_row": bags.n * 384 / (s_ms / s_n * 1e-3) / 1e9})
+    assert ctx.device_errors() == 0
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -929,7 +980,13 @@ def main():
                     help="one stream per call (no D2_SPLIT_STREAMS) for the timed steps")
     ap.add_argument("--no-cost-variants", action="store_true",
                     help="skip the timing of the other cost-build precisions")
+    ap.add_argument("--probe", default=None, choices=["assign_docs", "support_tc"],
+                    help="run one small profiling case instead of the benchmark")
+    ap.add_argument("--probe-n", type=int, default=0)
+    ap.add_argument("--probe-store", default="auto", choices=["auto", "dense", "sparse"])
     args = ap.parse_args()
+    if args.probe:
+        return run_probe(args)
     if args.impl == "reference":
         return run_reference(args)
 
