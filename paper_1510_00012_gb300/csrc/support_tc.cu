@@ -15,20 +15,22 @@
 //
 // Data flow per CTA (one chunk, one block of 64 support dimensions, which
 // fill TMEM lanes 0..63 of the M = 128 accumulator; rows 64..127 of A are
-// zero):
-//   * tiles of 64 rows are staged in shared memory as FP32 by asynchronous
-//     16-byte copies, two tiles ahead of their use (three stages);
-//   * each staged tile is centred, split into BF16 pieces and written
-//     transposed into the 128-byte-swizzled K-major A and B operands (one
-//     16-byte store per piece and 8 rows); the operands are double-buffered;
-//   * one thread issues the tile's MMAs (4 K steps of 16 rows x the piece
-//     products) and commits them to the buffer's mbarrier;
+// zero), warp-specialised:
+//   * converter warps stage tiles of 64 rows in shared memory as FP32 by
+//     asynchronous 16-byte copies, several tiles ahead of their use (as many
+//     stages as fit), then centre each staged tile, split it into BF16
+//     pieces and write it transposed into the 128-byte-swizzled K-major A and
+//     B operands (one 16-byte store per piece and 8 rows), one or two
+//     operand buffers;
+//   * one lane of the MMA warp issues each tile's MMAs (4 K steps of 16 rows
+//     x the piece products) once the converters have filled the buffer, and
+//     commits them to the buffer's mbarrier;
 //   * after the last tile two warps read the 64 TMEM lanes (support
-//     dimensions) and write the chunk's m x d partial sums, which k_xfinal
-//     adds up in a fixed order.
-// Every mbarrier wait is bounded (about 2 s of global time); on expiry the
-// CTA records D2F_DEV_TIMEOUT in the context's device error word, skips the
-// rest of its work, frees its tensor memory and returns.
+//     dimensions) and write the chunk's m x d partial sums, which the exact
+//     per-cluster sums of reduce.cu add up.
+// Every wait is bounded (about 2 s of global time); on expiry the CTA records
+// D2F_DEV_TIMEOUT in the context's device error word, skips the rest of its
+// work, frees its tensor memory and returns.
 #include <algorithm>
 
 #include "d2_internal.cuh"

@@ -96,3 +96,19 @@ def test_initial_barycenters_from_cluster_support():
         pts = torch.cat([b.supp[b.offsets[k]:b.offsets[k + 1]] for k in ids.tolist()])
         for i in range(6):
             assert bool((pts == x0[c, i]).all(1).any())
+
+
+def test_symbolic_bags_recipe():
+    """Symbolic histograms: the table is a squared-distance matrix (zero
+    diagonal, symmetric, non-negative); every bag's symbols are distinct ids in
+    [0, V) and its weights lie in the simplex."""
+    b = synth.symbolic_bags(3, 200, V=20, n_classes=4, mk=(4, 16))
+    D = b.symcost.double()
+    assert D.shape == (20, 20)
+    assert torch.allclose(D, D.T) and (D.diagonal() == 0).all() and (D >= 0).all()
+    sizes = b.sizes()
+    assert int(sizes.min()) >= 4 and int(sizes.max()) <= 16 and b.d == 1
+    for k in range(b.N):
+        t, w = b.symbols(k)
+        assert len(set(t.tolist())) == len(t) and t.min() >= 0 and t.max() < 20
+        assert abs(w.sum() - 1.0) < 1e-5 and (w >= 0).all()
