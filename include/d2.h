@@ -392,7 +392,7 @@ int d2_prune_train(d2_ctx* ctx, d2_prune* p, const d2_bags* bags,
  *            reached the phase cap (synchronises when given)
  * The exact solver is successive shortest paths with node potentials, one
  * warp per (bag, centroid) pair, flows and costs in FP32, the final cost
- * summed in FP64.  Requires m + max_mk <= 256 and the two m x max_mk FP32
+ * summed in FP64.  Requires 32 ceil(m / 32) + max_mk <= 256 and the two m x max_mk FP32
  * tableaus of a pair within 200 KiB (D2_ENOTSUP otherwise).  A solve that
  * reaches its phase cap (see d2_set_phase_limit) gives a wrong value: with
  * stats the call then returns D2_ENOCONV; without stats (asynchronous) it
@@ -445,7 +445,8 @@ int d2_w2_pairs(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,
  * synchronous: it reads back how many solves reached the phase cap.
  * Returns D2_OK, D2_EINVAL (bad pointers or sizes; supp and vocab both given
  * or both missing), D2_ESCRATCH (N * K > D2_NOALLOC_MAX_PAIRS), D2_ENOTSUP
- * (m + max_mk > 256, or the per-pair tableaus of d2_assign exceed 200 KiB),
+ * (32 ceil(m / 32) + max_mk > 256, or the per-pair tableaus of d2_assign
+ * exceed 200 KiB),
  * D2_ENOCONV (some solve reached the phase cap: its value and label are
  * wrong) or D2_ECUDA. */
 #define D2_NOALLOC_MAX_PAIRS (1 << 20)

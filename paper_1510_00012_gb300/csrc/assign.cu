@@ -94,11 +94,18 @@ struct WarpLayout {
     int E, MW;
 };
 __host__ __device__ inline size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
+// Node numbering: centroid point i is node i (i < m); bag point j is node
+// B + j with B = 32 ceil(m / 32), so that a lane's register slots t < B / 32
+// hold sources only and slots t >= B / 32 sinks only; nodes m .. B - 1 do not
+// exist.  Valid nodes keep their relative order (ties resolve as with nodes
+// numbered 0 .. m + n - 1).
+__host__ __device__ inline int sink_base(int m) { return 32 * ((m + 31) / 32); }
+
 __host__ __device__ inline WarpLayout warp_layout(int m, int ncap, bool sparse) {
     WarpLayout L;
-    const int ns = ncap | 1, V = m + ncap;
+    const int ns = ncap | 1, V = sink_base(m) + ncap;  // node span
     L.MW = (m + 31) / 32;
-    L.E = sparse ? 2 * V : 0;
+    L.E = sparse ? 2 * (m + ncap) : 0;
     L.c = 0;
     size_t o = al16((size_t)m * ns * 4);
     L.f = L.ef = L.mask = L.head = L.enext = L.esrc = o;
@@ -113,7 +120,7 @@ __host__ __device__ inline WarpLayout warp_layout(int m, int ncap, bool sparse) 
         L.esrc = L.enext + (size_t)L.E * 2;
         store = L.esrc + (size_t)L.E * 2 - o;
     }
-    const size_t stage = (size_t)AS_DC * V * 4;
+    const size_t stage = (size_t)AS_DC * (m + ncap) * 4;
     const bool stage_inside = stage <= store;
     o = al16(o + store);
     L.pot = o;
@@ -226,7 +233,9 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
     const int m = a.m, d = a.d;
     const int64_t r0 = a.offsets[bag];
     const int n = (int)(a.offsets[bag + 1] - r0);
-    const int V = m + n;
+    const int V = m + n;                 // nodes
+    const int SS = (m + 31) >> 5, B = SS << 5;
+    const int VS = B + n;                // node span (sinks start at B)
     const float* xc = a.x ? a.x + (int64_t)cent * m * d : nullptr;
 
     // ---- cost C[i][j] = sum_dd (x_i - y_j)^2 by direct differences, or the
@@ -274,8 +283,8 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
     } else {
         for (int e = lane; e < m * ns; e += 32) s.F[e] = 0.f;
     }
-    for (int v = lane; v < V; v += 32) {
-        s.exc[v] = (v < m) ? a.w[(int64_t)cent * m + v] : a.wt[r0 + (v - m)];
+    for (int v = lane; v < VS; v += 32) {
+        s.exc[v] = (v < m) ? a.w[(int64_t)cent * m + v] : (v >= B ? a.wt[r0 + (v - B)] : 0.f);
         s.pot[v] = 0.f;
     }
     __syncwarp();
@@ -290,15 +299,15 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
                 am = i;
             }
         }
-        s.pot[m + j] = mn;
-        s.pred[m + j] = (short)am;
+        s.pot[B + j] = mn;
+        s.pred[B + j] = (short)am;
     }
     __syncwarp();
     bool gov = false;  // sparse pool full during the greedy start (only under a test cap)
     if (lane == 0) {
         for (int j = 0; j < n; ++j) {
-            int i = s.pred[m + j];
-            float f = fminf(s.exc[m + j], s.exc[i]);
+            int i = s.pred[B + j];
+            float f = fminf(s.exc[B + j], s.exc[i]);
             if (f > 0.f) {
                 if (SP) {
                     const int k = pool_new(s, i, j, fbump, ffree);
@@ -311,7 +320,7 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
                 } else {
                     s.F[i * ns + j] += f;
                 }
-                s.exc[m + j] -= f;
+                s.exc[B + j] -= f;
                 s.exc[i] -= f;
             }
         }
@@ -328,8 +337,8 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
 #pragma unroll
     for (int t = 0; t < TV; ++t) {
         const int v = lane + 32 * t;
-        pot[t] = v < V ? s.pot[v] : 0.f;
-        exc[t] = v < V ? s.exc[v] : 0.f;
+        pot[t] = v < VS ? s.pot[v] : 0.f;
+        exc[t] = v < VS ? s.exc[v] : 0.f;
     }
     int phase = 0;
     for (;;) {
@@ -338,7 +347,7 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
 #pragma unroll
         for (int t = 0; t < TV; ++t) {
             const int v = lane + 32 * t;
-            if (v < V && exc[t] > tol) {
+            if (v < VS && exc[t] > tol) {
                 if (v < m) src = true; else snk = true;
             }
         }
@@ -355,21 +364,21 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
         for (int t = 0; t < TV; ++t) {
             const int v = lane + 32 * t;
             dist[t] = (v < m && exc[t] > tol) ? 0.f : AS_INF;
-            if (v < V) s.pred[v] = -1;
+            if (v < VS) s.pred[v] = -1;
         }
         // up to kt_max deficit sinks per pass (settled in order of distance);
         // the shortest paths to all of them become tight arcs after the
         // potential update, so flow is pushed along each (primal-dual step)
         int kt = 0, tgl = -1;  // lane q < kt holds the q-th target
         const int kt_max = as_kt(m, V);
-        for (int it = 0; it < V; ++it) {
+        for (int it = 0; it < V; ++it) {  // at most one settled node per step
             // warp argmin over unsettled nodes: smallest distance, then lowest index
             float bv = AS_INF;
             int bi = 0x7fffffff;
 #pragma unroll
             for (int t = 0; t < TV; ++t) {
                 const int v = lane + 32 * t;
-                if (v < V && !((vis >> t) & 1u) && dist[t] < bv) {
+                if (v < VS && !((vis >> t) & 1u) && dist[t] < bv) {
                     bv = dist[t];
                     bi = v;
                 }
@@ -380,7 +389,7 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
             const int u = (int)__reduce_min_sync(0xffffffffu, __float_as_uint(bv) == kmin ? (unsigned)bi : 0xffffffffu);
             const float du = __uint_as_float(kmin);
             if ((u & 31) == lane) vis |= 1u << (u >> 5);
-            if (u >= m && node_bcast<TV>(exc, u) > tol) {
+            if (u >= B && node_bcast<TV>(exc, u) > tol) {
                 if (lane == kt) tgl = u;
                 if (++kt == kt_max) break;
             }
@@ -389,9 +398,10 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
                 const float* crow = s.C + u * ns;
 #pragma unroll
                 for (int t = 0; t < TV; ++t) {
+                    if (t < SS) continue;  // source slots (warp-uniform)
                     const int v = lane + 32 * t;
-                    if (v >= m && v < V && !((vis >> t) & 1u)) {
-                        const float rc = fmaxf(crow[v - m] + pu - pot[t], 0.f);
+                    if (v < VS && !((vis >> t) & 1u)) {
+                        const float rc = fmaxf(crow[v - B] + pu - pot[t], 0.f);
                         const float nd = du + rc;
                         if (nd < dist[t]) {
                             dist[t] = nd;
@@ -400,9 +410,10 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
                     }
                 }
             } else {
-                const int j = u - m;
+                const int j = u - B;
 #pragma unroll
                 for (int t = 0; t < TV; ++t) {
+                    if (t >= SS) break;  // sink slots (warp-uniform)
                     const int i = lane + 32 * t;
                     const bool arc = SP ? (i < m && ((s.mask[j * s.MW + t] >> lane) & 1u))
                                         : (i < m && s.F[i * ns + j] > tol);
@@ -442,14 +453,14 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
                         src_node = v;
                         break;
                     }
-                    if (v < m) {  // backward arc (v, p - m)
+                    if (v < m) {  // backward arc (v, p - B)
                         float fv;
                         if (SP) {
                             int pv;
-                            const int k = pool_find(s, v, p - m, &pv);
+                            const int k = pool_find(s, v, p - B, &pv);
                             fv = k >= 0 ? s.ef[k] : 0.f;
                         } else {
-                            fv = s.F[v * ns + (p - m)];
+                            fv = s.F[v * ns + (p - B)];
                         }
                         dflow = fminf(dflow, fv);
                     }
@@ -469,31 +480,31 @@ __device__ double solve_pair(const AssignArgs& a, WarpMem& s, int64_t bag, int c
                     if (SP) {
                         if (v >= m) {  // forward arc p -> v
                             int pv;
-                            int k = pool_find(s, p, v - m, &pv);
-                            if (k < 0) k = pool_new(s, p, v - m, fbump, ffree);
+                            int k = pool_find(s, p, v - B, &pv);
+                            if (k < 0) k = pool_new(s, p, v - B, fbump, ffree);
                             if (k < 0) {
                                 ovf = true;
                                 break;
                             }
                             s.ef[k] += delta;
-                            pool_bit(s, p, v - m, s.ef[k] > tol);
-                        } else {       // backward arc: flow on (v, p - m) decreases
+                            pool_bit(s, p, v - B, s.ef[k] > tol);
+                        } else {       // backward arc: flow on (v, p - B) decreases
                             int pv;
-                            const int k = pool_find(s, v, p - m, &pv);
+                            const int k = pool_find(s, v, p - B, &pv);
                             if (k >= 0) {
                                 float f = s.ef[k] - delta;
                                 f = f > 0.f ? f : 0.f;
-                                if (f == 0.f) pool_free(s, p - m, k, pv, ffree);
+                                if (f == 0.f) pool_free(s, p - B, k, pv, ffree);
                                 else s.ef[k] = f;
-                                pool_bit(s, v, p - m, f > tol);
+                                pool_bit(s, v, p - B, f > tol);
                             }
                         }
                     } else {
                         if (v >= m) {  // forward arc p -> v
-                            s.F[p * ns + (v - m)] += delta;
-                        } else {       // backward arc: flow on (v, p - m) decreases
-                            const float f = s.F[v * ns + (p - m)] - delta;
-                            s.F[v * ns + (p - m)] = f > 0.f ? f : 0.f;
+                            s.F[p * ns + (v - B)] += delta;
+                        } else {       // backward arc: flow on (v, p - B) decreases
+                            const float f = s.F[v * ns + (p - B)] - delta;
+                            s.F[v * ns + (p - B)] = f > 0.f ? f : 0.f;
                         }
                     }
                     v = p;
@@ -683,9 +694,9 @@ static int pair_launch_config(AssignArgs& a, int64_t max_units, int device, bool
         *why = "m * max_mk too large for the per-warp tableau";
         return D2_ENOTSUP;
     }
-    L->fn = w2_kernel_for(a.m + a.nmax, sparse);
+    L->fn = w2_kernel_for(sink_base(a.m) + a.nmax, sparse);
     if (!L->fn) {
-        *why = "m + max_mk exceeds 256";
+        *why = "32 ceil(m / 32) + max_mk exceeds 256";
         return D2_ENOTSUP;
     }
     L->wpb = pick_wpb(a.warp_bytes);
