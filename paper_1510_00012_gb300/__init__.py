@@ -595,7 +595,7 @@ def d2_assign_noalloc(bags, x, w):
     rc = lib().d2_assign_noalloc(bags.ref(), x.shape[0], x.shape[1], _ptr(x), _ptr(w), _ptr(labels), _ptr(dist),
                                  _stream())
     if rc != D2_OK:
-        why = {D2_ESCRATCH: ": N * K exceeds the fixed scratch", D2_ENOTSUP: ": m + max_mk or the tableaus too large",
+        why = {D2_ESCRATCH: ": N * K exceeds the fixed scratch", D2_ENOTSUP: ": 32 ceil(m/32) + max_mk above 256 or the tableaus too large",
                D2_EINVAL: ": invalid arguments", D2_ENOCONV: ": a solve reached the phase cap"}.get(rc, "")
         raise D2Error(rc, "d2_assign_noalloc failed" + why)
     return labels, dist

@@ -674,11 +674,11 @@ static W2Fn w2_kernel_for(int V, bool sparse) {
     return nullptr;
 }
 
-// Launch shape of the pair solver for a.m + a.nmax nodes on `device` with
+// Launch shape of the pair solver for 32 ceil(a.m / 32) + a.nmax node slots on `device` with
 // the given flow store: kernel, warps per block, dynamic shared memory and a
 // grid bound (the kernel is a persistent stride loop; `resident` = warps per
 // SM).  Returns D2_OK, or D2_ENOTSUP when the per-warp memory exceeds 200 KiB
-// or m + max_mk exceeds 256 (then *why says which), or D2_ECUDA when a
+// or 32 ceil(m / 32) + max_mk exceeds 256 (then *why says which), or D2_ECUDA when a
 // runtime call fails.
 struct PairLaunch {
     W2Fn fn;

@@ -57,12 +57,12 @@ def test_rejects_problems_beyond_the_scratch(d2):
 
 
 def test_rejects_unsupported_and_invalid_shapes(d2):
-    """Both rejections happen on the host before any kernel runs: m + max_mk
-    above the solver's 256 nodes (D2_ENOTSUP), and bags with neither a
+    """Both rejections happen on the host before any kernel runs: 32 ceil(m/32)
+    + max_mk above the solver's 256 node slots (D2_ENOTSUP), and bags with neither a
     support matrix nor a vocabulary (D2_EINVAL)."""
     bags, _, _ = problem(4, 40, 1, 4, 3)
     db = d2.DeviceBags.from_synth(bags)
-    m = 257 - db.max_mk
+    m = 32 * ((257 - db.max_mk + 31) // 32)  # smallest multiple of 32 past the limit
     x = torch.zeros(1, m, 3, device="cuda")
     w = torch.full((1, m), 1.0 / m, device="cuda")
     with pytest.raises(d2.D2Error) as e:
