@@ -905,9 +905,13 @@ def run_probe(args):
     assign_docs : exact W^2 of 4,000 document bags (d = 300, Zipf words from a
                   50,000-word vocabulary) against K = 64 merge-initialised
                   centroids of m = 64 points, solved once warm and once timed;
-    support_tc  : one badmm_barycenter call (T = 11, tau = 10: one support
-                  update) on 256 clusters of the ragged recipe with the
-                  split-BF16 cost and the tensor-core support update.
+    support     : one badmm_barycenter call (T = 11, tau = 10: one support
+                  update) on 256 clusters of the ragged recipe (m = 32,
+                  d = 64) with the split-BF16 cost and the CUDA-core support
+                  partials;
+    support_tc  : the same with the tensor-core support update;
+    support_docs: the same call on 100,000 document bags (d = 300, Zipf words
+                  of a 50,000-word vocabulary) in 64 random clusters, m = 64.
     Prints one JSON line with the timing."""
     import paper_1510_00012_gb300 as d2
     from paper_1510_00012_gb300 import build
@@ -930,11 +934,23 @@ def run_probe(args):
         t = time.perf_counter() - t0
         out.update({"pairs": N * 64, "s": t, "pairs_per_s": N * 64 / t, "flow_store": args.probe_store,
                     "limit_hits": st["limit_hits"]})
-    elif args.probe == "support_tc":
-        bags, co, mem = synth.ragged_cluster_bags(7, args.probe_n or 256, device=dev)
-        x0, w0 = synth.sample_initial_barycenters(8, bags, co, mem, 32)
-        db = d2.DeviceBags(bags.offsets, bags.wt, bags.d, supp=bags.supp)
-        opts = d2.badmm_opts(iters=11, tau=10, cost="bf16x3", graph=False, support_tc=True)
+    elif args.probe in ("support", "support_tc", "support_docs"):
+        if args.probe == "support_docs":
+            N, K, m = args.probe_n or 100000, 64, 64
+            bags = synth.document_bags(5, N, V=50000, d=300, mk=(10, 60), device=dev)
+            db = d2.DeviceBags(bags.offsets, bags.wt, bags.d, vocab_idx=bags.vocab_idx, vocab=bags.vocab)
+            lab = torch.randint(0, K, (N,), generator=torch.Generator().manual_seed(9))
+            co = torch.zeros(K + 1, dtype=torch.int64)
+            co[1:] = torch.cumsum(torch.bincount(lab, minlength=K), 0)
+            co, mem = co.to(dev), torch.sort(lab, stable=True).indices.to(dev)
+            row_bytes = 4 * (m + 300)
+        else:
+            m = 32
+            bags, co, mem = synth.ragged_cluster_bags(7, args.probe_n or 256, device=dev)
+            db = d2.DeviceBags(bags.offsets, bags.wt, bags.d, supp=bags.supp)
+            row_bytes = 4 * (m + 64)
+        x0, w0 = synth.sample_initial_barycenters(8, bags, co, mem, m)
+        opts = d2.badmm_opts(iters=11, tau=10, cost="bf16x3", graph=False, support_tc=args.probe == "support_tc")
         x, w = x0.clone(), w0.clone()
         d2.badmm_barycenter(ctx, db, co, mem, x, w, None, None, opts)
         torch.cuda.synchronize()
@@ -944,8 +960,8 @@ def run_probe(args):
         torch.cuda.synchronize()
         kt = ctx.timing_read()
         s_ms, s_n = kt["support"]
-        out.update({"rows": bags.n, "support_ms": s_ms / s_n,
-                    "support_gbs_384B_per_row": bags.n * 384 / (s_ms / s_n * 1e-3) / 1e9})
+        out.update({"rows": bags.n, "support_ms": s_ms / s_n, "row_bytes": row_bytes,
+                    "support_gbs": bags.n * row_bytes / (s_ms / s_n * 1e-3) / 1e9})
     assert ctx.device_errors() == 0
     print(json.dumps(out), flush=True)
     return 0
@@ -980,7 +996,7 @@ def main():
                     help="one stream per call (no D2_SPLIT_STREAMS) for the timed steps")
     ap.add_argument("--no-cost-variants", action="store_true",
                     help="skip the timing of the other cost-build precisions")
-    ap.add_argument("--probe", default=None, choices=["assign_docs", "support_tc"],
+    ap.add_argument("--probe", default=None, choices=["assign_docs", "support", "support_tc", "support_docs"],
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--probe-n", type=int, default=0)
     ap.add_argument("--probe-store", default="auto", choices=["auto", "dense", "sparse"])

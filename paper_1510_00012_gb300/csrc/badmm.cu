@@ -821,134 +821,194 @@ __global__ void __launch_bounds__(XU_THREADS) k_xpartial(const int64_t* members,
 }
 
 
-// Pipelined support partials for m % 4 == 0 and d % 4 == 0: 128 threads own a
-// 32 (i) x 64 (d) output tile, 4 x 4 per thread; rows arrive in tiles of
-// XP_ROWS = 32 through double-buffered cp.async copies of the matching Pi2
-// and y slices.
-#define XP_ROWS 32
-#define XP_PS (32 + 4)
-#define XP_YS (64 + 4)
+// Support partials on the CUDA cores for m % 4 == 0 and d % 4 == 0 (rows of
+// 16-byte multiples).  A CTA owns one chunk and one 32 (i) x 64 (d) tile of
+// the chunk's m x d partial sum; the CTAs of one chunk are adjacent in the
+// grid, so the rows that several tiles read come from L2 after the first.
+// Its XW_WARPS warps take the chunk's row tiles of XW_RW rows round-robin,
+// each through a private ring of XW_S stages filled by 16-byte asynchronous
+// copies (no CTA barrier until the end).  Each lane accumulates an 8 x 8
+// block of the tile with paired FP32 fused multiply-adds (each product
+// rounded once, as fmaf), reading 16 values per row from shared memory.  The
+// warps' partial tiles are then added in warp order, so the result depends
+// on the chunk alone, not on timing.
+#define XW_WARPS 4
+#define XW_RW 8
+#define XW_S 4
+#define XW_RED (64 + 4)   // row stride of the partial tiles in shared memory (floats)
+
+struct XwStage {
+    float p[XW_RW][32];   // Pi2 row slice i0 .. i0 + 31
+    float y[XW_RW][64];   // support row slice d0 .. d0 + 63
+};
+static_assert(sizeof(XwStage) * XW_S >= 32 * XW_RED * 4, "a warp's ring holds its partial tile");
+constexpr size_t XW_SMEM = sizeof(XwStage) * XW_S * XW_WARPS;
 
 __device__ __forceinline__ void xp_cp16(void* sdst, const void* gsrc) {
     unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc));
 }
 
-__global__ void __launch_bounds__(128) k_xpartial_pipe(const int64_t* members, const int64_t* offsets,
-                                                       const float* supp, const int32_t* vidx, const float* vocab,
-                                                       int d, int m, const float* plan, const Chunk* chunks,
-                                                       const int64_t* nchunks, float* xpart) {
-    __shared__ __align__(16) float ps[2][XP_ROWS][XP_PS];
-    __shared__ __align__(16) float ys[2][XP_ROWS][XP_YS];
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__global__ void __launch_bounds__(XW_WARPS * 32, 4)
+k_xpartial_warp(const int64_t* members, const int64_t* offsets, const float* supp, const int32_t* vidx,
+                const float* vocab, int d, int m, const float* plan, const Chunk* chunks, const int64_t* nchunks,
+                int ntd, int ntiles, float* xpart) {
+    extern __shared__ __align__(16) unsigned char xw_raw[];
     __shared__ int64_t s_rs[D2_CHUNK];
     __shared__ int s_pre[D2_CHUNK + 1];
-    __shared__ int64_t s_row[2][XP_ROWS];
-    const int64_t q = blockIdx.x;
+    const int64_t q = blockIdx.x / (unsigned)ntiles;
+    const int tile = (int)(blockIdx.x - (unsigned)(q * ntiles));
     if (q >= *nchunks) return;
-    const int d0 = blockIdx.y * 64, i0 = blockIdx.z * 32;
-    if (d0 >= d || i0 >= m) return;
+    const int i0 = (tile / ntd) * 32, d0 = (tile % ntd) * 64;
     const Chunk ch = chunks[q];
     const int nm = (int)(ch.p1 - ch.p0);
-    const int tid = threadIdx.x;
-    if (tid < nm) {
-        int64_t k = members[ch.p0 + tid];
-        s_rs[tid] = offsets[k];
-        s_pre[tid + 1] = (int)(offsets[k + 1] - offsets[k]);
-    }
-    __syncthreads();
-    if (tid == 0) {
-        s_pre[0] = 0;
-        for (int t = 0; t < nm; ++t) s_pre[t + 1] += s_pre[t];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (w == 0) {
+        // row starts of the members and the exclusive prefix sums of their
+        // row counts (nm <= 64: two members per lane); entries past nm hold
+        // the total
+        const int t0 = 2 * lane, t1 = t0 + 1;
+        int c0 = 0, c1 = 0;
+        if (t0 < nm) {
+            const int64_t k = members[ch.p0 + t0];
+            s_rs[t0] = offsets[k];
+            c0 = (int)(offsets[k + 1] - offsets[k]);
+        }
+        if (t1 < nm) {
+            const int64_t k = members[ch.p0 + t1];
+            s_rs[t1] = offsets[k];
+            c1 = (int)(offsets[k + 1] - offsets[k]);
+        }
+        int incl = c0 + c1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int excl = incl - c0 - c1;
+        s_pre[t0] = excl;
+        s_pre[t1] = excl + c0;
+        if (lane == 31) s_pre[D2_CHUNK] = incl;
     }
     __syncthreads();
     const int R = s_pre[nm];
-    const int ntile = (R + XP_ROWS - 1) / XP_ROWS;
-    const int td = tid & 15, ti = tid >> 4;   // dd = td*4 .. +3, i = ti*4 .. +3
-    // accumulators in pairs along dd: acc2[u][h] = (acc[u][2h], acc[u][2h+1])
-    unsigned long long acc2[4][2];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) acc2[u][0] = acc2[u][1] = 0ull;
+    const int NT = (R + XW_RW - 1) / XW_RW;
+    XwStage* ring = reinterpret_cast<XwStage*>(xw_raw) + w * XW_S;
+    const int np4 = min(32, m - i0) >> 2, ny4 = min(64, d - d0) >> 2;
 
-    auto rows_of = [&](int t, int b) {  // global rows of tile t into s_row[b]
-        if (tid < XP_ROWS) {
-            const int lr = t * XP_ROWS + tid;
-            int64_t g = -1;
-            if (lr < R) {
-                int lo = 0, hi = nm - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (s_pre[mid] <= lr) lo = mid; else hi = mid - 1;
-                }
-                g = s_rs[lo] + (lr - s_pre[lo]);
+    // stage j of this warp: its row tile w + j XW_WARPS (an empty group past
+    // the end).  Lanes 0..7 find the row of plan row r = lane and lanes 8..15
+    // the support row of row r = lane - 8 (member by a fixed six-step search of
+    // the prefix sums, nm <= 64); each lane then copies two 16-byte Pi2
+    // segments and four support segments.  Rows past the chunk read as zero.
+    const int sr = lane & 7;
+    auto issue = [&](int j) {
+        const int t = w + j * XW_WARPS;
+        if (t < NT) {
+            XwStage& st = ring[j % XW_S];
+            const int lr = t * XW_RW + sr;
+            const float* rp = nullptr;
+            if (lane < 16 && lr < R) {
+                int lo = 0;
+#pragma unroll
+                for (int step = 32; step > 0; step >>= 1)
+                    if (lo + step < nm && s_pre[lo + step] <= lr) lo += step;
+                const int64_t g = s_rs[lo] + (lr - s_pre[lo]);
+                rp = lane < 8 ? plan + g * m + i0 : d2_row_ptr(supp, vidx, vocab, d, g) + d0;
             }
-            s_row[b][tid] = g;
-        }
-    };
-    auto issue = [&](int b) {
-        // Pi2 slices: XP_ROWS rows x 8 segments; y slices: XP_ROWS rows x 16 segments
-        for (int e = tid; e < XP_ROWS * 8; e += 128) {
-            const int r = e >> 3, sg = e & 7;
-            const int64_t g = s_row[b][r];
-            if (g >= 0 && i0 + sg * 4 < m) xp_cp16(&ps[b][r][sg * 4], plan + g * m + i0 + sg * 4);
-            else *reinterpret_cast<float4*>(&ps[b][r][sg * 4]) = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        for (int e = tid; e < XP_ROWS * 16; e += 128) {
-            const int r = e >> 4, sg = e & 15;
-            const int64_t g = s_row[b][r];
-            if (g >= 0 && d0 + sg * 4 < d) xp_cp16(&ys[b][r][sg * 4], d2_row_ptr(supp, vidx, vocab, d, g) + d0 + sg * 4);
-            else *reinterpret_cast<float4*>(&ys[b][r][sg * 4]) = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int it = 0; it < 2; ++it) {  // Pi2: 8 rows x 8 segments
+                const int r = (lane >> 3) + 4 * it, sg = lane & 7;
+                const float* src = reinterpret_cast<const float*>(__shfl_sync(0xffffffffu, (unsigned long long)rp, r));
+                float* dst = &st.p[r][sg * 4];
+                if (src && sg < np4) xp_cp16(dst, src + sg * 4);
+                else if (!src) *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int it = 0; it < 4; ++it) {  // support: 8 rows x 16 segments
+                const int r = (lane >> 4) + 2 * it, sg = lane & 15;
+                const float* src =
+                    reinterpret_cast<const float*>(__shfl_sync(0xffffffffu, (unsigned long long)rp, 8 + r));
+                float* dst = &st.y[r][sg * 4];
+                if (src && sg < ny4) xp_cp16(dst, src + sg * 4);
+                else if (!src) *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+                // (a column past m or d of a real row keeps whatever the stage
+                // held: it only meets accumulators that are never stored)
+            }
         }
         asm volatile("cp.async.commit_group;");
     };
-    if (ntile > 0) {
-        rows_of(0, 0);
-        __syncthreads();
-        issue(0);
-    }
-    for (int t = 0; t < ntile; ++t) {
-        const int b = t & 1;
-        if (t + 1 < ntile) {
-            rows_of(t + 1, b ^ 1);
-            __syncthreads();
-            issue(b ^ 1);
-            asm volatile("cp.async.wait_group 1;");
-        } else {
-            asm volatile("cp.async.wait_group 0;");
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int r = 0; r < XP_ROWS; ++r) {
-            const float4 pv = *reinterpret_cast<const float4*>(&ps[b][r][ti * 4]);
-            const float4 yv = *reinterpret_cast<const float4*>(&ys[b][r][td * 4]);
-            const float pa[4] = {pv.x, pv.y, pv.z, pv.w};
-            unsigned long long y01, y23;
-            asm("mov.b64 %0, {%1, %2};" : "=l"(y01) : "f"(yv.x), "f"(yv.y));
-            asm("mov.b64 %0, {%1, %2};" : "=l"(y23) : "f"(yv.z), "f"(yv.w));
+
+    // lane (ig, dg) owns i in {4 ig .. 4 ig + 3} + {0, 16} and d in {4 dg .. 4 dg + 3} + {0, 32}
+    const int ig = lane & 3, dg = lane >> 2;
+    unsigned long long acc[8][4];  // acc[a 4 + u][b 2 + h] = (i = 16 a + 4 ig + u; d = 32 b + 4 dg + 2 h, + 1)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                // two FP32 fused multiply-adds per instruction (each rounded once,
-                // as fmaf): acc[u][v] += pa[u] * ya[v]
-                unsigned long long pu;
-                asm("mov.b64 %0, {%1, %1};" : "=l"(pu) : "f"(pa[u]));
-                asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc2[u][0]) : "l"(pu), "l"(y01));
-                asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc2[u][1]) : "l"(pu), "l"(y23));
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0ull;
+#pragma unroll
+    for (int j = 0; j < XW_S - 1; ++j) issue(j);
+    const int nmine = NT > w ? (NT - w + XW_WARPS - 1) / XW_WARPS : 0;
+    for (int j = 0; j < nmine; ++j) {
+        issue(j + XW_S - 1);  // into the stage consumed in step j - 1
+        asm volatile("cp.async.wait_group %0;" ::"n"(XW_S - 1));
+        __syncwarp();
+        const XwStage& st = ring[j % XW_S];
+#pragma unroll 2
+        for (int r = 0; r < XW_RW; ++r) {
+            const float4 p0 = *reinterpret_cast<const float4*>(&st.p[r][4 * ig]);
+            const float4 p1 = *reinterpret_cast<const float4*>(&st.p[r][16 + 4 * ig]);
+            const float4 y0 = *reinterpret_cast<const float4*>(&st.y[r][4 * dg]);
+            const float4 y1 = *reinterpret_cast<const float4*>(&st.y[r][32 + 4 * dg]);
+            const unsigned long long yp[4] = {f2pack(y0.x, y0.y), f2pack(y0.z, y0.w), f2pack(y1.x, y1.y),
+                                              f2pack(y1.z, y1.w)};
+            const float pa[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const unsigned long long pu = f2pack(pa[u], pa[u]);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[u][v]) : "l"(pu), "l"(yp[v]));
             }
         }
-        __syncthreads();
+        __syncwarp();  // every lane has read the stage before it is refilled
     }
-    float acc[4][4];
+    asm volatile("cp.async.wait_group 0;");
+    __syncwarp();
+    // this warp's partial tile into its own ring, then the sum over warps in warp order
+    float* red = reinterpret_cast<float*>(ring);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[u][0]), "=f"(acc[u][1]) : "l"(acc2[u][0]));
-        asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[u][2]), "=f"(acc[u][3]) : "l"(acc2[u][1]));
-    }
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            float a0, a1, a2, a3;
+            asm("mov.b64 {%0, %1}, %2;" : "=f"(a0), "=f"(a1) : "l"(acc[u][2 * b]));
+            asm("mov.b64 {%0, %1}, %2;" : "=f"(a2), "=f"(a3) : "l"(acc[u][2 * b + 1]));
+            const int i = 16 * (u >> 2) + 4 * ig + (u & 3);
+            *reinterpret_cast<float4*>(&red[i * XW_RED + 32 * b + 4 * dg]) = make_float4(a0, a1, a2, a3);
+        }
+    __syncthreads();
     float* out = xpart + q * (int64_t)m * d;
+    const float* red0 = reinterpret_cast<const float*>(xw_raw);
+    constexpr int WSTRIDE = (int)(sizeof(XwStage) * XW_S / 4);  // floats between two warps' rings
+    for (int f = tid; f < 32 * 16; f += XW_WARPS * 32) {
+        const int i = f >> 4, c = f & 15;
+        if (i0 + i >= m || c >= ny4) continue;
+        float4 s = *reinterpret_cast<const float4*>(&red0[i * XW_RED + c * 4]);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int i = i0 + ti * 4 + u;
-        const int dd = d0 + td * 4;
-        if (i < m && dd < d)
-            *reinterpret_cast<float4*>(out + (int64_t)i * d + dd) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+        for (int v = 1; v < XW_WARPS; ++v) {
+            const float4 t = *reinterpret_cast<const float4*>(&red0[v * WSTRIDE + i * XW_RED + c * 4]);
+            s.x += t.x;
+            s.y += t.y;
+            s.z += t.z;
+            s.w += t.w;
+        }
+        *reinterpret_cast<float4*>(out + (int64_t)(i0 + i) * d + d0 + c * 4) = s;
     }
 }
 
@@ -1271,8 +1331,12 @@ static int badmm_impl(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_o
     }
     const int T = opts.iters, tau = opts.tau;
     // the d % 4 == 0 and m % 4 == 0 path copies 16-byte slices of plan and y rows
-    const bool xp_pipe = (d % 4 == 0) && (m % 4 == 0) &&
-        ((reinterpret_cast<uintptr_t>(bags->supp ? bags->supp : bags->vocab) & 15) == 0);
+    const int64_t xw_blocks = maxch * d2_ceil_div(d, 64) * d2_ceil_div(m, 32);
+    const bool xp_pipe = (d % 4 == 0) && (m % 4 == 0) && xw_blocks < ((int64_t)1 << 31) &&
+        ((reinterpret_cast<uintptr_t>(bags->supp ? bags->supp : bags->vocab) & 15) == 0) &&
+        ((reinterpret_cast<uintptr_t>(plan) & 15) == 0);
+    if (xp_pipe && !fix_x)
+        D2_CK(ctx, cudaFuncSetAttribute(k_xpartial_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XW_SMEM));
 
   auto enqueue = [&]() -> int {
     int rc = D2_OK;
@@ -1347,9 +1411,10 @@ static int badmm_impl(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_o
                                         st)))
                     return rc;
             } else if (xp_pipe) {
-                dim3 g2((unsigned)maxch, (unsigned)d2_ceil_div(d, 64), (unsigned)d2_ceil_div(m, 32));
-                k_xpartial_pipe<<<g2, 128, 0, st>>>(members, bags->offsets, bags->supp, bags->vocab_idx, bags->vocab,
-                                                    d, m, plan, cw.chunks, cw.nchunks, static_cast<float*>(vxp));
+                const int ntd = d2_ceil_div(d, 64), ntiles = ntd * d2_ceil_div(m, 32);
+                k_xpartial_warp<<<(unsigned)(maxch * ntiles), XW_WARPS * 32, XW_SMEM, st>>>(
+                    members, bags->offsets, bags->supp, bags->vocab_idx, bags->vocab, d, m, plan, cw.chunks,
+                    cw.nchunks, ntd, ntiles, static_cast<float*>(vxp));
             } else {
                 k_xpartial<<<g, XU_THREADS, 0, st>>>(members, bags->offsets, bags->supp, bags->vocab_idx,
                                                       bags->vocab, d, m, plan, cw.chunks, cw.nchunks,
