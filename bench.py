@@ -607,12 +607,16 @@ def docs_rounds(d2, ctx, dev, seed, rounds=2):
     out = {"workload": W["desc"].replace("5 rounds", "%d rounds" % rounds), "N": bags.N,
            "support_rows": bags.n, "generate_s": t_gen, "rounds": rounds,
            "s_per_round": t_cl / rounds, "obj_per_round": objs,
-           "assignment": "exact (certified lower bounds skip LPs; labels equal to the full N x K solve)",
+           "assignment": "exact (certified lower bounds -- the LP's one-sided relaxations, the means, and an "
+                         "entropic dual made feasible by a c-transform -- skip LPs; labels equal to the full N x K "
+                         "solve)",
            "exact_solves": cs["exact_solves"], "full_K_pairs": bags.N * K * rounds,
            "kernel_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in kt.items() if v[1]}}
     a_ms, a_n = kt["assign"]
     if a_n:
         out["exact_pairs_per_s"] = cs["exact_solves"] / (a_ms * 1e-3)
+    out["bound_s_per_round"] = kt["bound"][0] * 1e-3 / rounds
+    out["exact_solve_s_per_round"] = a_ms * 1e-3 / rounds
     f_ms, f_n = kt["sweep_fused"]
     if f_n:
         peak, peak_kind = load_peaks()
@@ -905,6 +909,9 @@ def run_probe(args):
     assign_docs : exact W^2 of 4,000 document bags (d = 300, Zipf words from a
                   50,000-word vocabulary) against K = 64 merge-initialised
                   centroids of m = 64 points, solved once warm and once timed;
+    bound_docs  : bounded exact assignment (certified and entropic dual
+                  bounds) of 8,000 document bags against K = 64
+                  merge-initialised centroids of m = 64 points;
     support     : one badmm_barycenter call (T = 11, tau = 10: one support
                   update) on 256 clusters of the ragged recipe (m = 32,
                   d = 64) with the split-BF16 cost and the CUDA-core support
@@ -934,6 +941,30 @@ def run_probe(args):
         t = time.perf_counter() - t0
         out.update({"pairs": N * 64, "s": t, "pairs_per_s": N * 64 / t, "flow_store": args.probe_store,
                     "limit_hits": st["limit_hits"]})
+    elif args.probe == "bound_docs":
+        N = args.probe_n or 8000
+        bags = synth.document_bags(5, N, V=50000, d=300, mk=(10, 60), device=dev)
+        db = d2.DeviceBags(bags.offsets, bags.wt, bags.d, vocab_idx=bags.vocab_idx, vocab=bags.vocab)
+        ids = torch.arange(0, 64 * 37, 37, device=dev) % N
+        x, w = d2.d2_merge_init(ctx, db, ids, 64)
+        d2.d2_assign(ctx, db, x, w, bounded=True)
+        torch.cuda.synchronize()
+        settings = [(-1, 0.0)]
+        if args.probe_dual:
+            settings = [tuple(float(v) for v in p.split(",")) for p in args.probe_dual.split(";")]
+        runs = []
+        for iters, eps in settings:
+            ctx.set_dual_bound(int(iters), eps)
+            ctx.timing(True)
+            t0 = time.perf_counter()
+            _, _, st = d2.d2_assign(ctx, db, x, w, want_stats=True, bounded=True)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            kt = ctx.timing_read()
+            runs.append({"dual_iters": int(iters), "dual_eps": eps, "s": t, "exact_solves": st["exact_solves"],
+                         "bound_ms": kt["bound"][0], "assign_ms": kt["assign"][0]})
+        ctx.set_dual_bound(-1, 0.0)
+        out.update({"pairs": N * 64, "runs": runs})
     elif args.probe in ("support", "support_tc", "support_docs"):
         if args.probe == "support_docs":
             N, K, m = args.probe_n or 100000, 64, 64
@@ -996,9 +1027,11 @@ def main():
                     help="one stream per call (no D2_SPLIT_STREAMS) for the timed steps")
     ap.add_argument("--no-cost-variants", action="store_true",
                     help="skip the timing of the other cost-build precisions")
-    ap.add_argument("--probe", default=None, choices=["assign_docs", "support", "support_tc", "support_docs"],
+    ap.add_argument("--probe", default=None, choices=["assign_docs", "bound_docs", "support", "support_tc", "support_docs"],
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--probe-n", type=int, default=0)
+    ap.add_argument("--probe-dual", default=None,
+                    help="bound_docs: 'iters,eps;iters,eps;...' settings of the entropic dual bound")
     ap.add_argument("--probe-store", default="auto", choices=["auto", "dense", "sparse"])
     args = ap.parse_args()
     if args.probe:

@@ -180,7 +180,8 @@ size_t d2_workspace_bytes(const d2_ctx* ctx);
 #define D2_KT_ASSIGN      4  /* exact assignment                                      */
 #define D2_KT_PRUNE       5  /* pruning network                                       */
 #define D2_KT_OTHER       6
-#define D2_KT_COUNT       7
+#define D2_KT_BOUND       7  /* lower bounds of the bounded exact assignment         */
+#define D2_KT_COUNT       8
 /* Turn per-launch timing on (1) or off (0); either way the totals restart. */
 int d2_timing_enable(d2_ctx* ctx, int on);
 /* Summed device milliseconds and launch counts per kind since the last
@@ -217,6 +218,18 @@ int d2_set_phase_limit(d2_ctx* ctx, int32_t max_phases);
  * entries below its default 2 (m + m_k), to exercise that path in tests.
  * Returns D2_EINVAL for a store outside 0..2 or a negative cap. */
 int d2_set_flow_store(d2_ctx* ctx, int32_t store, int32_t pool_cap);
+
+/* Entropic dual bound of d2_assign_bounded on this context (no counterpart in
+ * the paper; the argmin and its value stay those of the exact LP of Eq.
+ * primal).  For every pair that the cheap bounds leave, `iters` Sinkhorn
+ * iterations of the problem regularised by eps = eps_rel x the pair's mean
+ * cost give dual potentials, made feasible for the dual of Eq. (primal) by a
+ * c-transform; the dual objective is then a lower bound on W^2 that replaces
+ * the cheap one when larger, so fewer pairs need the exact solve.  Applies
+ * for m <= 64.  iters = -1 (default): 30 iterations when m >= 32, none below;
+ * 0: off.  eps_rel = 0: the default 0.05.  Returns D2_EINVAL for iters
+ * outside -1..10000 or eps_rel outside [0, 100]. */
+int d2_set_dual_bound(d2_ctx* ctx, int32_t iters, float eps_rel);
 
 /* Validate a bag set on the device (synchronous): offsets non-decreasing with
  * offsets[N] == n and every m_k in [1, max_mk]; weights finite, >= 0 and each

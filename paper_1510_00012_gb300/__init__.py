@@ -35,7 +35,7 @@ D2_REDUCE_SUM, D2_REDUCE_MAX = 0, 1
 # int reducer(void* user, int32 op, int64* buf, int64 count, void* stream)
 REDUCER_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_int32, c_void_p, c_int64, c_void_p)
 COST_PRECISION = {"fp32": 0, "bf16": D2_COST_BF16, "bf16x3": D2_COST_BF16X3, "bf16x6": D2_COST_BF16X6}
-KT_NAMES = ("sweep_fused", "sweep_half", "cost", "support", "assign", "prune", "other")
+KT_NAMES = ("sweep_fused", "sweep_half", "cost", "support", "assign", "prune", "other", "bound")
 KT_COUNT = len(KT_NAMES)
 
 
@@ -69,6 +69,7 @@ _SIGS = {
     "d2_device_errors": (c_int, [c_void_p, c_void_p]),
     "d2_set_phase_limit": (c_int, [c_void_p, c_int32]),
     "d2_set_flow_store": (c_int, [c_void_p, c_int32, c_int32]),
+    "d2_set_dual_bound": (c_int, [c_void_p, c_int32, c_float]),
     "d2_set_reducer": (c_int, [c_void_p, c_void_p, c_void_p]),
     "d2_sweep_tuning": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "d2_cluster_stats": (c_int, [c_void_p, c_void_p]),
@@ -234,6 +235,12 @@ class Context:
         caps the sparse pool (overflowed pairs are solved again densely)."""
         code = {"auto": 0, "dense": 1, "sparse": 2}[store]
         self.check(lib().d2_set_flow_store(self.h, code, int(pool_cap)))
+
+    def set_dual_bound(self, iters=-1, eps_rel=0.0):
+        """Entropic dual bound of d2_assign_bounded: Sinkhorn iterations per
+        pair (-1: automatic, 0: off) and eps as a fraction of the pair's mean
+        cost (0: default)."""
+        self.check(lib().d2_set_dual_bound(self.h, int(iters), float(eps_rel)))
 
     def sweep_tuning(self, m):
         """The plan-sweep autotuner's record for plan width m: None when untuned,

@@ -190,6 +190,13 @@ extern "C" int d2_set_flow_store(d2_ctx* ctx, int32_t store, int32_t pool_cap) {
     return D2_OK;
 }
 
+extern "C" int d2_set_dual_bound(d2_ctx* ctx, int32_t iters, float eps_rel) {
+    if (!ctx || iters < -1 || iters > 10000 || !(eps_rel >= 0.f) || eps_rel > 100.f) return D2_EINVAL;
+    ctx->dual_iters = iters;
+    ctx->dual_eps = eps_rel;
+    return D2_OK;
+}
+
 extern "C" int d2_set_phase_limit(d2_ctx* ctx, int32_t max_phases) {
     if (!ctx || max_phases < 0) return D2_EINVAL;
     ctx->phase_limit = max_phases;

@@ -39,6 +39,8 @@ struct LbArgs {
     const float* vocab;
     const float* wt;
     int d, m, K, nmax, ystride;
+    bool vec;          // 16-byte loads of support rows (d % 4 == 0, aligned rows)
+    int64_t ring_off;  // floats from the start of shared memory to the warps' rings
     const float* x;    // K x m x d
     const float* w;    // K x m
     const float* xn;   // K x m   ||x_i||^2
@@ -63,11 +65,144 @@ __global__ void k_centroid_stats(int K, int m, int d, const float* x, const floa
     }
 }
 
+// Cost entries C_ij = max(||x_i||^2 + ||y_j||^2 - 2 <x_i, y_j>, 0) of the
+// centroid points i0 .. i0 + 7 (rows past m repeat row m - 1) against the
+// lane's bag points j = lane + 32 q, each dot product summed in dimension
+// order.  With vec (d % 4 == 0, 16-byte aligned rows, ystride % 4 == 0) four
+// dimensions per step from 16-byte loads: eight centroid rows and JN bag rows
+// feed 32 JN multiply-adds.
+template <int JN>
+__device__ __forceinline__ void lb_cost8(const float* xc, const float* xn_c, int d, int m, int i0, const float* ys,
+                                         int ystride, const float* yn, int lane, bool vec, float (&cij)[8][JN]) {
+    float acc[8][JN];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int q = 0; q < JN; ++q) acc[u][q] = 0.f;
+    if (vec) {
+        for (int t = 0; t < d; t += 4) {
+            float4 yv[JN];
+#pragma unroll
+            for (int q = 0; q < JN; ++q) yv[q] = *reinterpret_cast<const float4*>(&ys[(lane + 32 * q) * ystride + t]);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = min(i0 + u, m - 1);
+                const float4 xv = __ldg(reinterpret_cast<const float4*>(xc + (int64_t)i * d + t));
+#pragma unroll
+                for (int q = 0; q < JN; ++q) {
+                    acc[u][q] = fmaf(xv.x, yv[q].x, acc[u][q]);
+                    acc[u][q] = fmaf(xv.y, yv[q].y, acc[u][q]);
+                    acc[u][q] = fmaf(xv.z, yv[q].z, acc[u][q]);
+                    acc[u][q] = fmaf(xv.w, yv[q].w, acc[u][q]);
+                }
+            }
+        }
+    } else {
+        for (int t = 0; t < d; ++t) {
+            float yv[JN];
+#pragma unroll
+            for (int q = 0; q < JN; ++q) yv[q] = ys[(lane + 32 * q) * ystride + t];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float xv = __ldg(xc + (int64_t)min(i0 + u, m - 1) * d + t);
+#pragma unroll
+                for (int q = 0; q < JN; ++q) acc[u][q] = fmaf(xv, yv[q], acc[u][q]);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const float xni = xn_c[min(i0 + u, m - 1)];
+#pragma unroll
+        for (int q = 0; q < JN; ++q) cij[u][q] = fmaxf(fmaf(-2.f, acc[u][q], xni + yn[lane + 32 * q]), 0.f);
+    }
+}
+
+// The same entries for every centroid point of a centroid, block by block
+// of 8 points, with the centroid's rows streamed through the warp's private
+// ring of LB_XS stages (8 rows x 32 dimensions each) by 16-byte asynchronous
+// copies, LB_XS - 1 stages ahead (vec layouts only).  on_block(i0, cij)
+// receives each block; every dot product is summed in dimension order, as in
+// lb_cost8.
+#define LB_XS 4
+#define LB_XSTAGE 256   // floats per ring stage
+
+__device__ __forceinline__ void lb_cp16(float* sdst, const float* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc));
+}
+
+template <int JN, typename OnBlock>
+__device__ __forceinline__ void lb_cost_stream(const float* xc, const float* xn_c, int d, int m, const float* ys,
+                                               int ystride, const float* yn, int lane, float* ring,
+                                               OnBlock&& on_block) {
+    const int nch = (d + 31) >> 5, steps = ((m + 7) >> 3) * nch;
+    auto issue = [&](int s) {
+        if (s < steps) {
+            const int ib = s / nch, ch = s - ib * nch;
+            float* st = ring + (s % LB_XS) * LB_XSTAGE;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {  // 8 rows x 8 segments of 16 bytes
+                const int e = lane + 32 * k, r = e >> 3, t = ch * 32 + (e & 7) * 4;
+                if (t < d) lb_cp16(st + r * 32 + (e & 7) * 4, xc + (int64_t)min(ib * 8 + r, m - 1) * d + t);
+            }
+        }
+        asm volatile("cp.async.commit_group;");
+    };
+#pragma unroll
+    for (int s = 0; s < LB_XS - 1; ++s) issue(s);
+    float acc[8][JN];
+    for (int s = 0; s < steps; ++s) {
+        issue(s + LB_XS - 1);  // into the stage read in step s - 1
+        asm volatile("cp.async.wait_group %0;" ::"n"(LB_XS - 1));
+        __syncwarp();
+        const int ib = s / nch, ch = s - ib * nch;
+        if (ch == 0) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int q = 0; q < JN; ++q) acc[u][q] = 0.f;
+        }
+        const float* st = ring + (s % LB_XS) * LB_XSTAGE;
+        const int tn = min(32, d - ch * 32);
+        for (int t = 0; t < tn; t += 4) {
+            float4 yv[JN];
+#pragma unroll
+            for (int q = 0; q < JN; ++q)
+                yv[q] = *reinterpret_cast<const float4*>(&ys[(lane + 32 * q) * ystride + ch * 32 + t]);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float4 xv = *reinterpret_cast<const float4*>(st + u * 32 + t);
+#pragma unroll
+                for (int q = 0; q < JN; ++q) {
+                    acc[u][q] = fmaf(xv.x, yv[q].x, acc[u][q]);
+                    acc[u][q] = fmaf(xv.y, yv[q].y, acc[u][q]);
+                    acc[u][q] = fmaf(xv.z, yv[q].z, acc[u][q]);
+                    acc[u][q] = fmaf(xv.w, yv[q].w, acc[u][q]);
+                }
+            }
+        }
+        __syncwarp();  // every lane has read the stage before it is refilled
+        if (ch == nch - 1) {
+            float cij[8][JN];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float xni = xn_c[min(ib * 8 + u, m - 1)];
+#pragma unroll
+                for (int q = 0; q < JN; ++q) cij[u][q] = fmaxf(fmaf(-2.f, acc[u][q], xni + yn[lane + 32 * q]), 0.f);
+            }
+            on_block(ib * 8, cij);
+        }
+    }
+    asm volatile("cp.async.wait_group 0;");
+    __syncwarp();
+}
+
 // One CTA per bag (grid-stride), the bag's rows in shared memory; warp w
 // bounds centroids w, w + 8, ...; lanes own bag points j = lane + 32 t.
 template <int JN>
 __global__ void __launch_bounds__(LB_WARPS * 32) k_lb_pairs(LbArgs a) {
-    extern __shared__ float lb_dyn[];
+    extern __shared__ __align__(16) float lb_dyn[];
     const int rows = 32 * JN;                             // tile rows (>= max_mk)
     float* ys = lb_dyn;                                   // rows x ystride
     float* yn = ys + (size_t)rows * a.ystride;            // rows
@@ -75,6 +210,9 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_lb_pairs(LbArgs a) {
     float* mp = uy + rows;                                // d
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int d = a.d, m = a.m, K = a.K;
+    // the warp's ring for streamed centroid rows (16-byte aligned: the host
+    // pads the tile to a multiple of 4 floats)
+    float* ring = lb_dyn + a.ring_off + (size_t)warp * LB_XS * LB_XSTAGE;
     for (int64_t bag = blockIdx.x; bag < a.N; bag += gridDim.x) {
         const int64_t r0 = a.offsets[bag];
         const int n = (int)(a.offsets[bag + 1] - r0);
@@ -102,32 +240,32 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_lb_pairs(LbArgs a) {
 #pragma unroll
             for (int q = 0; q < JN; ++q) colmin[q] = 3.0e38f;
             float lb2 = 0.f;
-            for (int i = 0; i < m; ++i) {
-                const float* xi = xc + (int64_t)i * d;
-                float dot[JN];
+            // (rows past n read zero-initialised tail rows of the tile: harmless)
+            auto on_block = [&](int i0, const float (&cij)[8][JN]) {
 #pragma unroll
-                for (int q = 0; q < JN; ++q) dot[q] = 0.f;
-                for (int t = 0; t < d; ++t) {
-                    const float xv = __ldg(xi + t);
+                for (int u = 0; u < 8; ++u) {
+                    if (i0 + u >= m) break;
+                    float rmin = 3.0e38f;
 #pragma unroll
                     for (int q = 0; q < JN; ++q) {
-                        // rows past n read zero-initialised tail rows of the tile (harmless)
-                        dot[q] = fmaf(xv, ys[(lane + 32 * q) * a.ystride + t], dot[q]);
+                        const int j = lane + 32 * q;
+                        if (j < n) {
+                            colmin[q] = fminf(colmin[q], cij[u][q]);
+                            rmin = fminf(rmin, cij[u][q]);
+                        }
                     }
+                    rmin = group_min<32>(rmin);
+                    lb2 = fmaf(a.w[(int64_t)c * m + i0 + u], rmin, lb2);
                 }
-                const float xni = a.xn[(int64_t)c * m + i];
-                float rmin = 3.0e38f;
-#pragma unroll
-                for (int q = 0; q < JN; ++q) {
-                    const int j = lane + 32 * q;
-                    if (j < n) {
-                        const float cij = fmaxf(fmaf(-2.f, dot[q], xni + yn[j]), 0.f);
-                        colmin[q] = fminf(colmin[q], cij);
-                        rmin = fminf(rmin, cij);
-                    }
+            };
+            if (a.vec) {
+                lb_cost_stream<JN>(xc, a.xn + (int64_t)c * m, d, m, ys, a.ystride, yn, lane, ring, on_block);
+            } else {
+                for (int i0 = 0; i0 < m; i0 += 8) {
+                    float cij[8][JN];
+                    lb_cost8<JN>(xc, a.xn + (int64_t)c * m, d, m, i0, ys, a.ystride, yn, lane, false, cij);
+                    on_block(i0, cij);
                 }
-                rmin = group_min<32>(rmin);
-                lb2 = fmaf(a.w[(int64_t)c * m + i], rmin, lb2);
             }
             float lb1 = 0.f;
 #pragma unroll
@@ -143,6 +281,260 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_lb_pairs(LbArgs a) {
             }
             lb3 = group_sum<32>(lb3);
             if (lane == 0) a.lb[bag * K + c] = fmaxf(fmaxf(lb1, lb2), lb3);
+        }
+    }
+}
+
+// Entropic dual bound.  The LP of Eq. (primal) has the dual
+//     max sum_i v_i f_i + sum_j u_j g_j   s.t.  f_i + g_j <= C_ij,
+// so every feasible (f, g) bounds W^2 from below.  Sinkhorn iterations of
+// the entropy-regularised problem (regularisation eps) give potentials close
+// to an optimal pair; the c-transform g'_j = min_i (C_ij - f_i) (or
+// f'_i = min_j (C_ij - g_j)) makes them feasible.  Only the final transform
+// and the two sums decide the bound's validity, so the iterations may use the
+// hardware's approximate 2^x and log2 x.  For the pairs that the bounds above
+// did not exclude, the larger of the two transformed duals replaces the
+// bound when it is larger.  One warp per (bag, centroid) pair: the pair's
+// m x m_k cost matrix in the warp's shared memory (m <= 64), potentials in
+// log2 units (F = f / (eps ln 2), G = g / (eps ln 2)), lanes owning centroid
+// points in the F update and bag points in the G update.
+#define LB_DUAL_MMAX 64
+#define LB_DUAL_KCAP 1024  // centroids listed per round of a bag
+#define LB_DUAL_ITERS 30    // Sinkhorn iterations by default (m >= 32)
+#define LB_DUAL_EPS 0.05f   // eps as a fraction of the pair's mean cost
+
+struct DualArgs {
+    const int32_t* cand;  // N x r first candidates (solved exactly)
+    const float* w2c;     // N x r their values
+    int r, iters, nw, cstride;
+    float eps_rel;
+};
+
+__device__ __forceinline__ float lb_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lb_lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <int JN>
+__global__ void __launch_bounds__(LB_WARPS * 32) k_lb_dual(LbArgs a, DualArgs da) {
+    extern __shared__ __align__(16) float lb_dyn[];
+    const int rows = 32 * JN;
+    float* ys = lb_dyn;                                   // rows x ystride
+    float* yn = ys + (size_t)rows * a.ystride;            // rows: ||y_j||^2
+    float* uy = yn + rows;                                // rows: u_j
+    float* ly = uy + rows;                                // rows: log2 u_j
+    float* wbase = ly + rows;                             // per warp below
+    __shared__ float s_thr;
+    __shared__ int s_cnt;
+    __shared__ int s_list[LB_DUAL_KCAP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int d = a.d, m = a.m, K = a.K, cs = da.cstride;
+    float* Cw = wbase + (size_t)warp * (LB_DUAL_MMAX * cs + 2 * LB_DUAL_MMAX + rows);
+    float* ring = lb_dyn + a.ring_off + (size_t)warp * LB_XS * LB_XSTAGE;
+    float* Fa = Cw + LB_DUAL_MMAX * cs;   // F_i + log2 v_i (v_i > 0), else -inf
+    float* Fs = Fa + LB_DUAL_MMAX;        // F_i
+    float* Gb = Fs + LB_DUAL_MMAX;        // G_j + log2 u_j
+    for (int64_t bag = blockIdx.x; bag < a.N; bag += gridDim.x) {
+        const int64_t r0 = a.offsets[bag];
+        const int n = (int)(a.offsets[bag + 1] - r0);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float best = 3.4e38f;
+            for (int t = 0; t < da.r; ++t) best = fminf(best, da.w2c[bag * da.r + t]);
+            s_thr = best * (1.f + LB_SLACK) + 1e-6f;
+        }
+        __syncthreads();
+        // skip the bag when none of its other centroids is left to exclude
+        int need = 0;
+        for (int c = threadIdx.x; c < K; c += blockDim.x) {
+            bool first = false;
+            for (int t = 0; t < da.r; ++t) first |= da.cand[bag * da.r + t] == c;
+            need |= !first && a.lb[bag * K + c] <= s_thr;
+        }
+        if (!__syncthreads_or(need)) continue;
+        for (int e = threadIdx.x; e < rows * d; e += blockDim.x) {
+            const int j = e / d, t = e - j * d;
+            ys[j * a.ystride + t] = j < n ? d2_row_ptr(a.supp, a.vidx, a.vocab, d, r0 + j)[t] : 0.f;
+        }
+        for (int j = threadIdx.x; j < rows; j += blockDim.x) {
+            const float u = j < n ? a.wt[r0 + j] : 0.f;
+            uy[j] = u;
+            ly[j] = u > 0.f ? lb_lg2(u) : -3.0e38f;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            float s = 0.f;
+            for (int t = 0; t < d; ++t) s = fmaf(ys[j * a.ystride + t], ys[j * a.ystride + t], s);
+            yn[j] = s;
+        }
+        __syncthreads();
+        const float thr = s_thr;
+        // the bag's pairs to bound, LB_DUAL_KCAP centroids at a time, dealt
+        // to the warps in turn (each pair's result is its own: the order in
+        // which they are listed does not matter)
+        for (int c0 = 0; c0 < K; c0 += LB_DUAL_KCAP) {
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        for (int c = c0 + threadIdx.x; c < min(K, c0 + LB_DUAL_KCAP); c += blockDim.x) {
+            bool first = false;
+            for (int t = 0; t < da.r; ++t) first |= da.cand[bag * da.r + t] == c;
+            if (!first && a.lb[bag * K + c] <= thr) s_list[atomicAdd(&s_cnt, 1)] = c;
+        }
+        __syncthreads();
+        const int cnt = s_cnt;
+        for (int li = warp; li < cnt; li += da.nw) {
+            const int c = s_list[li];
+            const float lb0 = a.lb[bag * K + c];
+            // the cost matrix, C_ij = max(||x_i||^2 + ||y_j||^2 - 2 <x_i, y_j>, 0)
+            const float* xc = a.x + (int64_t)c * m * d;
+            float csum = 0.f;
+            auto on_block = [&](int i0, const float (&cij)[8][JN]) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (i0 + u >= m) break;
+#pragma unroll
+                    for (int q = 0; q < JN; ++q) {
+                        const int j = lane + 32 * q;
+                        if (j < n) {
+                            Cw[(i0 + u) * cs + j] = cij[u][q];
+                            csum += cij[u][q];
+                        }
+                    }
+                }
+            };
+            if (a.vec) {
+                lb_cost_stream<JN>(xc, a.xn + (int64_t)c * m, d, m, ys, a.ystride, yn, lane, ring, on_block);
+            } else {
+                for (int i0 = 0; i0 < m; i0 += 8) {
+                    float cij[8][JN];
+                    lb_cost8<JN>(xc, a.xn + (int64_t)c * m, d, m, i0, ys, a.ystride, yn, lane, false, cij);
+                    on_block(i0, cij);
+                }
+            }
+            csum = group_sum<32>(csum);
+            const float eps = da.eps_rel * csum / (float)(m * n);
+            const float sc = eps > 0.f ? 1.4426950408889634f / eps : 0.f;  // 1 / (eps ln 2)
+            const float* wc = a.w + (int64_t)c * m;
+            // lanes own centroid points i = lane, lane + 32 in the F update
+            float lw[2];
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const int i = lane + 32 * p;
+                lw[p] = i < m && wc[i] > 0.f ? lb_lg2(wc[i]) : -3.0e38f;
+                if (i < m) {
+                    Fs[i] = 0.f;
+                    Fa[i] = lw[p];
+                }
+            }
+            for (int j = lane; j < rows; j += 32) Gb[j] = j < n ? ly[j] : -3.0e38f;
+            __syncwarp();
+            // Each log-sum-exp is shifted by the previous iteration's value of
+            // the same potential (its sum of powers is then near 1); a sum
+            // outside [2^-100, 2^100] is taken again with the exact maximum.
+            for (int it = 0; sc > 0.f && it < da.iters; ++it) {
+                // F_i = -log2 sum_j 2^(G_j + log2 u_j - sc C_ij)
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    const int i = lane + 32 * p;
+                    if (i < m) {
+                        const float* ci = Cw + i * cs;
+                        float sh = -Fs[i];
+                        float sum = 0.f;
+                        for (int j = 0; j < n; ++j) sum += lb_ex2(fmaf(-sc, ci[j], Gb[j]) - sh);
+                        if (!(sum >= 0x1p-100f && sum <= 0x1p100f)) {
+                            sh = -3.0e38f;
+                            for (int j = 0; j < n; ++j) sh = fmaxf(sh, fmaf(-sc, ci[j], Gb[j]));
+                            sum = 0.f;
+                            for (int j = 0; j < n; ++j) sum += lb_ex2(fmaf(-sc, ci[j], Gb[j]) - sh);
+                        }
+                        const float F = -(sh + lb_lg2(sum));
+                        Fs[i] = F;
+                        Fa[i] = lw[p] + F;
+                    }
+                }
+                __syncwarp();
+                // G_j = -log2 sum_i 2^(F_i + log2 v_i - sc C_ij) for u_j > 0:
+                // lanes take i = lane, lane + 32; a warp sum per column, four
+                // columns at a time
+                for (int j0 = 0; j0 < n; j0 += 4) {
+                    float sh[4], part[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int j = min(j0 + t, n - 1);
+                        sh[t] = -(Gb[j] - ly[j]);
+                        float v = 0.f;
+#pragma unroll
+                        for (int p = 0; p < 2; ++p) {
+                            const int i = lane + 32 * p;
+                            if (i < m) v += lb_ex2(fmaf(-sc, Cw[i * cs + j], Fa[i]) - sh[t]);
+                        }
+                        part[t] = v;
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) part[t] += __shfl_xor_sync(0xffffffffu, part[t], o);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int j = j0 + t;
+                        if (j >= n || !(uy[j] > 0.f)) continue;
+                        float sum = part[t], s2 = sh[t];
+                        // (every lane holds the sum, up to the order of its terms: decide together)
+                        if (__any_sync(0xffffffffu, !(sum >= 0x1p-100f && sum <= 0x1p100f))) {
+                            float mx = -3.0e38f;
+#pragma unroll
+                            for (int p = 0; p < 2; ++p) {
+                                const int i = lane + 32 * p;
+                                if (i < m) mx = fmaxf(mx, fmaf(-sc, Cw[i * cs + j], Fa[i]));
+                            }
+                            s2 = group_max<32>(mx);
+                            float v = 0.f;
+#pragma unroll
+                            for (int p = 0; p < 2; ++p) {
+                                const int i = lane + 32 * p;
+                                if (i < m) v += lb_ex2(fmaf(-sc, Cw[i * cs + j], Fa[i]) - s2);
+                            }
+                            sum = group_sum<32>(v);
+                        }
+                        __syncwarp();  // every lane has read Gb[j] (the shift) before it changes
+                        if (lane == 0) Gb[j] = -(s2 + lb_lg2(sum)) + ly[j];
+                    }
+                }
+                __syncwarp();
+            }
+            // both c-transforms, in cost units: f = F / sc, g = G / sc
+            const float isc = sc > 0.f ? 1.f / sc : 0.f;
+            float part_a = 0.f, part_b = 0.f;  // lane shares of the two dual objectives
+#pragma unroll
+            for (int q = 0; q < JN; ++q) {
+                const int j = lane + 32 * q;
+                if (j < n) {
+                    float g2 = 3.0e38f;
+                    for (int i = 0; i < m; ++i) g2 = fminf(g2, Cw[i * cs + j] - Fs[i] * isc);
+                    part_a = fmaf(uy[j], g2, part_a);
+                    part_b = fmaf(uy[j], (Gb[j] - ly[j]) * isc, part_b);
+                }
+            }
+            for (int i = lane; i < m; i += 32) {
+                const float* ci = Cw + i * cs;
+                float f2 = 3.0e38f;
+                for (int j = 0; j < n; ++j) f2 = fminf(f2, ci[j] - (Gb[j] - ly[j]) * isc);
+                part_a = fmaf(wc[i], Fs[i] * isc, part_a);
+                part_b = fmaf(wc[i], f2, part_b);
+            }
+            part_a = group_sum<32>(part_a);
+            part_b = group_sum<32>(part_b);
+            const float dual = fmaxf(part_a, part_b);
+            if (lane == 0 && dual > lb0 && dual < 3.0e38f) a.lb[bag * K + c] = dual;
+            __syncwarp();
+        }
+        __syncthreads();  // s_list is rebuilt for the next centroid range
         }
     }
 }
@@ -253,7 +645,7 @@ int d2_assign_bounded_impl(d2_ctx* ctx, const d2_bags* b, int K, int m, const fl
     int64_t* cnt = reinterpret_cast<int64_t*>(bb + o_cnt);
 
     // bounds for every pair
-    d2_time_begin(ctx, D2_KT_ASSIGN, st);
+    d2_time_begin(ctx, D2_KT_BOUND, st);
     k_centroid_stats<<<K, 128, 0, st>>>(K, m, d, x, w, xn, mq);
     d2_time_end(ctx, st);
     D2_LAUNCH_CK(ctx, "k_centroid_stats");
@@ -267,7 +659,12 @@ int d2_assign_bounded_impl(d2_ctx* ctx, const d2_bags* b, int K, int m, const fl
     a.m = m;
     a.K = K;
     a.nmax = b->max_mk;
-    a.ystride = d | 1;  // odd stride: lanes reading one column of consecutive rows hit distinct banks
+    // 16-byte loads when every row starts on a 16-byte boundary; the tile's row
+    // stride then a multiple of 4 floats with an odd quotient (8 consecutive
+    // lanes' 16-byte reads of one column hit distinct bank groups), else odd
+    // (lanes reading one column of consecutive rows hit distinct banks)
+    a.vec = d % 4 == 0 && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(b->supp ? b->supp : b->vocab)) & 15) == 0;
+    a.ystride = a.vec ? ((d / 4) % 2 ? d : d + 4) : (d | 1);
     a.x = x;
     a.w = w;
     a.xn = xn;
@@ -275,7 +672,8 @@ int d2_assign_bounded_impl(d2_ctx* ctx, const d2_bags* b, int K, int m, const fl
     a.lb = lb;
     a.N = N;
     const int JN = b->max_mk <= 32 ? 1 : b->max_mk <= 64 ? 2 : 4;
-    const size_t smem = ((size_t)32 * JN * a.ystride + 2 * (size_t)32 * JN + d) * 4;
+    a.ring_off = ((int64_t)32 * JN * a.ystride + 2 * 32 * JN + d + 3) & ~(int64_t)3;
+    const size_t smem = ((size_t)a.ring_off + (a.vec ? (size_t)LB_WARPS * LB_XS * LB_XSTAGE : 0)) * 4;
     if (smem > 200 * 1024) return d2_fail(ctx, D2_ENOTSUP, "bounded assignment: bag tile of %zu bytes", smem);
     const void* fn = JN == 1 ? (const void*)k_lb_pairs<1> : JN == 2 ? (const void*)k_lb_pairs<2> : (const void*)k_lb_pairs<4>;
     if (smem > 48 * 1024) D2_CK(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -283,7 +681,7 @@ int d2_assign_bounded_impl(d2_ctx* ctx, const d2_bags* b, int K, int m, const fl
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     D2_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LB_WARPS * 32, smem));
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(N, (int64_t)sms * std::max(per_sm, 1) * 4));
-    d2_time_begin(ctx, D2_KT_ASSIGN, st);
+    d2_time_begin(ctx, D2_KT_BOUND, st);
     if (JN == 1) k_lb_pairs<1><<<grid, LB_WARPS * 32, smem, st>>>(a);
     else if (JN == 2) k_lb_pairs<2><<<grid, LB_WARPS * 32, smem, st>>>(a);
     else k_lb_pairs<4><<<grid, LB_WARPS * 32, smem, st>>>(a);
@@ -298,6 +696,44 @@ int d2_assign_bounded_impl(d2_ctx* ctx, const d2_bags* b, int K, int m, const fl
     }
     if ((rc = d2_prune_solve_pairs(ctx, b, K, m, x, w, 3, N * r, nullptr, cand, r, nullptr, w2c, counters + 2, st)))
         return rc;
+    // the entropic dual bound for the pairs the cheap bounds left
+    const int iters = ctx->dual_iters >= 0 ? ctx->dual_iters : (m >= 32 ? LB_DUAL_ITERS : 0);
+    if (iters > 0 && m <= LB_DUAL_MMAX) {
+        DualArgs da;
+        da.cand = cand;
+        da.w2c = w2c;
+        da.r = r;
+        da.iters = iters;
+        da.eps_rel = ctx->dual_eps > 0.f ? ctx->dual_eps : LB_DUAL_EPS;
+        da.cstride = 32 * JN + 1;
+        const size_t tile = ((size_t)32 * JN * a.ystride + 3 * (size_t)32 * JN) * 4;
+        const size_t per_warp = ((size_t)LB_DUAL_MMAX * da.cstride + 2 * LB_DUAL_MMAX + 32 * JN +
+                                 (a.vec ? (size_t)LB_XS * LB_XSTAGE : 0)) * 4;
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+        // (less the static shared memory of the kernel and the per-CTA reserve)
+        const size_t avail = (size_t)std::max(0, optin - 1024 - (int)(LB_DUAL_KCAP * 4 + 64));
+        da.nw = avail > tile ? (int)std::min<size_t>(LB_WARPS, (avail - tile) / per_warp) : 0;
+        if (da.nw >= 1) {
+            const size_t dsm = tile + (size_t)da.nw * per_warp;
+            LbArgs ad = a;  // rings after the per-warp blocks (all sizes are multiples of 4 floats)
+            ad.ring_off = (int64_t)(tile / 4) +
+                          (int64_t)da.nw * (LB_DUAL_MMAX * da.cstride + 2 * LB_DUAL_MMAX + 32 * JN);
+            const void* dfn = JN == 1 ? (const void*)k_lb_dual<1> : JN == 2 ? (const void*)k_lb_dual<2>
+                                                                            : (const void*)k_lb_dual<4>;
+            D2_CK(ctx, cudaFuncSetAttribute(dfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+            int dper = 1;
+            D2_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dper, dfn, da.nw * 32, dsm));
+            const unsigned dgrid =
+                (unsigned)std::max<int64_t>(1, std::min<int64_t>(N, (int64_t)sms * std::max(dper, 1) * 4));
+            d2_time_begin(ctx, D2_KT_BOUND, st);
+            if (JN == 1) k_lb_dual<1><<<dgrid, da.nw * 32, dsm, st>>>(ad, da);
+            else if (JN == 2) k_lb_dual<2><<<dgrid, da.nw * 32, dsm, st>>>(ad, da);
+            else k_lb_dual<4><<<dgrid, da.nw * 32, dsm, st>>>(ad, da);
+            d2_time_end(ctx, st);
+            D2_LAUNCH_CK(ctx, "k_lb_dual");
+        }
+    }
     // every other centroid whose bound is not above the best value found
     D2_CK(ctx, cudaMemsetAsync(cnt, 0, 8, st));
     k_lb_second<<<(unsigned)d2_ceil_div(N, 8), 256, 0, st>>>(N, K, r, lb, cand, w2c, D, pb, pc, cnt);

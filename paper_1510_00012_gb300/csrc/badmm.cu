@@ -1421,7 +1421,7 @@ static int badmm_impl(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_o
                                                       static_cast<float*>(vxp));
             }
             D2_LAUNCH_CK(ctx, "k_xpartial");
-            rc = d2_fx_support(ctx, K, m, d, cw.chunk_first, static_cast<float*>(vxp), gcount, wbuf(it),
+            rc = d2_fx_support(ctx, K, m, d, cw.chunk_first, maxch, static_cast<float*>(vxp), gcount, wbuf(it),
                                xp_tc ? cw.mu : nullptr, x, fx, st);
             d2_time_end(ctx, st);
             if (rc) return rc;

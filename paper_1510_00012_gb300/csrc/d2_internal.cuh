@@ -87,6 +87,10 @@ struct d2_ctx {
     // the sparse pool's entries (0: none) -- testing and tuning
     int flow_store = 0;
     int pool_cap = 0;
+    // entropic dual bound of d2_assign_bounded: Sinkhorn iterations (-1:
+    // automatic) and eps as a fraction of the pair's mean cost (0: default)
+    int dual_iters = -1;
+    float dual_eps = 0.f;
     // split calls (D2_SPLIT_STREAMS): two child contexts, each on its own
     // stream, with the per-entry workspaces lent by this context
     d2_ctx* child[2] = {nullptr, nullptr};
@@ -256,7 +260,7 @@ int d2_fx_consensus(d2_ctx* ctx, int K, int m, const int64_t* cofs, const float*
 int d2_fx_rho(d2_ctx* ctx, int K, int m, const int64_t* chunk_first, const double* chunk_sum,
               const int64_t* chunk_rows, const int64_t* gcount, double rho0, double rho_fixed, float* rho,
               float* beta, int64_t* nrows, long long* fx, cudaStream_t st);
-int d2_fx_support(d2_ctx* ctx, int K, int m, int d, const int64_t* chunk_first, const float* xpart,
+int d2_fx_support(d2_ctx* ctx, int K, int m, int d, const int64_t* chunk_first, int64_t nseg, const float* xpart,
                   const int64_t* gcount, const float* w, const float* mu, float* x, long long* fx, cudaStream_t st);
 int d2_fx_finish(d2_ctx* ctx, int K, int m, const int64_t* cofs, const double* pos_obj, const int64_t* gcount,
                  const float* wfin, float* w_out, double* obj, long long* fx, cudaStream_t st);

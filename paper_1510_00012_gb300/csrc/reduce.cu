@@ -19,6 +19,7 @@
 //     bound on their count, so that no sum can reach 2^62.
 // Quantisation: at most 2^-(F+1) per term, i.e. below 2^-62 of the largest
 // possible sum -- far inside the FP32 rounding of the values themselves.
+#include <algorithm>
 #include <cmath>
 
 #include "d2_internal.cuh"
@@ -178,20 +179,27 @@ int d2_fx_consensus(d2_ctx* ctx, int K, int m, const int64_t* cofs, const float*
 // segments seg_first[c] .. seg_first[c + 1] - 1 (chunks or member positions)
 // ---------------------------------------------------------------------------
 
+__device__ __forceinline__ float abs_max(float acc, float v) { return fmaxf(acc, fabsf(v)); }
+__device__ __forceinline__ double abs_max(double acc, double v) { return fmax(acc, fabs(v)); }
+
+// mkey[c] = max(mkey[c], key of the largest |value| of the cluster's
+// segments); blocks (g, c), g < G, split the cluster's contiguous value range
+// (the maximum is exact in the values' own type)
 template <typename T>
-__global__ void k_fx_segmax(int K, const int64_t* seg_first, const T* vals, int64_t width, long long* mkey) {
+__global__ void k_fx_segmax(int K, const int64_t* seg_first, const T* vals, int64_t width, int G, long long* mkey) {
     __shared__ long long s_m[256];
-    const int c = blockIdx.x;
+    const int c = blockIdx.y;
     const int64_t a = seg_first[c] * width, b = seg_first[c + 1] * width;
-    double mx = 0.0;
-    for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) mx = fmax(mx, fabs((double)vals[e]));
-    s_m[threadIdx.x] = max_key(mx);
+    T mx = 0;
+    for (int64_t e = a + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < b; e += (int64_t)G * blockDim.x)
+        mx = abs_max(mx, vals[e]);
+    s_m[threadIdx.x] = max_key((double)mx);
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if ((int)threadIdx.x < o) s_m[threadIdx.x] = max(s_m[threadIdx.x], s_m[threadIdx.x + o]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) mkey[c] = s_m[0];
+    if (threadIdx.x == 0 && s_m[0] > 0) atomicMax(&mkey[c], s_m[0]);
 }
 
 __device__ __forceinline__ int64_t fx_val(float v, int F) { return fx_f32s(v, F); }
@@ -199,30 +207,47 @@ __device__ __forceinline__ int64_t fx_val(double v, int F) { return fx_f64s(v, F
 
 // out[c, e] = sum over the cluster's segments of round(vals 2^F_c), F_c from
 // the cluster's (reduced) largest magnitude and the bound `cnt_bound[c]` on
-// its number of segments
+// its number of segments; the FX_SY thread rows of a block take every
+// FX_SY-th segment (integer sums: the split does not change the result)
+#define FX_SX 128
+#define FX_SY 8
 template <typename T>
-__global__ void k_fx_segsum(int K, const int64_t* seg_first, const T* vals, int64_t width, const long long* mkey,
-                            const int64_t* cnt_bound, long long* out) {
+__global__ void __launch_bounds__(FX_SX * FX_SY) k_fx_segsum(int K, const int64_t* seg_first, const T* vals,
+                                                            int64_t width, const long long* mkey,
+                                                            const int64_t* cnt_bound, long long* out) {
+    __shared__ long long s_acc[FX_SY][FX_SX];
     const int c = blockIdx.y;
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= width) return;
+    const int64_t e = blockIdx.x * (int64_t)FX_SX + threadIdx.x;
     const int F = fx_scale(key_val(mkey[c]), cnt_bound[c]);
     long long acc = 0;
-    for (int64_t s = seg_first[c]; s < seg_first[c + 1]; ++s) acc += fx_val(vals[s * width + e], F);
-    out[(int64_t)c * width + e] = acc;
+    if (e < width)
+        for (int64_t s = seg_first[c] + threadIdx.y; s < seg_first[c + 1]; s += FX_SY)
+            acc += fx_val(vals[s * width + e], F);
+    s_acc[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && e < width) {
+        long long t = 0;
+#pragma unroll
+        for (int y = 0; y < FX_SY; ++y) t += s_acc[y][threadIdx.x];
+        out[(int64_t)c * width + e] = t;
+    }
 }
 
 // Exact per-cluster sums (K x width int64 in out, scale via fx_scale of the
 // reduced max in mkey) of segmented values, reduced across participants.
 template <typename T>
-int d2_fx_segsum(d2_ctx* ctx, int K, const int64_t* seg_first, const T* vals, int64_t width,
+int d2_fx_segsum(d2_ctx* ctx, int K, const int64_t* seg_first, const T* vals, int64_t width, int64_t nseg,
                  const int64_t* cnt_bound, long long* mkey, long long* out, cudaStream_t st) {
-    k_fx_segmax<T><<<K, 256, 0, st>>>(K, seg_first, vals, width, mkey);
+    // blocks per cluster for the maximum: about 4,096 values per block on
+    // average (the largest clusters hold far more than the average)
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(64, nseg * width / ((int64_t)K * 4096)));
+    D2_CK(ctx, cudaMemsetAsync(mkey, 0, (size_t)K * sizeof(long long), st));
+    k_fx_segmax<T><<<dim3((unsigned)G, (unsigned)K), 256, 0, st>>>(K, seg_first, vals, width, G, mkey);
     D2_LAUNCH_CK(ctx, "k_fx_segmax");
     int rc = d2_reduce(ctx, D2_REDUCE_MAX, reinterpret_cast<int64_t*>(mkey), K, st);
     if (rc) return rc;
-    dim3 g((unsigned)d2_ceil_div(width, 128), (unsigned)K);
-    k_fx_segsum<T><<<g, 128, 0, st>>>(K, seg_first, vals, width, mkey, cnt_bound, out);
+    dim3 g((unsigned)d2_ceil_div(width, FX_SX), (unsigned)K);
+    k_fx_segsum<T><<<g, dim3(FX_SX, FX_SY), 0, st>>>(K, seg_first, vals, width, mkey, cnt_bound, out);
     D2_LAUNCH_CK(ctx, "k_fx_segsum");
     return d2_reduce(ctx, D2_REDUCE_SUM, reinterpret_cast<int64_t*>(out), (int64_t)K * width, st);
 }
@@ -270,7 +295,7 @@ int d2_fx_rho(d2_ctx* ctx, int K, int m, const int64_t* chunk_first, const doubl
     int64_t* rows = reinterpret_cast<int64_t*>(fx + 2 * K);
     int rc;
     if (chunk_sum) {
-        if ((rc = d2_fx_segsum<double>(ctx, K, chunk_first, chunk_sum, 1, gcount, mkey, ssum, st))) return rc;
+        if ((rc = d2_fx_segsum<double>(ctx, K, chunk_first, chunk_sum, 1, 0, gcount, mkey, ssum, st))) return rc;
         k_fx_rows<<<(unsigned)d2_ceil_div(K, 128), 128, 0, st>>>(K, chunk_first, chunk_rows, rows);
         D2_LAUNCH_CK(ctx, "k_fx_rows");
         if ((rc = d2_reduce(ctx, D2_REDUCE_SUM, rows, K, st))) return rc;
@@ -303,12 +328,12 @@ __global__ void k_fx_xfinal(int K, int m, int d, const long long* mkey, const lo
 }
 
 // xpart: per chunk m x d FP32 partial sums; fx: K + K m d int64 of scratch
-int d2_fx_support(d2_ctx* ctx, int K, int m, int d, const int64_t* chunk_first, const float* xpart,
+int d2_fx_support(d2_ctx* ctx, int K, int m, int d, const int64_t* chunk_first, int64_t nseg, const float* xpart,
                   const int64_t* gcount, const float* w, const float* mu, float* x, long long* fx, cudaStream_t st) {
     long long* mkey = fx;
     long long* sx = fx + K;
     const int64_t width = (int64_t)m * d;
-    int rc = d2_fx_segsum<float>(ctx, K, chunk_first, xpart, width, gcount, mkey, sx, st);
+    int rc = d2_fx_segsum<float>(ctx, K, chunk_first, xpart, width, nseg, gcount, mkey, sx, st);
     if (rc) return rc;
     dim3 g((unsigned)d2_ceil_div(width, 256), (unsigned)K);
     k_fx_xfinal<<<g, 256, 0, st>>>(K, m, d, mkey, sx, gcount, w, mu, x);
@@ -341,7 +366,7 @@ int d2_fx_finish(d2_ctx* ctx, int K, int m, const int64_t* cofs, const double* p
                  const float* wfin, float* w_out, double* obj, long long* fx, cudaStream_t st) {
     long long* mkey = fx;
     long long* sobj = fx + K;
-    int rc = d2_fx_segsum<double>(ctx, K, cofs, pos_obj, 1, gcount, mkey, sobj, st);
+    int rc = d2_fx_segsum<double>(ctx, K, cofs, pos_obj, 1, 0, gcount, mkey, sobj, st);
     if (rc) return rc;
     k_fx_finish<<<(unsigned)d2_ceil_div(K, 128), 128, 0, st>>>(K, m, mkey, sobj, gcount, wfin, w_out, obj);
     D2_LAUNCH_CK(ctx, "k_fx_finish");

@@ -187,6 +187,44 @@ def test_bounded_assignment_equals_full_exact(d2, ctx, case):
     print("%s: bounded solves %d of %d" % (case, sb["exact_solves"], sf["exact_solves"]))
 
 
+@pytest.mark.parametrize("case", ["docs64", "docs32_long"])
+def test_entropic_dual_bound_keeps_the_exact_argmin(d2, ctx, case):
+    """The entropic dual bound (Sinkhorn potentials made feasible by a
+    c-transform, a lower bound of the LP of Eq. primal) excludes more pairs
+    than the cheap bounds and leaves the labels and distances of the full
+    N x K solve unchanged; merge-initialised centroids carry zero-weight
+    padding points, which the bound must handle."""
+    if case == "docs64":
+        bags = synth.document_bags(81, 400, V=3000, d=300, mk=(10, 60))
+        K, m = 16, 64
+    else:
+        bags = synth.document_bags(82, 300, V=2000, d=64, mk=(40, 120))
+        K, m = 12, 32
+    db = d2.DeviceBags.from_synth(bags)
+    g = torch.Generator().manual_seed(6)
+    ids = torch.randperm(bags.N, generator=g)[:K].cuda()
+    x, w = d2.d2_merge_init(ctx, db, ids, m)
+    lf, df_, sf = d2.d2_assign(ctx, db, x, w, want_stats=True)
+    ctx.set_dual_bound(0)
+    l0, d0, s0 = d2.d2_assign(ctx, db, x, w, want_stats=True, bounded=True)
+    ctx.set_dual_bound(-1)
+    l1, d1, s1 = d2.d2_assign(ctx, db, x, w, want_stats=True, bounded=True)
+    ctx.set_dual_bound(60, 0.02)
+    l2, d2_, s2 = d2.d2_assign(ctx, db, x, w, want_stats=True, bounded=True)
+    ctx.set_dual_bound(-1)
+    for lab, dist in ((l0, d0), (l1, d1), (l2, d2_)):
+        assert torch.equal(lf, lab)
+        assert torch.equal(df_, dist)
+    assert s1["exact_solves"] < s0["exact_solves"] < sf["exact_solves"]
+    assert s2["exact_solves"] < s0["exact_solves"]
+    print("%s: exact solves full %d, cheap bounds %d, dual bound %d (60 iterations, eps 0.02: %d)"
+          % (case, sf["exact_solves"], s0["exact_solves"], s1["exact_solves"], s2["exact_solves"]))
+    for bad in ((-2, 0.0), (10001, 0.0), (5, -1.0), (5, float("nan"))):
+        with pytest.raises(d2.D2Error) as e:
+            ctx.set_dual_bound(*bad)
+        assert e.value.code == d2.D2_EINVAL
+
+
 def test_bounded_assignment_with_pruner_candidates(d2, ctx):
     bags = synth.gaussian_class_bags(64, 400, 8, 5, mk=(4, 30), mu_sigma=2.5)
     db = d2.DeviceBags.from_synth(bags)
