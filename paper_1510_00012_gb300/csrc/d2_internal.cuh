@@ -35,6 +35,7 @@ enum WsSlot {
     WS_VOCAB_T,      // vocabulary cost table rows (<= min(n, K V) x m floats)
     WS_ASSIGN_OVF,   // exact solver: pairs whose sparse flow pool overflowed
     WS_FIXED,        // exact fixed-point reductions: counts, consensus sums, scratch
+    WS_MLP,          // pruning network forward on the tensor cores: point offsets, pooled partials
     WS_NSLOTS
 };
 
@@ -91,6 +92,9 @@ struct d2_ctx {
     // automatic) and eps as a fraction of the pair's mean cost (0: default)
     int dual_iters = -1;
     float dual_eps = 0.f;
+    // pruning network forward on the CUDA cores even where the tensor-core
+    // kernel applies (testing: the two forwards side by side)
+    int mlp_cuda_cores = 0;
     // split calls (D2_SPLIT_STREAMS): two child contexts, each on its own
     // stream, with the per-entry workspaces lent by this context
     d2_ctx* child[2] = {nullptr, nullptr};

@@ -22,6 +22,7 @@
 #include <cuda_fp16.h>
 
 #include "d2_internal.cuh"
+#include "tc_util.cuh"
 
 struct AssignArgs;
 size_t d2_assign_warp_bytes(int m, int nmax);
@@ -53,6 +54,7 @@ struct MlpArgs {
     const float* cx;   // centroids K x m x d
     const float* cw;   // K x m
     int m;
+    int max_mk;        // largest bag (bounds the point count)
     int d, H, E;
     const float* params;
     int64_t oW1, ob1, oW2, ob2, oW3;
@@ -201,6 +203,321 @@ __global__ void k_mlp_fwd(MlpArgs a) {
         for (int e = threadIdx.x; e < E; e += blockDim.x) {
             float acc = 0.f;
             for (int t = 0; t < H; ++t) acc = fmaf(__half2float(W3h[e * H + t]), sg[t], acc);
+            a.f[s * E + e] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward on the tensor cores (tcgen05 / TMEM) for d <= 128 and H <= 128.
+// The points of all slots, numbered by the slots' point offsets, are cut into
+// tiles of 128 (one per TMEM lane); a CTA (4 warps, thread = row) takes a tile
+// at a time:
+//   * the rows' centred, FP16-rounded points u_j form the A operand of layer 1
+//     (K-major, 128-byte swizzle, K = d padded to 64);
+//   * one thread issues kind::f16 MMAs (FP16 A and B, FP32 accumulator in
+//     TMEM) against W1 (H x d, K-major as stored), waits on an mbarrier;
+//   * each thread reads its row of the accumulator, adds b1, applies ReLU and
+//     the FP16 rounding and writes the A operand of layer 2, which multiplies
+//     W2 into the same TMEM columns;
+//   * the layer-2 rows (b2 added, ReLU) go through shared memory to one
+//     thread per column, which adds w_j h2_j row by row per slot: a partial sum
+//     per (slot, tile), stored at index slot + tile (a slot that continues
+//     into the next tile ends this one, so no two pairs share an index).
+// k_mlp_pool then adds each slot's partials in tile order (a fixed order) and
+// applies W3.  The products are those of the CUDA-core kernel (FP16 operands
+// are exact in FP32); only the order of the FP32 additions differs.  Every
+// mbarrier wait is bounded (about 2 s); on expiry the CTA records
+// D2F_DEV_TIMEOUT, stops, frees its tensor memory and returns.
+// ---------------------------------------------------------------------------
+#define MT_ROWS 128
+#define MT_HMAX 128
+
+struct MlpTc {
+    int nkb1, nkb2;     // K blocks of 64 halves for layer 1 (d) and layer 2 (H)
+    int pc;             // columns per pooling pass (shared stage of 128 x (pc + 1) floats)
+    uint32_t tcols;     // TMEM columns (power of 2 >= H)
+    float* part;        // (nslots + tiles) x H pooled partials
+    int* err;           // sticky device error word
+};
+
+// weighted mean of every slot, the centring of its points (FP32, point order)
+__global__ void k_mlp_mu(MlpArgs a) {
+    for (int64_t s = blockIdx.x; s < a.nslots; s += gridDim.x) {
+        const float* rows;
+        const int32_t* vrows;
+        const float* wts;
+        int cnt;
+        bool is_bag;
+        slot_source(a, s, rows, vrows, wts, cnt, is_bag);
+        for (int t = threadIdx.x; t < a.d; t += blockDim.x) {
+            float acc = 0.f;
+            for (int j = 0; j < cnt; ++j) acc = fmaf(wts[j], point_coord(a, rows, vrows, j, t), acc);
+            a.mu[s * a.d + t] = acc;
+        }
+    }
+}
+
+// exclusive prefix of the slots' point counts into pt_off (one block)
+__global__ void k_mlp_pt_scan(MlpArgs a, int64_t* pt_off) {
+    __shared__ int64_t sh[1024];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < a.nslots; b0 += 1024) {
+        const int64_t s = b0 + threadIdx.x;
+        int64_t v = 0;
+        if (s < a.nslots) {
+            const float* rows;
+            const int32_t* vrows;
+            const float* wts;
+            int cnt;
+            bool is_bag;
+            slot_source(a, s, rows, vrows, wts, cnt, is_bag);
+            v = cnt;
+        }
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            const int64_t u = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += u;
+            __syncthreads();
+        }
+        if (s < a.nslots) pt_off[s] = carry + sh[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += sh[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) pt_off[a.nslots] = carry;
+}
+
+__device__ __forceinline__ uint4 pack_half8(const float* v) {
+    uint4 u;
+    uint32_t* w = reinterpret_cast<uint32_t*>(&u);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const __half2 h = __floats2half2_rn(v[2 * q], v[2 * q + 1]);
+        w[q] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    return u;
+}
+
+__global__ void __launch_bounds__(MT_ROWS) k_mlp_fwd_tc(MlpArgs a, MlpTc t) {
+    extern __shared__ uint8_t mt_raw[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ int64_t s_slot[MT_ROWS];
+    __shared__ float s_w[MT_ROWS];
+    __shared__ float s_b1[MT_HMAX], s_b2[MT_HMAX];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int d = a.d, H = a.H;
+    // shared layout (1024-byte aligned for the swizzle): W1, W2, A1, A2 (the
+    // pooling stage reuses A2 once layer 2's MMAs have read it)
+    const uint32_t raw = smem_u32(mt_raw);
+    uint8_t* base = mt_raw + (((raw + 1023u) & ~1023u) - raw);
+    uint8_t* W1s = base;                                   // nkb1 blocks of H rows x 128 B
+    uint8_t* W2s = W1s + (size_t)t.nkb1 * H * 128;         // nkb2 blocks of H rows x 128 B
+    uint8_t* A1 = W2s + (size_t)t.nkb2 * H * 128;          // nkb1 blocks of 128 rows x 128 B
+    uint8_t* A2 = A1 + (size_t)t.nkb1 * MT_ROWS * 128;     // nkb2 blocks of 128 rows x 128 B
+    float* P = reinterpret_cast<float*>(A2);
+    const int PS = t.pc + 1;                               // odd row stride: conflict-free columns
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(t.tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&s_bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // B operands: W1 (H x d) and W2 (H x H) as FP16, K padded with zeros
+    const float* W1 = a.params + a.oW1;
+    const float* W2 = a.params + a.oW2;
+    for (int e = tid; e < H * t.nkb1 * 8; e += MT_ROWS) {
+        const int h = e / (t.nkb1 * 8), rem = e - h * (t.nkb1 * 8), kb = rem >> 3, k0 = kb * 64 + (rem & 7) * 8;
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = k0 + q < d ? W1[(int64_t)h * d + k0 + q] : 0.f;
+        *reinterpret_cast<uint4*>(W1s + (size_t)kb * H * 128 + sw128_off(h, (rem & 7) * 8)) = pack_half8(v);
+    }
+    for (int e = tid; e < H * t.nkb2 * 8; e += MT_ROWS) {
+        const int h = e / (t.nkb2 * 8), rem = e - h * (t.nkb2 * 8), kb = rem >> 3, k0 = kb * 64 + (rem & 7) * 8;
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = k0 + q < H ? W2[(int64_t)h * H + k0 + q] : 0.f;
+        *reinterpret_cast<uint4*>(W2s + (size_t)kb * H * 128 + sw128_off(h, (rem & 7) * 8)) = pack_half8(v);
+    }
+    for (int h = tid; h < H; h += MT_ROWS) {
+        s_b1[h] = hround(a.params[a.ob1 + h]);
+        s_b2[h] = hround(a.params[a.ob2 + h]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t bar = smem_u32(&s_bar);
+    const uint32_t idesc = idesc_f16_f32(MT_ROWS, H);
+    const int64_t npts = a.pt_off[a.nslots];
+    const int64_t ntiles = (npts + MT_ROWS - 1) / MT_ROWS;
+    uint32_t ph = 0;
+    bool dead = false;
+
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        // this thread's row: point p of slot s (largest s with pt_off[s] <= p)
+        const int64_t p = tile * MT_ROWS + tid;
+        const bool valid = p < npts;
+        int64_t s = -1;
+        const float* rows = nullptr;
+        const int32_t* vrows = nullptr;
+        const float* wts = nullptr;
+        int j = 0;
+        if (valid) {
+            int64_t lo = 0, hi = a.nslots - 1;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (a.pt_off[mid] <= p) lo = mid; else hi = mid - 1;
+            }
+            s = lo;
+            int cnt;
+            bool is_bag;
+            slot_source(a, s, rows, vrows, wts, cnt, is_bag);
+            j = (int)(p - a.pt_off[s]);
+        }
+        s_slot[tid] = s;
+        s_w[tid] = valid ? wts[j] : 0.f;
+        // layer 1 operand: u = half(y - mu), zero past d and for rows past the points
+        for (int kb = 0; kb < t.nkb1; ++kb)
+            for (int c8 = 0; c8 < 8; ++c8) {
+                float v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int k = kb * 64 + c8 * 8 + q;
+                    v[q] = 0.f;
+                    if (valid && k < d) {
+                        v[q] = hround(point_coord(a, rows, vrows, j, k) - a.mu[s * d + k]);
+                        if (a.pu) a.pu[p * d + k] = v[q];
+                    }
+                }
+                *reinterpret_cast<uint4*>(A1 + (size_t)kb * MT_ROWS * 128 + sw128_off(tid, c8 * 8)) = pack_half8(v);
+            }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            for (int kb = 0; kb < t.nkb1; ++kb)
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks)
+                    umma_bf16(tmem, sdesc_sw128(smem_u32(A1 + (size_t)kb * MT_ROWS * 128) + ks * 32),
+                              sdesc_sw128(smem_u32(W1s + (size_t)kb * H * 128) + ks * 32), idesc,
+                              (kb | ks) ? 1u : 0u);
+            umma_commit(bar);
+        }
+        if (!mbar_wait_bounded(bar, ph)) dead = true;
+        ph ^= 1u;
+        if (__syncthreads_or(dead)) break;
+        tc_fence_after();
+        // layer 1 epilogue: h1 = half(relu(acc + b1)) into the layer 2 operand
+        for (int cb = 0; cb < t.nkb2 * 64; cb += 16) {
+            float acc[16];
+            if (cb < H) tmem_ld16(trow + (uint32_t)cb, acc);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int col = cb + q;
+                acc[q] = col < H ? hround(fmaxf(acc[q] + s_b1[col], 0.f)) : 0.f;
+                if (valid && col < H && a.ph1) a.ph1[p * H + col] = acc[q];
+            }
+            uint8_t* blk = A2 + (size_t)(cb >> 6) * MT_ROWS * 128;
+            *reinterpret_cast<uint4*>(blk + sw128_off(tid, cb & 63)) = pack_half8(acc);
+            *reinterpret_cast<uint4*>(blk + sw128_off(tid, (cb & 63) + 8)) = pack_half8(acc + 8);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            for (int kb = 0; kb < t.nkb2; ++kb)
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks)
+                    umma_bf16(tmem, sdesc_sw128(smem_u32(A2 + (size_t)kb * MT_ROWS * 128) + ks * 32),
+                              sdesc_sw128(smem_u32(W2s + (size_t)kb * H * 128) + ks * 32), idesc,
+                              (kb | ks) ? 1u : 0u);
+            umma_commit(bar);
+        }
+        if (!mbar_wait_bounded(bar, ph)) dead = true;
+        ph ^= 1u;
+        if (__syncthreads_or(dead)) break;
+        tc_fence_after();
+        // layer 2 epilogue and pooling, pc columns at a time through shared memory
+        for (int c0 = 0; c0 < H; c0 += t.pc) {
+            const int nc = min(t.pc, H - c0);
+            for (int cb = 0; cb < nc; cb += 16) {
+                float acc[16];
+                tmem_ld16(trow + (uint32_t)(c0 + cb), acc);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int col = c0 + cb + q;
+                    if (cb + q < nc) {
+                        const float v = fmaxf(acc[q] + s_b2[col], 0.f);
+                        P[tid * PS + cb + q] = v;
+                        if (valid && a.ph2) a.ph2[p * H + col] = v;
+                    }
+                }
+            }
+            __syncthreads();
+            if (tid < nc) {
+                float acc = 0.f;
+                int64_t cur = -1;
+                for (int r = 0; r < MT_ROWS; ++r) {
+                    const int64_t sr = s_slot[r];
+                    if (sr != cur) {
+                        if (cur >= 0) t.part[(cur + tile) * H + c0 + tid] = acc;
+                        acc = 0.f;
+                        cur = sr;
+                    }
+                    if (sr >= 0) acc = fmaf(s_w[r], P[r * PS + tid], acc);
+                }
+                if (cur >= 0) t.part[(cur + tile) * H + c0 + tid] = acc;
+            }
+            __syncthreads();
+        }
+        if (valid && a.pw) a.pw[p] = s_w[tid];
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    if (dead && tid == 0) atomicOr(t.err, D2F_DEV_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(t.tcols) : "memory");
+}
+
+// per slot: g = its partials added in tile order; f = W3 half(g)
+__global__ void k_mlp_pool(MlpArgs a, const float* part) {
+    __shared__ float sg[MT_HMAX];
+    const int H = a.H, E = a.E;
+    const float* W3 = a.params + a.oW3;
+    for (int64_t s = blockIdx.x; s < a.nslots; s += gridDim.x) {
+        const int64_t p0 = a.pt_off[s], p1 = a.pt_off[s + 1];
+        for (int h = threadIdx.x; h < H; h += blockDim.x) {
+            float g = 0.f;
+            if (p1 > p0)
+                for (int64_t tile = p0 / MT_ROWS; tile <= (p1 - 1) / MT_ROWS; ++tile) g += part[(s + tile) * H + h];
+            if (a.g) a.g[s * H + h] = g;
+            sg[h] = hround(g);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < E; e += blockDim.x) {
+            float acc = 0.f;
+            for (int q = 0; q < H; ++q) acc = fmaf(hround(W3[(int64_t)e * H + q]), sg[q], acc);
             a.f[s * E + e] = acc;
         }
         __syncthreads();
@@ -420,6 +737,7 @@ static MlpArgs mlp_args(const d2_prune* p, const d2_bags* b, const float* cx, co
         a.vidx = b->vocab_idx;
         a.vocab = b->vocab;
         a.wt = b->wt;
+        a.max_mk = b->max_mk;
     }
     a.cx = cx;
     a.cw = cw;
@@ -436,7 +754,69 @@ static MlpArgs mlp_args(const d2_prune* p, const d2_bags* b, const float* cx, co
     return a;
 }
 
+// The tensor-core forward covers d <= 128 and H <= 128 (H % 32 == 0): its
+// weights and two operand tiles then fit in shared memory with room for two
+// CTAs per SM; other shapes use the CUDA-core kernel.
+static bool mlp_tc_applies(const d2_prune* p) { return p->d <= 128 && p->H <= MT_HMAX && p->H % 32 == 0; }
+
+static int launch_fwd_tc(d2_ctx* ctx, const d2_prune* p, const MlpArgs& a0, cudaStream_t st) {
+    MlpArgs a = a0;
+    const int H = p->H;
+    const int64_t maxpts = a.nbag_slots * (int64_t)a.max_mk + (a.nslots - a.nbag_slots) * (int64_t)a.m;
+    const int64_t tiles = d2_ceil_div(std::max<int64_t>(maxpts, 1), MT_ROWS);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_pt = take((size_t)(a.nslots + 1) * 8), o_part = take((size_t)(a.nslots + tiles) * H * 4);
+    void* base = nullptr;
+    int rc = d2_ws(ctx, WS_MLP, off, &base);
+    if (rc) return rc;
+    int64_t* ptoff = reinterpret_cast<int64_t*>(static_cast<char*>(base) + o_pt);
+    float* part = reinterpret_cast<float*>(static_cast<char*>(base) + o_part);
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    d2_time_begin(ctx, D2_KT_PRUNE, st);
+    if (!a.pt_off) {
+        k_mlp_pt_scan<<<1, 1024, 0, st>>>(a, ptoff);
+        D2_LAUNCH_CK(ctx, "k_mlp_pt_scan");
+        a.pt_off = ptoff;
+    }
+    const unsigned sgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(a.nslots, (int64_t)sms * 8));
+    k_mlp_mu<<<sgrid, 128, 0, st>>>(a);
+    D2_LAUNCH_CK(ctx, "k_mlp_mu");
+    MlpTc t;
+    t.nkb1 = (p->d + 63) / 64;
+    t.nkb2 = (H + 63) / 64;
+    t.pc = (t.nkb2 * 32 - 1) / 16 * 16;  // 128 rows of pc + 1 floats within the layer-2 operand
+    uint32_t cols = 32;
+    while ((int)cols < H) cols <<= 1;
+    t.tcols = cols;
+    t.part = part;
+    t.err = ctx->dev_flags + D2_DEV_ERR_WORD;
+    size_t smem = 1024 + (size_t)(t.nkb1 + t.nkb2) * H * 128 + (size_t)(t.nkb1 + t.nkb2) * MT_ROWS * 128;
+    // at most 512 / cols resident CTAs per SM (tensor memory): size the request
+    const int max_ctas = 512 / (int)cols;
+    const size_t cap_req = (size_t)228 * 1024 / (size_t)(max_ctas + 1) + 1;
+    if (max_ctas < 16 && smem < cap_req) smem = cap_req;
+    D2_CK(ctx, cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per = 1;
+    D2_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mlp_fwd_tc, MT_ROWS, smem));
+    per = std::max(1, std::min(per, max_ctas));
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * per));
+    k_mlp_fwd_tc<<<grid, MT_ROWS, smem, st>>>(a, t);
+    D2_LAUNCH_CK(ctx, "k_mlp_fwd_tc");
+    k_mlp_pool<<<sgrid, 128, 0, st>>>(a, part);
+    D2_LAUNCH_CK(ctx, "k_mlp_pool");
+    d2_time_end(ctx, st);
+    return D2_OK;
+}
+
 static int launch_fwd(d2_ctx* ctx, const d2_prune* p, const MlpArgs& a, cudaStream_t st) {
+    if (a.nslots <= 0) return D2_OK;
+    if (mlp_tc_applies(p) && !ctx->mlp_cuda_cores) return launch_fwd_tc(ctx, p, a, st);
     size_t smem = fwd_smem(p);
     if (smem > 220 * 1024) return d2_fail(ctx, D2_ENOTSUP, "pruner: d x H too large for shared memory");
     D2_CK(ctx, cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -1,7 +1,8 @@
 // Small sm_103a helpers shared by the tensor-core kernels: shared-memory
 // addresses, bounded mbarrier waits, tcgen05 fences, shared-memory matrix and
 // instruction descriptors for kind::f16 (BF16 in, FP32 accumulate), MMA issue
-// and commit, TMEM loads, and the BF16 piece split of FP32 operands.
+// and commit, TMEM loads, and the BF16 piece split of FP32 operands; the
+// FP16 instruction descriptor for the pruning network's layers.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -71,6 +72,12 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor of kind::f16: FP16 A and B (K-major), FP32 D.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// (kind::f16 covers both 16-bit input types; the instruction descriptor says which)
 __device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
     asm volatile(

@@ -323,3 +323,45 @@ def test_loss_and_gradient_elementwise(d2, ctx):
     assert caught, "the element-wise check cannot see a missing pair term"
     print("MLP element-wise: embedding %.2e, gradient blocks %s (relative to the block max)"
           % (emb_err, {k: "%.1e" % v for k, v in worst.items()}))
+
+
+@pytest.mark.parametrize("d,H,E", [(8, 32, 16), (64, 128, 64), (100, 64, 32)])
+def test_tensor_core_forward_matches_cuda_core_forward(d2, ctx, d, H, E):
+    """Layers 1 and 2 as tcgen05 GEMMs (FP16 operands, FP32 accumulation in
+    tensor memory, points of many slots packed into 128-row tiles and pooled
+    per slot) against the CUDA-core forward: the same products, other
+    addition orders, so the means are bitwise equal and the embeddings, loss
+    and gradients agree to FP16 rounding of the first hidden layer."""
+    bags = synth.gaussian_class_bags(70 + d, 300, d, 5, mk=(2, 60), mu_sigma=2.0, alpha=1.0)
+    db = d2.DeviceBags.from_synth(bags)
+    g = torch.Generator().manual_seed(d)
+    K, m = 7, 12
+    x = (torch.randn(K, m, d, generator=g) * 2.0).float().cuda()
+    w = torch.rand(K, m, generator=g) + 0.1
+    w = (w / w.sum(1, keepdim=True)).float().cuda()
+    p = d2.Pruner(ctx, d, hidden=H, embed=E, seed=d + H)
+    ids = torch.arange(bags.N, dtype=torch.int64, device="cuda")
+    pb = torch.arange(0, bags.N, 3, dtype=torch.int64, device="cuda")
+    pc = (pb % K).to(torch.int32)
+    tg = torch.rand(pb.numel(), generator=g).float().cuda() * 10.0
+    out = {}
+    for path in ("auto", "cuda_cores"):
+        ctx.set_prune_forward(path)
+        emb, mu = p.embed(db, ids)
+        loss, grad = p.loss_grad(db, x, w, pb, pc, tg)
+        torch.cuda.synchronize()
+        out[path] = (emb.cpu().double(), mu.cpu(), float(loss), grad.cpu().double())
+    ctx.set_prune_forward("auto")
+    (e1, m1, l1, g1), (e2, m2, l2, g2) = out["auto"], out["cuda_cores"]
+    assert torch.equal(m1, m2)
+    emb_err = float((e1 - e2).abs().max() / e2.abs().max())
+    assert emb_err <= 3e-3, emb_err
+    assert abs(l1 - l2) <= 3e-3 * abs(l2), (l1, l2)
+    gerr = float((g1 - g2).abs().max() / g2.abs().max())
+    assert gerr <= 1e-2, gerr
+    assert ctx.device_errors() == 0
+    print("tensor-core forward d=%d H=%d: embedding %.1e, loss %.1e, gradient %.1e (of the max)"
+          % (d, H, emb_err, abs(l1 - l2) / abs(l2), gerr))
+    with pytest.raises(d2.D2Error) as e:
+        ctx.check(d2.lib().d2_set_prune_forward(ctx.h, 2))
+    assert e.value.code == d2.D2_EINVAL
