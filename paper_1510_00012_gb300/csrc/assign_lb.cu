@@ -567,15 +567,69 @@ __global__ void k_lb_first(int64_t N, int K, int r, const float* lb, int32_t* ca
     for (int t = 0; t < r; ++t) cand[k * r + t] = bi[t];
 }
 
-// First-pass values into D (N x K, +inf elsewhere) and the pair list of every
-// other centroid whose bound does not exceed the best first-pass value.
-__global__ void k_lb_second(int64_t N, int K, int r, const float* lb, const int32_t* cand, const float* w2c,
-                            float* D, int64_t* pb, int32_t* pc, int64_t* npairs) {
+// After the dual bound: per bag, the centroid of smallest bound among those
+// not solved yet and not excluded (ties: lower index), as one extra exact
+// solve (the bound being within about 1 % of W^2 there, it is usually the
+// argmin, and its value tightens the exclusion test of every other one).
+__global__ void k_lb_next(int64_t N, int K, int r, const float* lb, const int32_t* cand, const float* w2c,
+                          int32_t* cand2, float* w2c2, int64_t* pb2, int32_t* pc2, int64_t* npairs2) {
     const int64_t k = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (k >= N) return;
     float best = 3.4e38f;
     for (int t = 0; t < r; ++t) best = fminf(best, w2c[k * r + t]);
+    const float thr = best * (1.f + LB_SLACK) + 1e-6f;
+    float bv = 3.4e38f;
+    int bi = 0x7fffffff;
+    for (int i = lane; i < K; i += 32) {
+        bool is_c = false;
+        for (int t = 0; t < r; ++t) is_c |= cand[k * r + t] == i;
+        const float v = lb[k * K + i];
+        if (!is_c && v <= thr && v < bv) {  // lanes scan ascending i: the first minimum
+            bv = v;
+            bi = i;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov < bv || (ov == bv && oi < bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    if (lane == 0) {
+        w2c2[k] = 3.4e38f;
+        cand2[k] = -1;
+        if (bi != 0x7fffffff) {
+            cand2[k] = bi;
+            const unsigned long long pos = atomicAdd(reinterpret_cast<unsigned long long*>(npairs2), 1ull);
+            pb2[pos] = k;
+            pc2[pos] = bi;
+        }
+    }
+}
+
+__global__ void k_lb_next_scatter(const int64_t* npairs2, const int64_t* pb2, const float* val2, float* w2c2) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= *npairs2) return;
+    w2c2[pb2[t]] = val2[t];
+}
+
+// First-pass values into D (N x K, +inf elsewhere) and the pair list of every
+// other centroid whose bound does not exceed the best value found (the r
+// first candidates and, when given, the extra one of k_lb_next)
+__global__ void k_lb_second(int64_t N, int K, int r, const float* lb, const int32_t* cand, const float* w2c,
+                            const int32_t* cand2, const float* w2c2, float* D, int64_t* pb, int32_t* pc,
+                            int64_t* npairs) {
+    const int64_t k = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (k >= N) return;
+    float best = 3.4e38f;
+    for (int t = 0; t < r; ++t) best = fminf(best, w2c[k * r + t]);
+    const int c2 = cand2 ? cand2[k] : -1;
+    if (c2 >= 0) best = fminf(best, w2c2[k]);
     const float thr = best * (1.f + LB_SLACK) + 1e-6f;
     for (int i = lane; i < K; i += 32) {
         bool is_c = false;
@@ -585,6 +639,10 @@ __global__ void k_lb_second(int64_t N, int K, int r, const float* lb, const int3
                 is_c = true;
                 v = w2c[k * r + t];
             }
+        if (i == c2) {
+            is_c = true;
+            v = w2c2[k];
+        }
         D[k * K + i] = v;
         if (!is_c && lb[k * K + i] <= thr) {
             const unsigned long long pos = atomicAdd(reinterpret_cast<unsigned long long*>(npairs), 1ull);
@@ -601,8 +659,8 @@ __global__ void k_scatter_list(const int64_t* npairs, const int64_t* pb, const i
     D[pb[t] * K + pc[t]] = val[t];
 }
 
-__global__ void k_lb_count(int64_t* counters, const int64_t* npairs, int64_t first) {
-    counters[0] += first + *npairs;
+__global__ void k_lb_count(int64_t* counters, const int64_t* npairs, const int64_t* npairs2, int64_t first) {
+    counters[0] += first + *npairs + (npairs2 ? *npairs2 : 0);
 }
 
 // from assign.cu
@@ -628,7 +686,8 @@ int d2_assign_bounded_impl(d2_ctx* ctx, const d2_bags* b, int K, int m, const fl
     const size_t o_lb = take((size_t)N * K * 4), o_D = take((size_t)N * K * 4), o_cand = take((size_t)N * r * 4),
                  o_w2c = take((size_t)N * r * 4), o_pb = take((size_t)N * K * 8), o_pc = take((size_t)N * K * 4),
                  o_val = take((size_t)N * K * 4), o_xn = take((size_t)K * m * 4), o_mq = take((size_t)K * d * 4),
-                 o_cnt = take(64);
+                 o_cnt = take(64), o_c2 = take((size_t)N * 4), o_w2 = take((size_t)N * 4),
+                 o_pb2 = take((size_t)N * 8), o_pc2 = take((size_t)N * 4), o_v2 = take((size_t)N * 4);
     void* base = nullptr;
     int rc = d2_ws(ctx, WS_ASSIGN, off, &base);
     if (rc) return rc;
@@ -642,7 +701,13 @@ int d2_assign_bounded_impl(d2_ctx* ctx, const d2_bags* b, int K, int m, const fl
     float* val = reinterpret_cast<float*>(bb + o_val);
     float* xn = reinterpret_cast<float*>(bb + o_xn);
     float* mq = reinterpret_cast<float*>(bb + o_mq);
-    int64_t* cnt = reinterpret_cast<int64_t*>(bb + o_cnt);
+    int64_t* cnt = reinterpret_cast<int64_t*>(bb + o_cnt);  // [0]: list, [1]: extra candidates
+    int32_t* cand2 = reinterpret_cast<int32_t*>(bb + o_c2);
+    float* w2c2 = reinterpret_cast<float*>(bb + o_w2);
+    int64_t* pb2 = reinterpret_cast<int64_t*>(bb + o_pb2);
+    int32_t* pc2 = reinterpret_cast<int32_t*>(bb + o_pc2);
+    float* val2 = reinterpret_cast<float*>(bb + o_v2);
+    bool extra = false;
 
     // bounds for every pair
     d2_time_begin(ctx, D2_KT_BOUND, st);
@@ -732,16 +797,27 @@ int d2_assign_bounded_impl(d2_ctx* ctx, const d2_bags* b, int K, int m, const fl
             else k_lb_dual<4><<<dgrid, da.nw * 32, dsm, st>>>(ad, da);
             d2_time_end(ctx, st);
             D2_LAUNCH_CK(ctx, "k_lb_dual");
+            // one more exact solve per bag: its smallest remaining bound
+            D2_CK(ctx, cudaMemsetAsync(cnt + 1, 0, 8, st));
+            k_lb_next<<<(unsigned)d2_ceil_div(N, 8), 256, 0, st>>>(N, K, r, lb, cand, w2c, cand2, w2c2, pb2, pc2,
+                                                                  cnt + 1);
+            D2_LAUNCH_CK(ctx, "k_lb_next");
+            if ((rc = d2_solve_pair_list(ctx, b, K, m, x, w, pb2, pc2, N, cnt + 1, val2, counters + 2, st)))
+                return rc;
+            k_lb_next_scatter<<<(unsigned)d2_ceil_div(N, 256), 256, 0, st>>>(cnt + 1, pb2, val2, w2c2);
+            D2_LAUNCH_CK(ctx, "k_lb_next_scatter");
+            extra = true;
         }
     }
     // every other centroid whose bound is not above the best value found
     D2_CK(ctx, cudaMemsetAsync(cnt, 0, 8, st));
-    k_lb_second<<<(unsigned)d2_ceil_div(N, 8), 256, 0, st>>>(N, K, r, lb, cand, w2c, D, pb, pc, cnt);
+    k_lb_second<<<(unsigned)d2_ceil_div(N, 8), 256, 0, st>>>(N, K, r, lb, cand, w2c, extra ? cand2 : nullptr,
+                                                               extra ? w2c2 : nullptr, D, pb, pc, cnt);
     D2_LAUNCH_CK(ctx, "k_lb_second");
     if ((rc = d2_solve_pair_list(ctx, b, K, m, x, w, pb, pc, N * K, cnt, val, counters + 2, st))) return rc;
     k_scatter_list<<<(unsigned)d2_ceil_div(N * K, 256), 256, 0, st>>>(cnt, pb, pc, val, K, D);
     D2_LAUNCH_CK(ctx, "k_scatter_list");
-    k_lb_count<<<1, 1, 0, st>>>(counters, cnt, N * r);
+    k_lb_count<<<1, 1, 0, st>>>(counters, cnt, extra ? cnt + 1 : nullptr, N * r);
     D2_LAUNCH_CK(ctx, "k_lb_count");
     return d2_argmin_rows(ctx, D, N, K, labels, dist, st);
 }
