@@ -912,6 +912,8 @@ def run_probe(args):
     bound_docs  : bounded exact assignment (certified and entropic dual
                   bounds) of 8,000 document bags against K = 64
                   merge-initialised centroids of m = 64 points;
+    mlp_embed   : the pruning network's embedding (d = 32, H = 128, E = 64) of
+                  50,000 Gaussian-class bags, tensor-core and CUDA-core forwards;
     support     : one badmm_barycenter call (T = 11, tau = 10: one support
                   update) on 256 clusters of the ragged recipe (m = 32,
                   d = 64) with the split-BF16 cost and the CUDA-core support
@@ -965,6 +967,24 @@ def run_probe(args):
                          "bound_ms": kt["bound"][0], "assign_ms": kt["assign"][0]})
         ctx.set_dual_bound(-1, 0.0)
         out.update({"pairs": N * 64, "runs": runs})
+    elif args.probe == "mlp_embed":
+        N = args.probe_n or 50000
+        bags = synth.gaussian_class_bags(3, N, 32, 64, mk=(16, 64), device=dev)
+        db = d2.DeviceBags(bags.offsets, bags.wt, bags.d, supp=bags.supp)
+        pr = d2.Pruner(ctx, 32, hidden=128, embed=64, seed=1)
+        ids = torch.arange(N, dtype=torch.int64, device=dev)
+        pr.embed(db, ids)
+        runs = {}
+        for path in ("auto", "cuda_cores"):
+            ctx.set_prune_forward(path)
+            pr.embed(db, ids)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pr.embed(db, ids)
+            torch.cuda.synchronize()
+            runs[path] = time.perf_counter() - t0
+        ctx.set_prune_forward("auto")
+        out.update({"bags": N, "points": bags.n, "s": runs})
     elif args.probe in ("support", "support_tc", "support_docs"):
         if args.probe == "support_docs":
             N, K, m = args.probe_n or 100000, 64, 64
@@ -1027,7 +1047,7 @@ def main():
                     help="one stream per call (no D2_SPLIT_STREAMS) for the timed steps")
     ap.add_argument("--no-cost-variants", action="store_true",
                     help="skip the timing of the other cost-build precisions")
-    ap.add_argument("--probe", default=None, choices=["assign_docs", "bound_docs", "support", "support_tc", "support_docs"],
+    ap.add_argument("--probe", default=None, choices=["assign_docs", "bound_docs", "mlp_embed", "support", "support_tc", "support_docs"],
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--probe-n", type=int, default=0)
     ap.add_argument("--probe-dual", default=None,

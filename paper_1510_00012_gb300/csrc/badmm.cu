@@ -1384,8 +1384,8 @@ static int badmm_impl(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_o
         D2_LAUNCH_CK(ctx, "k_sweep");
         if ((flags & SW_A) && s.w_next) {
             d2_time_begin(ctx, D2_KT_OTHER, st);
-            const int crc = d2_fx_consensus(ctx, K, m, cluster_offsets, sa.pos_part, rflag != 0, gcount, cons_sum,
-                                            s.w_next, cw.w64, st);
+            const int crc = d2_fx_consensus(ctx, K, m, cw.chunks, cw.nchunks, maxch, sa.pos_part, rflag != 0, gcount,
+                                            cons_sum, s.w_next, cw.w64, st);
             d2_time_end(ctx, st);
             if (crc) return crc;
         }

@@ -259,8 +259,9 @@ int d2_assign_sym_impl(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, c
 // per cluster over every process, then their total).
 int d2_reduce(d2_ctx* ctx, int op, int64_t* buf, int64_t count, cudaStream_t st);
 int d2_fx_counts(d2_ctx* ctx, int K, const int64_t* cofs, int64_t* gcount, cudaStream_t st);
-int d2_fx_consensus(d2_ctx* ctx, int K, int m, const int64_t* cofs, const float* pos_part, bool r2,
-                    const int64_t* gcount, long long* S, float* w_next, double* w_next64, cudaStream_t st);
+int d2_fx_consensus(d2_ctx* ctx, int K, int m, const Chunk* chunks, const int64_t* nchunks, int64_t maxch,
+                    const float* pos_part, bool r2, const int64_t* gcount, long long* S, float* w_next,
+                    double* w_next64, cudaStream_t st);
 int d2_fx_rho(d2_ctx* ctx, int K, int m, const int64_t* chunk_first, const double* chunk_sum,
               const int64_t* chunk_rows, const int64_t* gcount, double rho0, double rho_fixed, float* rho,
               float* beta, int64_t* nrows, long long* fx, cudaStream_t st);

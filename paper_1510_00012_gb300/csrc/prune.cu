@@ -802,6 +802,7 @@ static int launch_fwd_tc(d2_ctx* ctx, const d2_prune* p, const MlpArgs& a0, cuda
     const size_t cap_req = (size_t)228 * 1024 / (size_t)(max_ctas + 1) + 1;
     if (max_ctas < 16 && smem < cap_req) smem = cap_req;
     D2_CK(ctx, cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    D2_CK(ctx, cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     int per = 1;
     D2_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mlp_fwd_tc, MT_ROWS, smem));
     per = std::max(1, std::min(per, max_ctas));

@@ -101,36 +101,46 @@ int d2_fx_counts(d2_ctx* ctx, int K, const int64_t* cofs, int64_t* gcount, cudaS
 // weight consensus, Eq. (badmmw) / (badmmw2)
 // ---------------------------------------------------------------------------
 
-// S[c, i] = sum over the cluster's local members of round(part[p, i] 2^F):
-// one CTA per cluster, thread (g, i) takes the members p0 + g, p0 + g + G, ...
-#define FX_CONS_THREADS 1024
-__global__ void __launch_bounds__(FX_CONS_THREADS) k_fx_cons(const int64_t* cofs, const float* pos_part, int m,
-                                                             const int64_t* gcount, int K, long long* S) {
+// S[c, i] += sum over one chunk's member positions (<= 64, all of cluster c)
+// of round(part[p, i] 2^F): one CTA per chunk, thread (g, i) takes the
+// positions p0 + g, p0 + g + G, ...; the chunk's total is added to S by an
+// integer atomic (exact, so the order in which chunks land does not matter)
+#define FX_CONS_THREADS 128
+__global__ void __launch_bounds__(FX_CONS_THREADS) k_fx_cons(const Chunk* chunks, const int64_t* nchunks,
+                                                             const float* pos_part, int m, const int64_t* gcount,
+                                                             int K, long long* S) {
     __shared__ long long s_acc[FX_CONS_THREADS];
-    const int c = blockIdx.x;
-    const int64_t p0 = cofs[c], p1 = cofs[c + 1];
+    const int64_t q = blockIdx.x;
+    if (q >= *nchunks) return;
+    const Chunk ch = chunks[q];
     const int F = fx_cons_scale(gcount[K]);
-    const int G = FX_CONS_THREADS / m;
     const int t = threadIdx.x;
-    const int i = t % m, g = t / m;
-    long long acc = 0;
-    if (g < G) {
-        int64_t p = p0 + g;
-        for (; p + 7 * G < p1; p += 8 * G) {
-            float v[8];
+    for (int i0 = 0; i0 < m; i0 += FX_CONS_THREADS) {
+        const int mm = min(m - i0, FX_CONS_THREADS);
+        const int G = FX_CONS_THREADS / mm;
+        const int i = t % mm, g = t / mm;
+        long long acc = 0;
+        if (g < G) {
+            int64_t p = ch.p0 + g;
+            for (; p + 3 * G < ch.p1; p += 4 * G) {
+                float v[4];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = __ldcg(pos_part + (p + u * G) * m + i);
+                for (int u = 0; u < 4; ++u) v[u] = __ldcg(pos_part + (p + u * G) * m + i0 + i);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) acc += fx_f32(v[u], F);
+                for (int u = 0; u < 4; ++u) acc += fx_f32(v[u], F);
+            }
+            for (; p < ch.p1; p += G) acc += fx_f32(__ldcg(pos_part + p * m + i0 + i), F);
         }
-        for (; p < p1; p += G) acc += fx_f32(pos_part[p * m + i], F);
-    }
-    s_acc[t] = acc;
-    __syncthreads();
-    if (t < m) {
-        long long s = 0;
-        for (int h = 0; h < G; ++h) s += s_acc[h * m + t];
-        S[(int64_t)c * m + t] = s;
+        s_acc[t] = acc;
+        __syncthreads();
+        if (t < mm) {
+            long long sum = 0;
+            for (int h = 0; h < G; ++h) sum += s_acc[h * mm + t];
+            if (sum != 0)
+                atomicAdd(reinterpret_cast<unsigned long long*>(S + (int64_t)ch.c * m + i0 + t),
+                          (unsigned long long)sum);
+        }
+        __syncthreads();
     }
 }
 
@@ -162,9 +172,12 @@ __global__ void k_fx_cons_norm(int K, int m, const long long* S, const int64_t* 
     }
 }
 
-int d2_fx_consensus(d2_ctx* ctx, int K, int m, const int64_t* cofs, const float* pos_part, bool r2,
-                    const int64_t* gcount, long long* S, float* w_next, double* w_next64, cudaStream_t st) {
-    k_fx_cons<<<K, FX_CONS_THREADS, 0, st>>>(cofs, pos_part, m, gcount, K, S);
+int d2_fx_consensus(d2_ctx* ctx, int K, int m, const Chunk* chunks, const int64_t* nchunks, int64_t maxch,
+                    const float* pos_part, bool r2, const int64_t* gcount, long long* S, float* w_next,
+                    double* w_next64, cudaStream_t st) {
+    D2_CK(ctx, cudaMemsetAsync(S, 0, (size_t)K * m * sizeof(long long), st));
+    k_fx_cons<<<(unsigned)std::max<int64_t>(maxch, 1), FX_CONS_THREADS, 0, st>>>(chunks, nchunks, pos_part, m, gcount,
+                                                                              K, S);
     D2_LAUNCH_CK(ctx, "k_fx_cons");
     int rc = d2_reduce(ctx, D2_REDUCE_SUM, reinterpret_cast<int64_t*>(S), (int64_t)K * m, st);
     if (rc) return rc;
