@@ -187,7 +187,10 @@ def _d2_round_comparison(d2, ctx, dev, seed):
     bags = synth.gaussian_class_bags(seed, W["N"], W["d"], W["K"], mk=W["mk"], device=dev)
     db = d2.DeviceBags(bags.offsets, bags.wt, bags.d, supp=bags.supp)
     K, m, R = W["K"], W["m"], W["rounds"]
-    opts = d2.badmm_opts(iters=W["iters"], tau=W["tau"])
+    # the warm-up call tunes the sweep's launch shape for this plan width
+    # (kept in the context for every later batched call; the plain form's
+    # register-prefetch sweep is not tuned)
+    opts = d2.badmm_opts(iters=W["iters"], tau=W["tau"], autotune=True)
     out = {"workload": W["desc"]}
 
     def timed(fn):
@@ -197,8 +200,11 @@ def _d2_round_comparison(d2, ctx, dev, seed):
         torch.cuda.synchronize()
         return r, time.perf_counter() - t0
 
-    # batched: warm-up once, then timed
+    # batched: warm-up once (which also tunes the sweep), then timed
     d2.d2_cluster(ctx, db, K, m, 11, 1, opts)
+    tune = ctx.sweep_tuning(m)
+    if tune:
+        out["sweep_shape"] = tune["candidates"][tune["chosen"]]
     (xb, wb, lb, ob), tb = timed(lambda: d2.d2_cluster(ctx, db, K, m, 11, R, opts))
     # plain: the same rounds with one call per cluster
     nop = d2.badmm_opts(iters=W["iters"], tau=W["tau"])
