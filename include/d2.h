@@ -428,10 +428,13 @@ int d2_assign(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,
  * every (bag, centroid) pair it computes a certified lower bound on W^2:
  * the larger of the two one-sided relaxations of the LP of Eq. (primal)
  * (each bag point ships its mass to its nearest centroid point, and the
- * reverse) and ||mu_P - mu_Q||^2 (Jensen).  It solves each bag's r
- * smallest-bound centroids exactly (r = 2, or the pruner's r candidates when
- * `prune` is given), then every other centroid whose bound does not exceed
- * the best value found times (1 + 1e-4) (covering FP32 rounding).  Requires
+ * reverse) and ||mu_P - mu_Q||^2 (Jensen), and for m <= 64 where enabled
+ * the entropic dual bound (d2_set_dual_bound).  It solves each bag's r
+ * smallest-bound centroids exactly (r = 1, 2 where the dual bound runs, or
+ * the pruner's r candidates when `prune` is given), then the centroid of
+ * smallest remaining bound if that bound does not exceed the best value
+ * found, then every other centroid whose bound does not exceed the best value
+ * found times (1 + 1e-4) (covering FP32 rounding).  Requires
  * max_mk <= 128 and the conditions of d2_assign.  stats and D2_ENOCONV: as
  * for d2_assign (fall-backs stay 0). */
 int d2_assign_bounded(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m,

@@ -797,18 +797,17 @@ int d2_assign_bounded_impl(d2_ctx* ctx, const d2_bags* b, int K, int m, const fl
             else k_lb_dual<4><<<dgrid, da.nw * 32, dsm, st>>>(ad, da);
             d2_time_end(ctx, st);
             D2_LAUNCH_CK(ctx, "k_lb_dual");
-            // one more exact solve per bag: its smallest remaining bound
-            D2_CK(ctx, cudaMemsetAsync(cnt + 1, 0, 8, st));
-            k_lb_next<<<(unsigned)d2_ceil_div(N, 8), 256, 0, st>>>(N, K, r, lb, cand, w2c, cand2, w2c2, pb2, pc2,
-                                                                  cnt + 1);
-            D2_LAUNCH_CK(ctx, "k_lb_next");
-            if ((rc = d2_solve_pair_list(ctx, b, K, m, x, w, pb2, pc2, N, cnt + 1, val2, counters + 2, st)))
-                return rc;
-            k_lb_next_scatter<<<(unsigned)d2_ceil_div(N, 256), 256, 0, st>>>(cnt + 1, pb2, val2, w2c2);
-            D2_LAUNCH_CK(ctx, "k_lb_next_scatter");
-            extra = true;
         }
     }
+    // one more exact solve per bag: its smallest remaining bound, if that
+    // bound is not above the best value found so far
+    D2_CK(ctx, cudaMemsetAsync(cnt + 1, 0, 8, st));
+    k_lb_next<<<(unsigned)d2_ceil_div(N, 8), 256, 0, st>>>(N, K, r, lb, cand, w2c, cand2, w2c2, pb2, pc2, cnt + 1);
+    D2_LAUNCH_CK(ctx, "k_lb_next");
+    if ((rc = d2_solve_pair_list(ctx, b, K, m, x, w, pb2, pc2, N, cnt + 1, val2, counters + 2, st))) return rc;
+    k_lb_next_scatter<<<(unsigned)d2_ceil_div(N, 256), 256, 0, st>>>(cnt + 1, pb2, val2, w2c2);
+    D2_LAUNCH_CK(ctx, "k_lb_next_scatter");
+    extra = true;
     // every other centroid whose bound is not above the best value found
     D2_CK(ctx, cudaMemsetAsync(cnt, 0, 8, st));
     k_lb_second<<<(unsigned)d2_ceil_div(N, 8), 256, 0, st>>>(N, K, r, lb, cand, w2c, extra ? cand2 : nullptr,

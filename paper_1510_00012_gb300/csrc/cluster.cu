@@ -257,7 +257,12 @@ static int assign_any(d2_ctx* ctx, const d2_bags* bags, int32_t K, int32_t m, co
     int64_t* counters = static_cast<int64_t*>(sc);  // [0] exact solves, [1] fall-backs, [2] limit hits
     D2_CK(ctx, cudaMemsetAsync(counters, 0, 3 * sizeof(int64_t), st));
     if (bounded) {
-        int32_t r = 2;
+        // first exact solves per bag: 1, then at most one more (the smallest
+        // remaining bound) unless it is excluded; 2 up front where the
+        // entropic dual bound runs between the two (its threshold then comes
+        // from two values)
+        const int dual_iters = ctx->dual_iters >= 0 ? ctx->dual_iters : (m >= 32 ? 1 : 0);
+        int32_t r = dual_iters > 0 && m <= 64 ? 2 : 1;
         float delta = 0.f;
         if (prune) d2_prune_get_margin(prune, &r, &delta);
         rc = d2_assign_bounded_impl(ctx, bags, K, m, x, w, prune, r, labels, dist, counters, st);
