@@ -302,6 +302,7 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_lb_pairs(LbArgs a) {
 #define LB_DUAL_KCAP 1024  // centroids listed per round of a bag
 #define LB_DUAL_ITERS 30    // Sinkhorn iterations by default (m >= 32)
 #define LB_DUAL_EPS 0.05f   // eps as a fraction of the pair's mean cost
+#define LB_DUAL_CHECK 10    // iterations between checks of the bound against the threshold
 
 struct DualArgs {
     const int32_t* cand;  // N x r first candidates (solved exactly)
@@ -434,9 +435,37 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_lb_dual(LbArgs a, DualArgs da
             }
             for (int j = lane; j < rows; j += 32) Gb[j] = j < n ? ly[j] : -3.0e38f;
             __syncwarp();
+            // both c-transforms, in cost units (f = F / sc, g = G / sc): the
+            // larger dual objective (the same value on every lane)
+            auto dual_obj = [&]() -> float {
+                const float isc = sc > 0.f ? 1.f / sc : 0.f;
+                float part_a = 0.f, part_b = 0.f;  // lane shares of the two dual objectives
+#pragma unroll
+                for (int q = 0; q < JN; ++q) {
+                    const int j = lane + 32 * q;
+                    if (j < n) {
+                        float g2 = 3.0e38f;
+                        for (int i = 0; i < m; ++i) g2 = fminf(g2, Cw[i * cs + j] - Fs[i] * isc);
+                        part_a = fmaf(uy[j], g2, part_a);
+                        part_b = fmaf(uy[j], (Gb[j] - ly[j]) * isc, part_b);
+                    }
+                }
+                for (int i = lane; i < m; i += 32) {
+                    const float* ci = Cw + i * cs;
+                    float f2 = 3.0e38f;
+                    for (int j = 0; j < n; ++j) f2 = fminf(f2, ci[j] - (Gb[j] - ly[j]) * isc);
+                    part_a = fmaf(wc[i], Fs[i] * isc, part_a);
+                    part_b = fmaf(wc[i], f2, part_b);
+                }
+                part_a = group_sum<32>(part_a);
+                part_b = group_sum<32>(part_b);
+                return fmaxf(part_a, part_b);
+            };
             // Each log-sum-exp is shifted by the previous iteration's value of
             // the same potential (its sum of powers is then near 1); a sum
             // outside [2^-100, 2^100] is taken again with the exact maximum.
+            float dual = 0.f;
+            bool early = false;
             for (int it = 0; sc > 0.f && it < da.iters; ++it) {
                 // F_i = -log2 sum_j 2^(G_j + log2 u_j - sc C_ij)
 #pragma unroll
@@ -507,30 +536,16 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_lb_dual(LbArgs a, DualArgs da
                     }
                 }
                 __syncwarp();
-            }
-            // both c-transforms, in cost units: f = F / sc, g = G / sc
-            const float isc = sc > 0.f ? 1.f / sc : 0.f;
-            float part_a = 0.f, part_b = 0.f;  // lane shares of the two dual objectives
-#pragma unroll
-            for (int q = 0; q < JN; ++q) {
-                const int j = lane + 32 * q;
-                if (j < n) {
-                    float g2 = 3.0e38f;
-                    for (int i = 0; i < m; ++i) g2 = fminf(g2, Cw[i * cs + j] - Fs[i] * isc);
-                    part_a = fmaf(uy[j], g2, part_a);
-                    part_b = fmaf(uy[j], (Gb[j] - ly[j]) * isc, part_b);
+                // every LB_DUAL_CHECK iterations: stop once the pair is excluded
+                if ((it + 1) % LB_DUAL_CHECK == 0 && it + 1 < da.iters) {
+                    dual = dual_obj();
+                    if (dual > thr) {
+                        early = true;
+                        break;
+                    }
                 }
             }
-            for (int i = lane; i < m; i += 32) {
-                const float* ci = Cw + i * cs;
-                float f2 = 3.0e38f;
-                for (int j = 0; j < n; ++j) f2 = fminf(f2, ci[j] - (Gb[j] - ly[j]) * isc);
-                part_a = fmaf(wc[i], Fs[i] * isc, part_a);
-                part_b = fmaf(wc[i], f2, part_b);
-            }
-            part_a = group_sum<32>(part_a);
-            part_b = group_sum<32>(part_b);
-            const float dual = fmaxf(part_a, part_b);
+            if (!early) dual = dual_obj();
             if (lane == 0 && dual > lb0 && dual < 3.0e38f) a.lb[bag * K + c] = dual;
             __syncwarp();
         }
