@@ -221,11 +221,12 @@ int d2_set_flow_store(d2_ctx* ctx, int32_t store, int32_t pool_cap);
 
 /* Entropic dual bound of d2_assign_bounded on this context (no counterpart in
  * the paper; the argmin and its value stay those of the exact LP of Eq.
- * primal).  For every pair that the cheap bounds leave, `iters` Sinkhorn
+ * primal).  For every pair that the cheap bounds leave, up to `iters` Sinkhorn
  * iterations of the problem regularised by eps = eps_rel x the pair's mean
  * cost give dual potentials, made feasible for the dual of Eq. (primal) by a
  * c-transform; the dual objective is then a lower bound on W^2 that replaces
- * the cheap one when larger, so fewer pairs need the exact solve.  Applies
+ * the cheap one when larger, so fewer pairs need the exact solve (every 10
+ * iterations the bound is checked and the pair stops once excluded).  Applies
  * for m <= 64.  iters = -1 (default): 30 iterations when m >= 32, none below;
  * 0: off.  eps_rel = 0: the default 0.05.  Returns D2_EINVAL for iters
  * outside -1..10000 or eps_rel outside [0, 100]. */
