@@ -200,6 +200,54 @@ __device__ __forceinline__ void lb_cost_stream(const float* xc, const float* xn_
 
 // One CTA per bag (grid-stride), the bag's rows in shared memory; warp w
 // bounds centroids w, w + 8, ...; lanes own bag points j = lane + 32 t.
+// The one-sided relaxations of centroid c against the bag in the tile, with
+// JE bag-point slots per lane (JE = the smallest of 1, 2, 4 covering the bag:
+// a tile sized for the largest bag costs no lanes on a smaller one).
+template <int JE>
+__device__ __forceinline__ void lb_cheap_pair(const LbArgs& a, int c, int n, const float* ys, const float* yn,
+                                              const float* uy, int lane, float* ring, float& lb1, float& lb2) {
+    const int d = a.d, m = a.m;
+    const float* xc = a.x + (int64_t)c * m * d;
+    float colmin[JE];
+#pragma unroll
+    for (int q = 0; q < JE; ++q) colmin[q] = 3.0e38f;
+    lb2 = 0.f;
+    // (rows past n read zero-initialised tail rows of the tile: harmless)
+    auto on_block = [&](int i0, const float (&cij)[8][JE]) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (i0 + u >= m) break;
+            float rmin = 3.0e38f;
+#pragma unroll
+            for (int q = 0; q < JE; ++q) {
+                const int j = lane + 32 * q;
+                if (j < n) {
+                    colmin[q] = fminf(colmin[q], cij[u][q]);
+                    rmin = fminf(rmin, cij[u][q]);
+                }
+            }
+            rmin = group_min<32>(rmin);
+            lb2 = fmaf(a.w[(int64_t)c * m + i0 + u], rmin, lb2);
+        }
+    };
+    if (a.vec) {
+        lb_cost_stream<JE>(xc, a.xn + (int64_t)c * m, d, m, ys, a.ystride, yn, lane, ring, on_block);
+    } else {
+        for (int i0 = 0; i0 < m; i0 += 8) {
+            float cij[8][JE];
+            lb_cost8<JE>(xc, a.xn + (int64_t)c * m, d, m, i0, ys, a.ystride, yn, lane, false, cij);
+            on_block(i0, cij);
+        }
+    }
+    lb1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < JE; ++q) {
+        const int j = lane + 32 * q;
+        if (j < n) lb1 = fmaf(uy[j], colmin[q], lb1);
+    }
+    lb1 = group_sum<32>(lb1);
+}
+
 template <int JN>
 __global__ void __launch_bounds__(LB_WARPS * 32) k_lb_pairs(LbArgs a) {
     extern __shared__ __align__(16) float lb_dyn[];
@@ -235,45 +283,14 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_lb_pairs(LbArgs a) {
         }
         __syncthreads();
         for (int c = warp; c < K; c += LB_WARPS) {
-            const float* xc = a.x + (int64_t)c * m * d;
-            float colmin[JN];
-#pragma unroll
-            for (int q = 0; q < JN; ++q) colmin[q] = 3.0e38f;
-            float lb2 = 0.f;
-            // (rows past n read zero-initialised tail rows of the tile: harmless)
-            auto on_block = [&](int i0, const float (&cij)[8][JN]) {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    if (i0 + u >= m) break;
-                    float rmin = 3.0e38f;
-#pragma unroll
-                    for (int q = 0; q < JN; ++q) {
-                        const int j = lane + 32 * q;
-                        if (j < n) {
-                            colmin[q] = fminf(colmin[q], cij[u][q]);
-                            rmin = fminf(rmin, cij[u][q]);
-                        }
-                    }
-                    rmin = group_min<32>(rmin);
-                    lb2 = fmaf(a.w[(int64_t)c * m + i0 + u], rmin, lb2);
-                }
-            };
-            if (a.vec) {
-                lb_cost_stream<JN>(xc, a.xn + (int64_t)c * m, d, m, ys, a.ystride, yn, lane, ring, on_block);
+            float lb1, lb2;
+            if constexpr (JN == 1) {
+                lb_cheap_pair<1>(a, c, n, ys, yn, uy, lane, ring, lb1, lb2);
             } else {
-                for (int i0 = 0; i0 < m; i0 += 8) {
-                    float cij[8][JN];
-                    lb_cost8<JN>(xc, a.xn + (int64_t)c * m, d, m, i0, ys, a.ystride, yn, lane, false, cij);
-                    on_block(i0, cij);
-                }
+                if (n <= 32) lb_cheap_pair<1>(a, c, n, ys, yn, uy, lane, ring, lb1, lb2);
+                else if (JN == 2 || n <= 64) lb_cheap_pair<2>(a, c, n, ys, yn, uy, lane, ring, lb1, lb2);
+                else lb_cheap_pair<JN>(a, c, n, ys, yn, uy, lane, ring, lb1, lb2);
             }
-            float lb1 = 0.f;
-#pragma unroll
-            for (int q = 0; q < JN; ++q) {
-                const int j = lane + 32 * q;
-                if (j < n) lb1 = fmaf(uy[j], colmin[q], lb1);
-            }
-            lb1 = group_sum<32>(lb1);
             float lb3 = 0.f;
             for (int t = lane; t < d; t += 32) {
                 const float df = mp[t] - a.mq[(int64_t)c * d + t];
@@ -320,6 +337,40 @@ __device__ __forceinline__ float lb_lg2(float x) {
     float y;
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// The pair's cost matrix into the warp's Cw (rows cs floats apart) with JE
+// bag-point slots per lane; returns the sum of its entries (every lane).
+template <int JE>
+__device__ __forceinline__ float lb_dual_cost(const LbArgs& a, int c, int n, const float* ys, const float* yn,
+                                              int lane, float* ring, float* Cw, int cs) {
+    const int d = a.d, m = a.m;
+    const float* xc = a.x + (int64_t)c * m * d;
+    float csum = 0.f;
+    auto on_block = [&](int i0, const float (&cij)[8][JE]) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (i0 + u >= m) break;
+#pragma unroll
+            for (int q = 0; q < JE; ++q) {
+                const int j = lane + 32 * q;
+                if (j < n) {
+                    Cw[(i0 + u) * cs + j] = cij[u][q];
+                    csum += cij[u][q];
+                }
+            }
+        }
+    };
+    if (a.vec) {
+        lb_cost_stream<JE>(xc, a.xn + (int64_t)c * m, d, m, ys, a.ystride, yn, lane, ring, on_block);
+    } else {
+        for (int i0 = 0; i0 < m; i0 += 8) {
+            float cij[8][JE];
+            lb_cost8<JE>(xc, a.xn + (int64_t)c * m, d, m, i0, ys, a.ystride, yn, lane, false, cij);
+            on_block(i0, cij);
+        }
+    }
+    return group_sum<32>(csum);
 }
 
 template <int JN>
@@ -393,32 +444,14 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_lb_dual(LbArgs a, DualArgs da
             const int c = s_list[li];
             const float lb0 = a.lb[bag * K + c];
             // the cost matrix, C_ij = max(||x_i||^2 + ||y_j||^2 - 2 <x_i, y_j>, 0)
-            const float* xc = a.x + (int64_t)c * m * d;
-            float csum = 0.f;
-            auto on_block = [&](int i0, const float (&cij)[8][JN]) {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    if (i0 + u >= m) break;
-#pragma unroll
-                    for (int q = 0; q < JN; ++q) {
-                        const int j = lane + 32 * q;
-                        if (j < n) {
-                            Cw[(i0 + u) * cs + j] = cij[u][q];
-                            csum += cij[u][q];
-                        }
-                    }
-                }
-            };
-            if (a.vec) {
-                lb_cost_stream<JN>(xc, a.xn + (int64_t)c * m, d, m, ys, a.ystride, yn, lane, ring, on_block);
+            float csum;
+            if constexpr (JN == 1) {
+                csum = lb_dual_cost<1>(a, c, n, ys, yn, lane, ring, Cw, cs);
             } else {
-                for (int i0 = 0; i0 < m; i0 += 8) {
-                    float cij[8][JN];
-                    lb_cost8<JN>(xc, a.xn + (int64_t)c * m, d, m, i0, ys, a.ystride, yn, lane, false, cij);
-                    on_block(i0, cij);
-                }
+                csum = n <= 32                ? lb_dual_cost<1>(a, c, n, ys, yn, lane, ring, Cw, cs)
+                       : (JN == 2 || n <= 64) ? lb_dual_cost<2>(a, c, n, ys, yn, lane, ring, Cw, cs)
+                                              : lb_dual_cost<JN>(a, c, n, ys, yn, lane, ring, Cw, cs);
             }
-            csum = group_sum<32>(csum);
             const float eps = da.eps_rel * csum / (float)(m * n);
             const float sc = eps > 0.f ? 1.4426950408889634f / eps : 0.f;  // 1 / (eps ln 2)
             const float* wc = a.w + (int64_t)c * m;
