@@ -232,12 +232,15 @@ int d2_set_flow_store(d2_ctx* ctx, int32_t store, int32_t pool_cap);
  * outside -1..10000 or eps_rel outside [0, 100]. */
 int d2_set_dual_bound(d2_ctx* ctx, int32_t iters, float eps_rel);
 
-/* Forward of the pruning network on this context: path = 0 (default) runs
- * layers 1 and 2 as tensor-core GEMMs (tcgen05, FP16 operands, FP32
- * accumulation in tensor memory) where d <= 128 and H <= 128 with H a
- * multiple of 32, else on the CUDA cores; path = 1 always on the CUDA cores
- * (the same FP16-rounded operands; the two differ in the order of FP32
- * additions only).  Returns D2_EINVAL for another path. */
+/* Pruning network kernels on this context: path = 0 (default) runs the
+ * forward's layers 1 and 2 as tensor-core GEMMs (tcgen05, FP16 operands,
+ * FP32 accumulation in tensor memory) where d <= 128 and H <= 128 with H a
+ * multiple of 32, and the backward's weight-gradient contractions on the
+ * tensor cores (split-BF16 operands) where both sides are <= 128 wide, else
+ * on the CUDA cores; path = 1 always on the CUDA cores (the forward's
+ * operands are the same FP16-rounded values; the results differ in the order
+ * of FP32 additions and, for the gradients, by the split's 2^-16).  Returns
+ * D2_EINVAL for another path. */
 int d2_set_prune_forward(d2_ctx* ctx, int32_t path);
 
 /* Validate a bag set on the device (synchronous): offsets non-decreasing with

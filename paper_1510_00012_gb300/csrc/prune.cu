@@ -610,6 +610,175 @@ __global__ void k_chunk_reduce(const float* part, int64_t nchunk, int64_t n, flo
     out[e] = s;
 }
 
+// Weight-gradient contractions on the tensor cores: part[c] = A_c^T B_c and
+// sum_part[c] = the column sums of A_c over the OT_ROWS rows of chunk c
+// (A: R x NA, B: R x NB, row-major; NA, NB <= 128).  In both operands the
+// rows are the contraction index, so the row-major arrays are MN-major
+// operands as they stand: each 64-row K chunk is split into BF16 pieces
+// (hi + lo) element by element into the 128-byte-swizzled MN-major layout,
+// and one thread issues kind::f16 MMAs (M = 128 rows of D = columns of A,
+// zero past NA; N = NB rounded up to 64; the products hi*hi + hi*lo + lo*hi)
+// into an FP32 accumulator in tensor memory, two operand buffers alternating
+// so that the conversion of chunk k + 1 overlaps the MMAs of chunk k.  Every
+// mbarrier wait is bounded (about 2 s); on expiry the CTA records
+// D2F_DEV_TIMEOUT, stops, frees its tensor memory and returns.
+#define OT_ROWS 512
+#define OT_KC 64
+
+__device__ __forceinline__ void split_bf16x8(const float* v, uint4& hi, uint4& lo) {
+    float r[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) r[q] = v[q] - bf16_round(v[q]);
+    const uint2 h0 = pack_bf16x4(v[0], v[1], v[2], v[3]), h1 = pack_bf16x4(v[4], v[5], v[6], v[7]);
+    const uint2 l0 = pack_bf16x4(r[0], r[1], r[2], r[3]), l1 = pack_bf16x4(r[4], r[5], r[6], r[7]);
+    hi = make_uint4(h0.x, h0.y, h1.x, h1.y);
+    lo = make_uint4(l0.x, l0.y, l1.x, l1.y);
+}
+
+__global__ void __launch_bounds__(128) k_outer_tc(const float* A, int NA, const float* B, int NB, int NBp,
+                                                  int64_t R, float* part, float* sum_part, uint32_t tcols,
+                                                  int* err) {
+    extern __shared__ uint8_t ot_raw[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ float s_cs[128][9];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t raw = smem_u32(ot_raw);
+    uint8_t* base = ot_raw + (((raw + 1023u) & ~1023u) - raw);
+    const uint32_t sboA = 2048u, sboB = (uint32_t)(NBp >> 6) * 1024u;
+    const uint32_t abytes = 8u * sboA, bbytes = 8u * sboB;  // 64 K rows = 8 groups
+    const uint32_t bufbytes = 2u * (abytes + bbytes);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&s_bar[0]), 1);
+        mbar_init(smem_u32(&s_bar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t bar0 = smem_u32(&s_bar[0]);
+    const uint32_t idesc = idesc_bf16_f32_mn(128, NBp);
+    const int64_t r0 = blockIdx.x * (int64_t)OT_ROWS, r1 = min(R, r0 + OT_ROWS);
+    const int nkc = (int)((r1 - r0 + OT_KC - 1) / OT_KC);
+    float csum[8];  // column sums of A for columns 8 (tid % 16) .. + 7 over this thread's rows
+#pragma unroll
+    for (int q = 0; q < 8; ++q) csum[q] = 0.f;
+    uint32_t ph = 0u, pend = 0u;
+    bool dead = false;
+    for (int kc = 0; kc < nkc; ++kc) {
+        const int b = kc & 1;
+        if ((pend >> b) & 1u) {  // the MMAs that last read this buffer
+            if (!mbar_wait_bounded(bar0 + 8 * b, (ph >> b) & 1u)) dead = true;
+            ph ^= 1u << b;
+            pend &= ~(1u << b);
+            if (__syncthreads_or(dead)) break;
+        }
+        uint8_t* Ahi = base + (size_t)b * bufbytes;
+        uint8_t* Alo = Ahi + abytes;
+        uint8_t* Bhi = Alo + abytes;
+        uint8_t* Blo = Bhi + bbytes;
+        const int64_t rk = r0 + (int64_t)kc * OT_KC;
+        // A: 64 rows x 16 chunks of 8 columns (columns past NA are zero)
+#pragma unroll
+        for (int s8 = 0; s8 < 8; ++s8) {
+            const int e = tid + 128 * s8, kk = e >> 4, c8 = e & 15;
+            const int64_t r = rk + kk;
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int col = c8 * 8 + q;
+                v[q] = (r < r1 && col < NA) ? A[r * NA + col] : 0.f;
+                csum[q] += v[q];
+            }
+            uint4 hi, lo;
+            split_bf16x8(v, hi, lo);
+            const uint32_t off = sw128_mn_off(kk, c8 * 8, sboA);
+            *reinterpret_cast<uint4*>(Ahi + off) = hi;
+            *reinterpret_cast<uint4*>(Alo + off) = lo;
+        }
+        // B: 64 rows x NBp / 8 chunks
+        const int nbc = NBp >> 3;
+        for (int e = tid; e < OT_KC * nbc; e += 128) {
+            const int kk = e / nbc, c8 = e - kk * nbc;
+            const int64_t r = rk + kk;
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int col = c8 * 8 + q;
+                v[q] = (r < r1 && col < NB) ? B[r * NB + col] : 0.f;
+            }
+            uint4 hi, lo;
+            split_bf16x8(v, hi, lo);
+            const uint32_t off = sw128_mn_off(kk, c8 * 8, sboB);
+            *reinterpret_cast<uint4*>(Bhi + off) = hi;
+            *reinterpret_cast<uint4*>(Blo + off) = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+#pragma unroll
+            for (int ks = 0; ks < OT_KC / 16; ++ks) {  // 16 K rows = two 8-row groups
+                const uint32_t ao = (uint32_t)ks * 2u * sboA, bo = (uint32_t)ks * 2u * sboB;
+                const uint64_t ah = sdesc_sw128_mn(smem_u32(Ahi) + ao, 1024u, sboA);
+                const uint64_t al = sdesc_sw128_mn(smem_u32(Alo) + ao, 1024u, sboA);
+                const uint64_t bh = sdesc_sw128_mn(smem_u32(Bhi) + bo, 1024u, sboB);
+                const uint64_t bl = sdesc_sw128_mn(smem_u32(Blo) + bo, 1024u, sboB);
+                umma_bf16(tmem, ah, bh, idesc, (kc | ks) ? 1u : 0u);
+                umma_bf16(tmem, ah, bl, idesc, 1u);
+                umma_bf16(tmem, al, bh, idesc, 1u);
+            }
+            umma_commit(bar0 + 8 * b);
+        }
+        pend |= 1u << b;
+    }
+    // drain: no MMA may still be in flight when the accumulator is read or freed
+    for (int b = 0; b < 2; ++b) {
+        if (((pend >> b) & 1u) && !dead) {
+            if (!mbar_wait_bounded(bar0 + 8 * b, (ph >> b) & 1u)) dead = true;
+            pend &= ~(1u << b);
+        }
+    }
+    dead = __syncthreads_or(dead);
+    tc_fence_after();
+    if (!dead && nkc > 0) {
+        const int i = tid;  // row i of D = TMEM lane i = column i of A
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int cb = 0; cb < NBp; cb += 16) {
+            float v[16];
+            tmem_ld16(trow + (uint32_t)cb, v);
+            if (i < NA)
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (cb + q < NB) part[((int64_t)blockIdx.x * NA + i) * NB + cb + q] = v[q];
+        }
+    }
+    if (dead && tid == 0) atomicOr(err, D2F_DEV_TIMEOUT);
+    // column sums: the 8 threads that took column chunk c8 = tid % 16, in thread order
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s_cs[tid][q] = csum[q];
+    __syncthreads();
+    if (sum_part && tid < NA) {
+        const int c8 = tid >> 3, q = tid & 7;
+        float sv = 0.f;
+        for (int t = c8; t < 128; t += 16) sv += s_cs[t][q];
+        sum_part[(int64_t)blockIdx.x * NA + tid] = sv;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+}
+
 // per pair b: residual of ||f_a - f_q||^2 against t - ||mu_a - mu_q||^2
 __global__ void k_pair_loss(int64_t B, int E, int d, const float* f, const float* mu, int64_t nbag_slots,
                             const int32_t* pair_cent, const float* target, float* gd, double* lossb) {
@@ -835,6 +1004,28 @@ static int launch_fwd(d2_ctx* ctx, const d2_prune* p, const MlpArgs& a, cudaStre
 
 static int outer_sum(d2_ctx* ctx, const float* A, int NA, const float* B, int NB, int64_t R, float* out,
                      float* colsum, float* scratch, cudaStream_t st) {
+    if (R > 0 && NA <= 128 && NB <= 128 && !ctx->mlp_cuda_cores) {
+        // tensor cores (k_outer_tc); chunks of OT_ROWS rows, no more than the
+        // scratch's OS_ROWS chunks
+        const int64_t nch = d2_ceil_div(R, OT_ROWS);
+        float* part = scratch;
+        float* spart = scratch + nch * (int64_t)NA * NB;
+        const int NBp = (NB + 63) / 64 * 64;
+        const uint32_t tcols = (uint32_t)NBp;  // 64 or 128
+        const size_t smem = 1024 + (size_t)2 * 2 * (8 * 2048 + 8 * (NBp / 64) * 1024);
+        D2_CK(ctx, cudaFuncSetAttribute(k_outer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_outer_tc<<<(unsigned)nch, 128, smem, st>>>(A, NA, B, NB, NBp, R, part, colsum ? spart : nullptr, tcols,
+                                                     ctx->dev_flags + D2_DEV_ERR_WORD);
+        D2_LAUNCH_CK(ctx, "k_outer_tc");
+        const int64_t n = (int64_t)NA * NB;
+        k_chunk_reduce<<<(unsigned)d2_ceil_div(n, 256), 256, 0, st>>>(part, nch, n, out);
+        D2_LAUNCH_CK(ctx, "k_chunk_reduce");
+        if (colsum) {
+            k_chunk_reduce<<<(unsigned)d2_ceil_div(NA, 256), 256, 0, st>>>(spart, nch, NA, colsum);
+            D2_LAUNCH_CK(ctx, "k_chunk_reduce");
+        }
+        return D2_OK;
+    }
     const int64_t nch = std::max<int64_t>(1, d2_ceil_div(R, OS_ROWS));
     float* part = scratch;
     float* spart = scratch + nch * (int64_t)NA * NB;

@@ -67,9 +67,36 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return desc;
 }
 
+// Shared-memory matrix descriptor of an MN-major operand in the 128-byte
+// swizzle layout: atoms of 8 K rows x 64 16-bit MN elements (1 KB, each K row
+// 128 bytes), atoms along MN `lbo` bytes apart, groups of 8 K rows `sbo`
+// bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t desc = 0;
+    desc |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    desc |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    desc |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    desc |= (uint64_t)1 << 46;
+    desc |= (uint64_t)2 << 61;
+    return desc;
+}
+
+// Byte offset of element (k, mn) of an MN-major swizzled operand with MN
+// atoms 1 KB apart and 8-row K groups `sbo` bytes apart (the 16-byte chunks
+// of a 128-byte row are exchanged by k mod 8, as in the K-major layout).
+__device__ __forceinline__ uint32_t sw128_mn_off(int k, int mn, uint32_t sbo) {
+    return (uint32_t)(k >> 3) * sbo + (uint32_t)(mn >> 6) * 1024u + (uint32_t)(k & 7) * 128u +
+           ((((uint32_t)(mn & 63) >> 3) ^ (uint32_t)(k & 7)) << 4) + (uint32_t)(mn & 7) * 2u;
+}
+
 // Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B, both MN-major, FP32 D.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N) {
+    return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
 }
 
 // Instruction descriptor of kind::f16: FP16 A and B (K-major), FP32 D.

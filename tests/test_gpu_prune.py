@@ -329,9 +329,11 @@ def test_loss_and_gradient_elementwise(d2, ctx):
 def test_tensor_core_forward_matches_cuda_core_forward(d2, ctx, d, H, E):
     """Layers 1 and 2 as tcgen05 GEMMs (FP16 operands, FP32 accumulation in
     tensor memory, points of many slots packed into 128-row tiles and pooled
-    per slot) against the CUDA-core forward: the same products, other
-    addition orders, so the means are bitwise equal and the embeddings, loss
-    and gradients agree to FP16 rounding of the first hidden layer."""
+    per slot) and the weight-gradient contractions as tcgen05 GEMMs on
+    MN-major split-BF16 operands, against the CUDA-core forward and backward:
+    the same products up to the split's 2^-16, other addition orders, so the
+    means are bitwise equal and the embeddings, loss and gradients agree to
+    FP16 rounding of the first hidden layer."""
     bags = synth.gaussian_class_bags(70 + d, 300, d, 5, mk=(2, 60), mu_sigma=2.0, alpha=1.0)
     db = d2.DeviceBags.from_synth(bags)
     g = torch.Generator().manual_seed(d)
