@@ -1342,6 +1342,7 @@ static int badmm_impl(d2_ctx* ctx, const d2_bags* bags, const int64_t* cluster_o
     int rc = D2_OK;
     if ((rc = d2_setup_clusters(ctx, cluster_offsets, P, K, &pos_cluster, &cw, st))) return rc;
     if ((rc = d2_fx_counts(ctx, K, cluster_offsets, gcount, st))) return rc;
+    D2_CK(ctx, cudaMemsetAsync(cons_sum, 0, (size_t)K * m * sizeof(long long), st));
     D2_CK(ctx, cudaMemsetAsync(cw.counters, 0, (size_t)K * 4, st));
     D2_CK(ctx, cudaMemcpyAsync(cw.wb[0], w, (size_t)K * m * 4, cudaMemcpyDeviceToDevice, st));
     // initial cost and rho (Eq. rho)

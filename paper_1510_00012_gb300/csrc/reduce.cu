@@ -146,16 +146,17 @@ __global__ void __launch_bounds__(FX_CONS_THREADS) k_fx_cons(const Chunk* chunks
 
 // w_i = S_i / sum S (R1) or S_i^2 / sum S^2 (R2) of every cluster with members
 // (on any participant); FP64, then FP32
-__global__ void k_fx_cons_norm(int K, int m, const long long* S, const int64_t* gcount, bool r2, float* w_next,
+__global__ void k_fx_cons_norm(int K, int m, long long* S, const int64_t* gcount, bool r2, float* w_next,
                                double* w_next64) {
     __shared__ double s_v[256];
     __shared__ double s_tot;
     const int c = blockIdx.x;
-    if (gcount[c] == 0) return;  // no member anywhere: weights unchanged
+    if (gcount[c] == 0) return;  // no member anywhere: weights unchanged (its sums stay 0)
     const int F = fx_cons_scale(gcount[K]);
     const int t = threadIdx.x;
     if (t < m) {
         const double v = ldexp((double)S[(int64_t)c * m + t], -F);
+        S[(int64_t)c * m + t] = 0;  // cleared for the next iteration's atomics
         s_v[t] = r2 ? v * v : v;
     }
     __syncthreads();
@@ -175,7 +176,8 @@ __global__ void k_fx_cons_norm(int K, int m, const long long* S, const int64_t* 
 int d2_fx_consensus(d2_ctx* ctx, int K, int m, const Chunk* chunks, const int64_t* nchunks, int64_t maxch,
                     const float* pos_part, bool r2, const int64_t* gcount, long long* S, float* w_next,
                     double* w_next64, cudaStream_t st) {
-    D2_CK(ctx, cudaMemsetAsync(S, 0, (size_t)K * m * sizeof(long long), st));
+    // S is zero here: cleared at the start of the B-ADMM call and by each
+    // normalisation after it has read the sums
     k_fx_cons<<<(unsigned)std::max<int64_t>(maxch, 1), FX_CONS_THREADS, 0, st>>>(chunks, nchunks, pos_part, m, gcount,
                                                                               K, S);
     D2_LAUNCH_CK(ctx, "k_fx_cons");
