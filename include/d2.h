@@ -232,6 +232,15 @@ int d2_set_flow_store(d2_ctx* ctx, int32_t store, int32_t pool_cap);
  * outside -1..10000 or eps_rel outside [0, 100]. */
 int d2_set_dual_bound(d2_ctx* ctx, int32_t iters, float eps_rel);
 
+/* Cheap lower bounds of d2_assign_bounded on this context: path = 0 (default)
+ * computes their cost entries as tensor-core contractions (tcgen05, split-
+ * BF16 operands, FP32 accumulation; each bound lowered by a bound on the
+ * products' error, so it stays below W^2) for bags of <= 64 points,
+ * 32 <= d <= 320 and m dividing 128 (m >= 16), else on the CUDA cores;
+ * path = 1 always on the CUDA cores.  The labels and distances are the exact
+ * ones either way.  Returns D2_EINVAL for another path. */
+int d2_set_bound_kernels(d2_ctx* ctx, int32_t path);
+
 /* Pruning network kernels on this context: path = 0 (default) runs the
  * forward's layers 1 and 2 as tensor-core GEMMs (tcgen05, FP16 operands,
  * FP32 accumulation in tensor memory) where d <= 128 and H <= 128 with H a

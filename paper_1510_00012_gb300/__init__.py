@@ -71,6 +71,7 @@ _SIGS = {
     "d2_set_flow_store": (c_int, [c_void_p, c_int32, c_int32]),
     "d2_set_dual_bound": (c_int, [c_void_p, c_int32, c_float]),
     "d2_set_prune_forward": (c_int, [c_void_p, c_int32]),
+    "d2_set_bound_kernels": (c_int, [c_void_p, c_int32]),
     "d2_set_reducer": (c_int, [c_void_p, c_void_p, c_void_p]),
     "d2_sweep_tuning": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "d2_cluster_stats": (c_int, [c_void_p, c_void_p]),
@@ -242,6 +243,11 @@ class Context:
         pair (-1: automatic, 0: off) and eps as a fraction of the pair's mean
         cost (0: default)."""
         self.check(lib().d2_set_dual_bound(self.h, int(iters), float(eps_rel)))
+
+    def set_bound_kernels(self, path="auto"):
+        """Cheap bounds of the bounded assignment: "auto" (tensor cores where
+        they apply) or "cuda_cores"."""
+        self.check(lib().d2_set_bound_kernels(self.h, {"auto": 0, "cuda_cores": 1}[path]))
 
     def set_prune_forward(self, path="auto"):
         """Pruning network forward: "auto" (tensor cores where they apply) or

@@ -190,6 +190,12 @@ extern "C" int d2_set_flow_store(d2_ctx* ctx, int32_t store, int32_t pool_cap) {
     return D2_OK;
 }
 
+extern "C" int d2_set_bound_kernels(d2_ctx* ctx, int32_t path) {
+    if (!ctx || path < 0 || path > 1) return D2_EINVAL;
+    ctx->bound_cuda_cores = path;
+    return D2_OK;
+}
+
 extern "C" int d2_set_prune_forward(d2_ctx* ctx, int32_t path) {
     if (!ctx || path < 0 || path > 1) return D2_EINVAL;
     ctx->mlp_cuda_cores = path;

@@ -711,6 +711,10 @@ __global__ void k_lb_count(int64_t* counters, const int64_t* npairs, const int64
     counters[0] += first + *npairs + (npairs2 ? *npairs2 : 0);
 }
 
+// from assign_lb_tc.cu
+int d2_lb_pairs_tc(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w, const float* xn,
+                   const float* mq, float* lb, cudaStream_t st, bool* used);
+
 // from assign.cu
 int d2_argmin_rows(d2_ctx* ctx, const float* D, int64_t N, int K, int32_t* labels, float* dist, cudaStream_t st);
 int d2_prune_solve_pairs(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, const float* w, int mode,
@@ -792,14 +796,20 @@ int d2_assign_bounded_impl(d2_ctx* ctx, const d2_bags* b, int K, int m, const fl
     if (smem > 48 * 1024) D2_CK(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int sms = 152, per_sm = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    D2_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LB_WARPS * 32, smem));
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(N, (int64_t)sms * std::max(per_sm, 1) * 4));
-    d2_time_begin(ctx, D2_KT_BOUND, st);
-    if (JN == 1) k_lb_pairs<1><<<grid, LB_WARPS * 32, smem, st>>>(a);
-    else if (JN == 2) k_lb_pairs<2><<<grid, LB_WARPS * 32, smem, st>>>(a);
-    else k_lb_pairs<4><<<grid, LB_WARPS * 32, smem, st>>>(a);
-    d2_time_end(ctx, st);
-    D2_LAUNCH_CK(ctx, "k_lb_pairs");
+    // the cost entries on the tensor cores where that kernel applies
+    bool tc_bounds = false;
+    if ((rc = d2_lb_pairs_tc(ctx, b, K, m, x, w, xn, mq, lb, st, &tc_bounds))) return rc;
+    if (!tc_bounds) {
+        D2_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LB_WARPS * 32, smem));
+        const unsigned grid =
+            (unsigned)std::max<int64_t>(1, std::min<int64_t>(N, (int64_t)sms * std::max(per_sm, 1) * 4));
+        d2_time_begin(ctx, D2_KT_BOUND, st);
+        if (JN == 1) k_lb_pairs<1><<<grid, LB_WARPS * 32, smem, st>>>(a);
+        else if (JN == 2) k_lb_pairs<2><<<grid, LB_WARPS * 32, smem, st>>>(a);
+        else k_lb_pairs<4><<<grid, LB_WARPS * 32, smem, st>>>(a);
+        d2_time_end(ctx, st);
+        D2_LAUNCH_CK(ctx, "k_lb_pairs");
+    }
     // first candidates: the pruner's r, else the r smallest bounds
     if (prune) {
         if ((rc = d2_prune_candidates(ctx, b, K, m, x, w, prune, r, cand, st))) return rc;

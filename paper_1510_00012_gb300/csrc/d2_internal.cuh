@@ -36,6 +36,7 @@ enum WsSlot {
     WS_ASSIGN_OVF,   // exact solver: pairs whose sparse flow pool overflowed
     WS_FIXED,        // exact fixed-point reductions: counts, consensus sums, scratch
     WS_MLP,          // pruning network forward on the tensor cores: point offsets, pooled partials
+    WS_LBTC,         // bounded assignment: centroid points as tensor-core tiles, their largest norms
     WS_NSLOTS
 };
 
@@ -95,6 +96,9 @@ struct d2_ctx {
     // pruning network forward on the CUDA cores even where the tensor-core
     // kernel applies (testing: the two forwards side by side)
     int mlp_cuda_cores = 0;
+    // cheap bounds of the bounded assignment on the CUDA cores even where the
+    // tensor-core kernel applies (testing: the two side by side)
+    int bound_cuda_cores = 0;
     // split calls (D2_SPLIT_STREAMS): two child contexts, each on its own
     // stream, with the per-entry workspaces lent by this context
     d2_ctx* child[2] = {nullptr, nullptr};

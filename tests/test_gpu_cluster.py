@@ -225,6 +225,49 @@ def test_entropic_dual_bound_keeps_the_exact_argmin(d2, ctx, case):
         assert e.value.code == d2.D2_EINVAL
 
 
+@pytest.mark.parametrize("case", ["docs300_m64", "gauss32_m32", "gauss48_m16"])
+def test_tensor_core_bounds_keep_the_exact_argmin(d2, ctx, case):
+    """The cheap bounds with their cost entries on the tensor cores (split
+    BF16, each bound lowered by the products' error bound) exclude as many
+    LPs as the CUDA-core bounds, up to that margin, and the labels and
+    distances stay those of the full N x K solve."""
+    if case == "docs300_m64":
+        bags = synth.document_bags(91, 500, V=4000, d=300, mk=(10, 60))
+        K, m = 20, 64
+    elif case == "gauss32_m32":
+        bags = synth.gaussian_class_bags(92, 600, 32, 12, mk=(4, 64), mu_sigma=2.0)
+        K, m = 12, 32
+    else:
+        bags = synth.gaussian_class_bags(93, 400, 48, 9, mk=(2, 40), mu_sigma=1.5)
+        K, m = 9, 16
+    db = d2.DeviceBags.from_synth(bags)
+    g = torch.Generator().manual_seed(7)
+    ids = torch.randperm(bags.N, generator=g)[:K].cuda()
+    x, w = d2.d2_merge_init(ctx, db, ids, m)
+    lf, df_, sf = d2.d2_assign(ctx, db, x, w, want_stats=True)
+    out = {}
+    for path in ("cuda_cores", "auto"):
+        ctx.set_bound_kernels(path)
+        for dual in (0, -1):
+            ctx.set_dual_bound(dual)
+            lab, dist, st = d2.d2_assign(ctx, db, x, w, want_stats=True, bounded=True)
+            assert torch.equal(lf, lab), (path, dual)
+            assert torch.equal(df_, dist), (path, dual)
+            out[path, dual] = st["exact_solves"]
+    ctx.set_bound_kernels("auto")
+    ctx.set_dual_bound(-1)
+    assert ctx.device_errors() == 0
+    for dual in (0, -1):
+        assert out["auto", dual] <= 1.02 * out["cuda_cores", dual] + 2, out
+        assert out["auto", dual] < sf["exact_solves"]
+    print("%s: exact solves full %d; cheap bounds CUDA cores %d, tensor cores %d; with the dual bound %d, %d"
+          % (case, sf["exact_solves"], out["cuda_cores", 0], out["auto", 0], out["cuda_cores", -1],
+             out["auto", -1]))
+    with pytest.raises(d2.D2Error) as e:
+        ctx.check(d2.lib().d2_set_bound_kernels(ctx.h, 2))
+    assert e.value.code == d2.D2_EINVAL
+
+
 def test_bounded_assignment_with_pruner_candidates(d2, ctx):
     bags = synth.gaussian_class_bags(64, 400, 8, 5, mk=(4, 30), mu_sigma=2.5)
     db = d2.DeviceBags.from_synth(bags)
