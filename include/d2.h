@@ -236,7 +236,7 @@ int d2_set_dual_bound(d2_ctx* ctx, int32_t iters, float eps_rel);
  * computes their cost entries as tensor-core contractions (tcgen05, split-
  * BF16 operands, FP32 accumulation; each bound lowered by a bound on the
  * products' error, so it stays below W^2) for bags of <= 64 points,
- * 32 <= d <= 320 and m dividing 128 (m >= 16), else on the CUDA cores;
+ * 64 <= d <= 320 and m dividing 128 (m >= 16), else on the CUDA cores;
  * path = 1 always on the CUDA cores.  The labels and distances are the exact
  * ones either way.  Returns D2_EINVAL for another path. */
 int d2_set_bound_kernels(d2_ctx* ctx, int32_t path);

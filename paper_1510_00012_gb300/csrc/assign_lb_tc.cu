@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(128) k_lb_pairs_tc(LtArgs a) {
 }  // namespace
 
 // The cheap lower bounds of every (bag, centroid) pair into lb (N x K) on the
-// tensor cores, for bags of <= 64 points, 32 <= d <= 320 and m dividing 128
+// tensor cores, for bags of <= 64 points, 64 <= d <= 320 and m dividing 128
 // (16 <= m <= 128); *used = false (and nothing launched) otherwise, or when
 // the context asks for the CUDA-core bounds.  xn and mq as from
 // k_centroid_stats.
@@ -304,7 +304,8 @@ int d2_lb_pairs_tc(d2_ctx* ctx, const d2_bags* b, int K, int m, const float* x, 
                    const float* mq, float* lb, cudaStream_t st, bool* used) {
     *used = false;
     const int d = b->d;
-    if (ctx->bound_cuda_cores || b->max_mk > LT_N || m < 16 || m > LT_M || LT_M % m != 0 || d < 32 ||
+    // (below d = 64 the CUDA-core dot products cost less than the tile schedule)
+    if (ctx->bound_cuda_cores || b->max_mk > LT_N || m < 16 || m > LT_M || LT_M % m != 0 || d < 64 ||
         d > 64 * LT_KBMAX || b->N < 1)
         return D2_OK;
     const int nkb = (d + 63) / 64;

@@ -225,7 +225,7 @@ def test_entropic_dual_bound_keeps_the_exact_argmin(d2, ctx, case):
         assert e.value.code == d2.D2_EINVAL
 
 
-@pytest.mark.parametrize("case", ["docs300_m64", "gauss32_m32", "gauss48_m16"])
+@pytest.mark.parametrize("case", ["docs300_m64", "gauss64_m32", "gauss96_m16"])
 def test_tensor_core_bounds_keep_the_exact_argmin(d2, ctx, case):
     """The cheap bounds with their cost entries on the tensor cores (split
     BF16, each bound lowered by the products' error bound) exclude as many
@@ -234,11 +234,11 @@ def test_tensor_core_bounds_keep_the_exact_argmin(d2, ctx, case):
     if case == "docs300_m64":
         bags = synth.document_bags(91, 500, V=4000, d=300, mk=(10, 60))
         K, m = 20, 64
-    elif case == "gauss32_m32":
-        bags = synth.gaussian_class_bags(92, 600, 32, 12, mk=(4, 64), mu_sigma=2.0)
+    elif case == "gauss64_m32":
+        bags = synth.gaussian_class_bags(92, 600, 64, 12, mk=(4, 64), mu_sigma=1.0)
         K, m = 12, 32
     else:
-        bags = synth.gaussian_class_bags(93, 400, 48, 9, mk=(2, 40), mu_sigma=1.5)
+        bags = synth.gaussian_class_bags(93, 400, 96, 9, mk=(2, 40), mu_sigma=0.7)
         K, m = 9, 16
     db = d2.DeviceBags.from_synth(bags)
     g = torch.Generator().manual_seed(7)
