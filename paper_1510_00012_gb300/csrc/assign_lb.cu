@@ -122,14 +122,24 @@ __device__ __forceinline__ void lb_cost8(const float* xc, const float* xn_c, int
 // of 8 points, with the centroid's rows streamed through the warp's private
 // ring of LB_XS stages (8 rows x 32 dimensions each) by 16-byte asynchronous
 // copies, LB_XS - 1 stages ahead (vec layouts only).  on_block(i0, cij)
-// receives each block; every dot product is summed in dimension order, as in
-// lb_cost8.
+// receives each block.  Each dot product is taken as two partial sums, of
+// the even and of the odd dimensions (each in dimension order, by paired
+// FP32 fused multiply-adds on adjacent dimensions), added at the end.
 #define LB_XS 4
 #define LB_XSTAGE 256   // floats per ring stage
 
 __device__ __forceinline__ void lb_cp16(float* sdst, const float* gsrc) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc));
+}
+
+__device__ __forceinline__ void lb_fma2(unsigned long long& acc, unsigned long long a, unsigned long long b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ float lb_hsum2(unsigned long long v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return lo + hi;
 }
 
 template <int JN, typename OnBlock>
@@ -151,7 +161,7 @@ __device__ __forceinline__ void lb_cost_stream(const float* xc, const float* xn_
     };
 #pragma unroll
     for (int s = 0; s < LB_XS - 1; ++s) issue(s);
-    float acc[8][JN];
+    unsigned long long acc[8][JN];  // (even, odd) dimension partial sums
     for (int s = 0; s < steps; ++s) {
         issue(s + LB_XS - 1);  // into the stage read in step s - 1
         asm volatile("cp.async.wait_group %0;" ::"n"(LB_XS - 1));
@@ -161,24 +171,22 @@ __device__ __forceinline__ void lb_cost_stream(const float* xc, const float* xn_
 #pragma unroll
             for (int u = 0; u < 8; ++u)
 #pragma unroll
-                for (int q = 0; q < JN; ++q) acc[u][q] = 0.f;
+                for (int q = 0; q < JN; ++q) acc[u][q] = 0ull;
         }
         const float* st = ring + (s % LB_XS) * LB_XSTAGE;
         const int tn = min(32, d - ch * 32);
         for (int t = 0; t < tn; t += 4) {
-            float4 yv[JN];
+            ulonglong2 yv[JN];  // dimensions (t, t + 1), (t + 2, t + 3)
 #pragma unroll
             for (int q = 0; q < JN; ++q)
-                yv[q] = *reinterpret_cast<const float4*>(&ys[(lane + 32 * q) * ystride + ch * 32 + t]);
+                yv[q] = *reinterpret_cast<const ulonglong2*>(&ys[(lane + 32 * q) * ystride + ch * 32 + t]);
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const float4 xv = *reinterpret_cast<const float4*>(st + u * 32 + t);
+                const ulonglong2 xv = *reinterpret_cast<const ulonglong2*>(st + u * 32 + t);
 #pragma unroll
                 for (int q = 0; q < JN; ++q) {
-                    acc[u][q] = fmaf(xv.x, yv[q].x, acc[u][q]);
-                    acc[u][q] = fmaf(xv.y, yv[q].y, acc[u][q]);
-                    acc[u][q] = fmaf(xv.z, yv[q].z, acc[u][q]);
-                    acc[u][q] = fmaf(xv.w, yv[q].w, acc[u][q]);
+                    lb_fma2(acc[u][q], xv.x, yv[q].x);
+                    lb_fma2(acc[u][q], xv.y, yv[q].y);
                 }
             }
         }
@@ -189,7 +197,8 @@ __device__ __forceinline__ void lb_cost_stream(const float* xc, const float* xn_
             for (int u = 0; u < 8; ++u) {
                 const float xni = xn_c[min(ib * 8 + u, m - 1)];
 #pragma unroll
-                for (int q = 0; q < JN; ++q) cij[u][q] = fmaxf(fmaf(-2.f, acc[u][q], xni + yn[lane + 32 * q]), 0.f);
+                for (int q = 0; q < JN; ++q)
+                    cij[u][q] = fmaxf(fmaf(-2.f, lb_hsum2(acc[u][q]), xni + yn[lane + 32 * q]), 0.f);
             }
             on_block(ib * 8, cij);
         }
@@ -374,7 +383,7 @@ __device__ __forceinline__ float lb_dual_cost(const LbArgs& a, int c, int n, con
 }
 
 template <int JN>
-__global__ void __launch_bounds__(LB_WARPS * 32) k_lb_dual(LbArgs a, DualArgs da) {
+__global__ void __launch_bounds__(LB_WARPS * 32, 1) k_lb_dual(LbArgs a, DualArgs da) {
     extern __shared__ __align__(16) float lb_dyn[];
     const int rows = 32 * JN;
     float* ys = lb_dyn;                                   // rows x ystride
@@ -386,7 +395,8 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_lb_dual(LbArgs a, DualArgs da
     __shared__ int s_cnt;
     __shared__ int s_list[LB_DUAL_KCAP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int d = a.d, m = a.m, K = a.K, cs = da.cstride;
+    const int d = a.d, m = a.m, K = a.K;
+    constexpr int cs = 32 * JN + 1;  // cost row stride (odd: rows fall in distinct banks)
     float* Cw = wbase + (size_t)warp * (LB_DUAL_MMAX * cs + 2 * LB_DUAL_MMAX + rows);
     float* ring = lb_dyn + a.ring_off + (size_t)warp * LB_XS * LB_XSTAGE;
     float* Fa = Cw + LB_DUAL_MMAX * cs;   // F_i + log2 v_i (v_i > 0), else -inf
@@ -497,76 +507,125 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_lb_dual(LbArgs a, DualArgs da
             // Each log-sum-exp is shifted by the previous iteration's value of
             // the same potential (its sum of powers is then near 1); a sum
             // outside [2^-100, 2^100] is taken again with the exact maximum.
+            // F_i from its row's sum (sh: the shift the sum was taken with)
+            auto f_finish = [&](int i, float sh, float sum, float lwi) {
+                if (!(sum >= 0x1p-100f && sum <= 0x1p100f)) {
+                    const float* ci = Cw + i * cs;
+                    sh = -3.0e38f;
+                    for (int j = 0; j < n; ++j) sh = fmaxf(sh, fmaf(-sc, ci[j], Gb[j]));
+                    sum = 0.f;
+                    for (int j = 0; j < n; ++j) sum += lb_ex2(fmaf(-sc, ci[j], Gb[j]) - sh);
+                }
+                const float F = -(sh + lb_lg2(sum));
+                Fs[i] = F;
+                Fa[i] = lwi + F;
+            };
             float dual = 0.f;
             bool early = false;
             for (int it = 0; sc > 0.f && it < da.iters; ++it) {
-                // F_i = -log2 sum_j 2^(G_j + log2 u_j - sc C_ij)
-#pragma unroll
-                for (int p = 0; p < 2; ++p) {
-                    const int i = lane + 32 * p;
-                    if (i < m) {
-                        const float* ci = Cw + i * cs;
-                        float sh = -Fs[i];
-                        float sum = 0.f;
-                        for (int j = 0; j < n; ++j) sum += lb_ex2(fmaf(-sc, ci[j], Gb[j]) - sh);
-                        if (!(sum >= 0x1p-100f && sum <= 0x1p100f)) {
-                            sh = -3.0e38f;
-                            for (int j = 0; j < n; ++j) sh = fmaxf(sh, fmaf(-sc, ci[j], Gb[j]));
-                            sum = 0.f;
-                            for (int j = 0; j < n; ++j) sum += lb_ex2(fmaf(-sc, ci[j], Gb[j]) - sh);
-                        }
-                        const float F = -(sh + lb_lg2(sum));
-                        Fs[i] = F;
-                        Fa[i] = lw[p] + F;
+                // F_i = -log2 sum_j 2^(G_j + log2 u_j - sc C_ij): lanes own
+                // rows i = lane (and lane + 32); several partial sums per row
+                // keep the chains of dependent additions short
+                if (m > 32) {
+                    const int i1 = lane + 32;
+                    const bool h1 = i1 < m;
+                    const float* c0 = Cw + lane * cs;
+                    const float* c1 = Cw + (h1 ? i1 : lane) * cs;
+                    const float sh0 = -Fs[lane], sh1 = -Fs[h1 ? i1 : lane];
+                    float s0a = 0.f, s0b = 0.f, s1a = 0.f, s1b = 0.f;
+                    int j = 0;
+                    for (; j + 1 < n; j += 2) {
+                        const float g0 = Gb[j], g1 = Gb[j + 1];
+                        s0a += lb_ex2(fmaf(-sc, c0[j], g0) - sh0);
+                        s1a += lb_ex2(fmaf(-sc, c1[j], g0) - sh1);
+                        s0b += lb_ex2(fmaf(-sc, c0[j + 1], g1) - sh0);
+                        s1b += lb_ex2(fmaf(-sc, c1[j + 1], g1) - sh1);
                     }
+                    if (j < n) {
+                        const float g0 = Gb[j];
+                        s0a += lb_ex2(fmaf(-sc, c0[j], g0) - sh0);
+                        s1a += lb_ex2(fmaf(-sc, c1[j], g0) - sh1);
+                    }
+                    f_finish(lane, sh0, s0a + s0b, lw[0]);
+                    if (h1) f_finish(i1, sh1, s1a + s1b, lw[1]);
+                } else {
+                    const int i0 = lane < m ? lane : 0;  // lanes past m: row 0, result unused
+                    const float* c0 = Cw + i0 * cs;
+                    const float sh0 = lane < m ? -Fs[lane] : 0.f;
+                    float s[4] = {0.f, 0.f, 0.f, 0.f};
+                    int j = 0;
+                    for (; j + 3 < n; j += 4) {
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) s[t] += lb_ex2(fmaf(-sc, c0[j + t], Gb[j + t]) - sh0);
+                    }
+                    for (; j < n; ++j) s[0] += lb_ex2(fmaf(-sc, c0[j], Gb[j]) - sh0);
+                    if (lane < m) f_finish(lane, sh0, (s[0] + s[1]) + (s[2] + s[3]), lw[0]);
                 }
                 __syncwarp();
-                // G_j = -log2 sum_i 2^(F_i + log2 v_i - sc C_ij) for u_j > 0:
-                // lanes take i = lane, lane + 32; a warp sum per column, four
-                // columns at a time
-                for (int j0 = 0; j0 < n; j0 += 4) {
-                    float sh[4], part[4];
+                // G_j = -log2 sum_i 2^(F_i + log2 v_i - sc C_ij) for u_j > 0.
+                // A lane per column for the first 32 floor(n / 32) columns
+                // (four partial sums over i, no shuffles) ...
+                const int nfull = n & ~31;
+                for (int jb = 0; jb < nfull; jb += 32) {
+                    const int j = jb + lane;
+                    const float* cj = Cw + j;
+                    const float sh = ly[j] - Gb[j];  // minus the previous G_j
+                    float s[4] = {0.f, 0.f, 0.f, 0.f};
+                    int i = 0;
+                    for (; i + 3 < m; i += 4) {
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const int j = min(j0 + t, n - 1);
-                        sh[t] = -(Gb[j] - ly[j]);
+                        for (int t = 0; t < 4; ++t) s[t] += lb_ex2(fmaf(-sc, cj[(i + t) * cs], Fa[i + t]) - sh);
+                    }
+                    for (; i < m; ++i) s[0] += lb_ex2(fmaf(-sc, cj[i * cs], Fa[i]) - sh);
+                    float sum = (s[0] + s[1]) + (s[2] + s[3]), s2 = sh;
+                    if (uy[j] > 0.f) {
+                        if (!(sum >= 0x1p-100f && sum <= 0x1p100f)) {
+                            s2 = -3.0e38f;
+                            for (int i2 = 0; i2 < m; ++i2) s2 = fmaxf(s2, fmaf(-sc, cj[i2 * cs], Fa[i2]));
+                            sum = 0.f;
+                            for (int i2 = 0; i2 < m; ++i2) sum += lb_ex2(fmaf(-sc, cj[i2 * cs], Fa[i2]) - s2);
+                        }
+                        Gb[j] = -(s2 + lb_lg2(sum)) + ly[j];
+                    }
+                }
+                // ... and gs lanes per column for the rest (rem gs <= 32): each
+                // lane sums a contiguous block of rows, then a butterfly sum
+                // within its group of gs lanes (the same value on all of them)
+                const int rem = n - nfull;
+                if (rem > 0) {
+                    int lg = 5;
+                    while ((rem << lg) > 32) --lg;
+                    const int gs = 1 << lg;
+                    const int g = lane >> lg, il = lane & (gs - 1);
+                    const bool act = g < rem;
+                    const int j = nfull + (act ? g : 0);  // idle groups read a real column
+                    const int rpl = (m + gs - 1) >> lg;
+                    const int ib = min(m, il * rpl), ie = min(m, ib + rpl);
+                    const float* cj = Cw + j;
+                    const float sh = ly[j] - Gb[j];
+                    float s0 = 0.f, s1 = 0.f;
+                    int i = ib;
+                    for (; i + 1 < ie; i += 2) {
+                        s0 += lb_ex2(fmaf(-sc, cj[i * cs], Fa[i]) - sh);
+                        s1 += lb_ex2(fmaf(-sc, cj[(i + 1) * cs], Fa[i + 1]) - sh);
+                    }
+                    if (i < ie) s0 += lb_ex2(fmaf(-sc, cj[i * cs], Fa[i]) - sh);
+                    float sum = s0 + s1, s2 = sh;
+                    for (int o = gs >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                    const bool live = act && uy[j] > 0.f;
+                    if (__any_sync(0xffffffffu, live && !(sum >= 0x1p-100f && sum <= 0x1p100f))) {
+                        float mx = -3.0e38f;
+                        for (int i2 = ib; i2 < ie; ++i2) mx = fmaxf(mx, fmaf(-sc, cj[i2 * cs], Fa[i2]));
+                        for (int o = gs >> 1; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
                         float v = 0.f;
-#pragma unroll
-                        for (int p = 0; p < 2; ++p) {
-                            const int i = lane + 32 * p;
-                            if (i < m) v += lb_ex2(fmaf(-sc, Cw[i * cs + j], Fa[i]) - sh[t]);
+                        for (int i2 = ib; i2 < ie; ++i2) v += lb_ex2(fmaf(-sc, cj[i2 * cs], Fa[i2]) - mx);
+                        for (int o = gs >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        if (!(sum >= 0x1p-100f && sum <= 0x1p100f)) {
+                            s2 = mx;
+                            sum = v;
                         }
-                        part[t] = v;
                     }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                        for (int t = 0; t < 4; ++t) part[t] += __shfl_xor_sync(0xffffffffu, part[t], o);
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const int j = j0 + t;
-                        if (j >= n || !(uy[j] > 0.f)) continue;
-                        float sum = part[t], s2 = sh[t];
-                        // (every lane holds the sum, up to the order of its terms: decide together)
-                        if (__any_sync(0xffffffffu, !(sum >= 0x1p-100f && sum <= 0x1p100f))) {
-                            float mx = -3.0e38f;
-#pragma unroll
-                            for (int p = 0; p < 2; ++p) {
-                                const int i = lane + 32 * p;
-                                if (i < m) mx = fmaxf(mx, fmaf(-sc, Cw[i * cs + j], Fa[i]));
-                            }
-                            s2 = group_max<32>(mx);
-                            float v = 0.f;
-#pragma unroll
-                            for (int p = 0; p < 2; ++p) {
-                                const int i = lane + 32 * p;
-                                if (i < m) v += lb_ex2(fmaf(-sc, Cw[i * cs + j], Fa[i]) - s2);
-                            }
-                            sum = group_sum<32>(v);
-                        }
-                        __syncwarp();  // every lane has read Gb[j] (the shift) before it changes
-                        if (lane == 0) Gb[j] = -(s2 + lb_lg2(sum)) + ly[j];
-                    }
+                    if (live && il == 0) Gb[j] = -(s2 + lb_lg2(sum)) + ly[j];
                 }
                 __syncwarp();
                 // every LB_DUAL_CHECK iterations: stop once the pair is excluded
