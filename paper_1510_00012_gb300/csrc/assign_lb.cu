@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_lb_pairs(LbArgs a) {
 struct DualArgs {
     const int32_t* cand;  // N x r first candidates (solved exactly)
     const float* w2c;     // N x r their values
-    int r, iters, nw, cstride;
+    int r, iters, nw;
     float eps_rel;
 };
 
@@ -887,9 +887,9 @@ int d2_assign_bounded_impl(d2_ctx* ctx, const d2_bags* b, int K, int m, const fl
         da.r = r;
         da.iters = iters;
         da.eps_rel = ctx->dual_eps > 0.f ? ctx->dual_eps : LB_DUAL_EPS;
-        da.cstride = 32 * JN + 1;
+        const int cstride = 32 * JN + 1;  // the kernel's cost row stride (floats)
         const size_t tile = ((size_t)32 * JN * a.ystride + 3 * (size_t)32 * JN) * 4;
-        const size_t per_warp = ((size_t)LB_DUAL_MMAX * da.cstride + 2 * LB_DUAL_MMAX + 32 * JN +
+        const size_t per_warp = ((size_t)LB_DUAL_MMAX * cstride + 2 * LB_DUAL_MMAX + 32 * JN +
                                  (a.vec ? (size_t)LB_XS * LB_XSTAGE : 0)) * 4;
         int optin = 0;
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
@@ -900,7 +900,7 @@ int d2_assign_bounded_impl(d2_ctx* ctx, const d2_bags* b, int K, int m, const fl
             const size_t dsm = tile + (size_t)da.nw * per_warp;
             LbArgs ad = a;  // rings after the per-warp blocks (all sizes are multiples of 4 floats)
             ad.ring_off = (int64_t)(tile / 4) +
-                          (int64_t)da.nw * (LB_DUAL_MMAX * da.cstride + 2 * LB_DUAL_MMAX + 32 * JN);
+                          (int64_t)da.nw * (LB_DUAL_MMAX * cstride + 2 * LB_DUAL_MMAX + 32 * JN);
             const void* dfn = JN == 1 ? (const void*)k_lb_dual<1> : JN == 2 ? (const void*)k_lb_dual<2>
                                                                             : (const void*)k_lb_dual<4>;
             D2_CK(ctx, cudaFuncSetAttribute(dfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
