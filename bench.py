@@ -1042,6 +1042,9 @@ def main():
     ap.add_argument("--no-pruning", action="store_true", help="skip the learned-pruning assignment at scale")
     ap.add_argument("--no-pilot", action="store_true", help="skip the N=64 pilot and the rho0 / R1-R2 study")
     ap.add_argument("--no-docs-rounds", action="store_true", help="skip the two document-workload rounds")
+    ap.add_argument("--dual-iters", type=int, default=None,
+                    help="Sinkhorn iterations of the entropic dual bound in the bounded assignments of the "
+                         "secondary workloads (default: the library's; a positive count also applies below m = 32)")
     ap.add_argument("--docs-n", type=int, default=None, help="document count of --docs (default 200,000)")
     ap.add_argument("--docs", action="store_true",
                     help="also run D2-clustering of the 200k document-like bags (d=300, K=64, m=64)")
@@ -1094,6 +1097,8 @@ def main():
     obj = torch.empty(K, dtype=torch.float64, device=dev)
     opts = d2.badmm_opts(iters=T, tau=W["tau"], cost=args.cost, split_streams=not args.no_split)
     ctx = d2.Context(local)
+    if args.dual_iters is not None:
+        ctx.set_dual_bound(args.dual_iters)
 
     def step(o=opts):
         x.copy_(x0)
@@ -1270,7 +1275,8 @@ def main():
                            "iters": T, "cost_precision": args.cost,
                            "split_streams": not args.no_split, "l2": "inputs larger than L2 (Pi, Lambda, C: %.1f GB per GPU)"
                            % (12 * entries / 1e9),
-                           "parallelism": "independent problem per GPU" if world > 1 else "single GPU"},
+                           "parallelism": "independent problem per GPU" if world > 1 else "single GPU"}
+                          | ({"dual_bound_iters": args.dual_iters} if args.dual_iters is not None else {}),
                 "roofline": roof, "cost_roofline": cost_roof, "cost_variants": variants,
                 "sweep_autotune": ctx.sweep_tuning(m), "grouped_two_streams": grouped,
                 "kernel_breakdown_ms_per_step": breakdown, "cpu_baseline": cpu,

@@ -227,7 +227,7 @@ int d2_set_flow_store(d2_ctx* ctx, int32_t store, int32_t pool_cap);
  * c-transform; the dual objective is then a lower bound on W^2 that replaces
  * the cheap one when larger, so fewer pairs need the exact solve (every 10
  * iterations the bound is checked and the pair stops once excluded).  Applies
- * for m <= 64.  iters = -1 (default): 30 iterations when m >= 32, none below;
+ * for m <= 64.  iters = -1 (default): 40 iterations when m >= 32, none below;
  * 0: off.  eps_rel = 0: the default 0.05.  Returns D2_EINVAL for iters
  * outside -1..10000 or eps_rel outside [0, 100]. */
 int d2_set_dual_bound(d2_ctx* ctx, int32_t iters, float eps_rel);

@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_lb_pairs(LbArgs a) {
 // points in the F update and bag points in the G update.
 #define LB_DUAL_MMAX 64
 #define LB_DUAL_KCAP 1024  // centroids listed per round of a bag
-#define LB_DUAL_ITERS 30    // Sinkhorn iterations by default (m >= 32)
+#define LB_DUAL_ITERS 40    // Sinkhorn iterations by default (m >= 32)
 #define LB_DUAL_EPS 0.05f   // eps as a fraction of the pair's mean cost
 #define LB_DUAL_CHECK 10    // iterations between checks of the bound against the threshold
 
