@@ -27,7 +27,9 @@ MASK64 = (1 << 64) - 1
 
 
 def splitmix64(state):
-    """One SplitMix64 step: returns (new_state, output), all arithmetic mod 2^64."""
+    """One SplitMix64 step (Steele, Lea & Flood, OOPSLA 2014): returns
+    (new_state, output), all arithmetic mod 2^64.  The generator of the random
+    initialisation of Algorithm 1 (a reading: the paper names none)."""
     state = (state + 0x9E3779B97F4A7C15) & MASK64
     z = state
     z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64

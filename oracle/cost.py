@@ -8,7 +8,8 @@ import numpy as np
 
 
 def cost_matrix(x, y):
-    """C[i, j] = sum_d (x[i, d] - y[j, d])^2, by direct differences in FP64.
+    """C[i, j] = sum_d (x[i, d] - y[j, d])^2, by direct differences in FP64
+    (Section 2: the ground cost with p = 2, C(x, x^(k)) of the notation list).
 
     x: (m, d) barycenter support, y: (m_k, d) member support -> (m, m_k).
     """

@@ -26,11 +26,13 @@ PARAM_NAMES = ("W1", "b1", "W2", "b2", "W3")
 
 
 def mean_of(y, w):
+    """mu_P = sum_j w_j y_j, the mean of the translation identity (module header)."""
     return np.asarray(w, np.float64) @ np.asarray(y, np.float64)
 
 
 def embed(params, y, w, want_cache=False):
-    """f(P) for one distribution; params hold float arrays W1 (H,d) b1 (H) W2 (H,H) b2 (H) W3 (E,H)."""
+    """f(P) for one distribution (the embedding of the module header; no paper
+    passage); params hold float arrays W1 (H,d) b1 (H) W2 (H,H) b2 (H) W3 (E,H)."""
     y = np.asarray(y, np.float64)
     w = np.asarray(w, np.float64)
     W1, b1, W2, b2, W3 = (np.asarray(params[k], np.float64) for k in PARAM_NAMES)
@@ -48,7 +50,8 @@ def embed(params, y, w, want_cache=False):
 
 
 def embed_backward(params, cache, df):
-    """Gradients of <df, f(P)> with respect to the parameters (same names)."""
+    """Gradients of <df, f(P)> with respect to the parameters (same names), by
+    the chain rule through the embedding of the module header."""
     W1, b1, W2, b2, W3 = (np.asarray(params[k], np.float64) for k in PARAM_NAMES)
     g, w, h2, a2, h1, a1, u = (cache[k] for k in ("g", "w", "h2", "a2", "h1", "a1", "u"))
     gW3 = np.outer(df, g)
@@ -65,7 +68,8 @@ def embed_backward(params, cache, df):
 
 
 def pair_loss_and_grad(params, bags, cents, pairs, targets):
-    """Loss L and its gradient for pairs (bag index a, centroid index q).
+    """Loss L of the module header and its gradient for pairs (bag index a,
+    centroid index q).
 
     bags, cents: lists of (y, w); targets: exact W^2 values of the pairs.
     """
@@ -97,7 +101,8 @@ def pair_loss_and_grad(params, bags, cents, pairs, targets):
 
 
 def predict(params, bag, cents):
-    """What^2(P, Q_i) for every centroid, and the exact mean terms."""
+    """What^2(P, Q_i) for every centroid (the predictor of the module header),
+    and the exact mean terms."""
     fP = embed(params, *bag)
     muP = mean_of(*bag)
     pred, mean_term = [], []
@@ -111,7 +116,9 @@ def predict(params, bag, cents):
 
 
 def prune_assign_one(pred, mean_term, exact_fn, r, delta):
-    """Label of one distribution by the pruned rule; exact_fn(i) gives W^2 to centroid i.
+    """Label of one distribution by the pruned rule of the module header (exact
+    W^2 of Eq. primal on the candidates, the margin test, else all K);
+    exact_fn(i) gives W^2 to centroid i.
 
     Returns (label, W^2 to it, fell_back, number of exact solves).
     """

@@ -14,7 +14,8 @@ from .cost import cost_matrix
 
 
 def transport_lp(C, a, b):
-    """Optimal value and plan of min <C, P> s.t. P 1 = a, P^T 1 = b, P >= 0.
+    """Optimal value and plan of min <C, P> s.t. P 1 = a, P^T 1 = b, P >= 0
+    (Eq. primal, Section 2).
 
     a and b are rescaled to the same total (their mean total) so that tiny
     rounding differences in the inputs do not make the LP infeasible.

@@ -3,7 +3,8 @@ baseline infrastructure only, like the rest of this package)."""
 
 
 def barycenter_job(args):
-    """One whole cluster through badmm_barycenter: (members, x0, w0, T, tau)."""
+    """One whole cluster through badmm_barycenter (Algorithm badmm):
+    (members, x0, w0, T, tau)."""
     from .badmm import badmm_barycenter
     members, x0, w0, T, tau = args
     badmm_barycenter(members, x0, w0, T=T, tau=tau)

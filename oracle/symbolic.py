@@ -22,7 +22,8 @@ from .ot import transport_lp
 
 
 def sym_cost(D, s, t):
-    """C[i, j] = D[s_i, t_j]: the cost matrix between symbols s (m) and t (m_k)."""
+    """C[i, j] = D[s_i, t_j]: the cost matrix between symbols s (m) and t (m_k)
+    (Section 2: the given symbol-to-symbol dissimilarity as the ground cost)."""
     D = np.asarray(D, dtype=np.float64)
     return D[np.ix_(np.asarray(s, dtype=np.int64), np.asarray(t, dtype=np.int64))]
 
@@ -41,7 +42,8 @@ def badmm_sym(D, members, s, w0, **kw):
 
 def project_to_symbols(D, s, t, wt):
     """Weights on the symbols s of a distribution (t, wt): each t_j's mass goes
-    to its nearest symbol in s (first minimum of D[s_i, t_j] over i)."""
+    to its nearest symbol in s (first minimum of D[s_i, t_j] over i); the
+    initialisation reading for symbolic supports of the module header."""
     C = sym_cost(D, s, t)
     w = np.zeros(len(s))
     for j in range(len(t)):
@@ -50,7 +52,8 @@ def project_to_symbols(D, s, t, wt):
 
 
 def sym_init_pick(N, K, seed):
-    """K distinct ids of 0..N-1 by the partial Fisher-Yates shuffle driven by SplitMix64."""
+    """K distinct ids of 0..N-1 by the partial Fisher-Yates shuffle driven by
+    SplitMix64: the random initialisation of Algorithm 1 (module header)."""
     ids = list(range(N))
     state = seed & MASK64
     for t in range(K):
