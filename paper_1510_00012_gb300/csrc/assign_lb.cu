@@ -257,6 +257,10 @@ __device__ __forceinline__ void lb_cheap_pair(const LbArgs& a, int c, int n, con
     lb1 = group_sum<32>(lb1);
 }
 
+// The cheap bounds LB1, LB2 (the LP's one-sided relaxations) and LB3 (the
+// means) of every (bag, centroid) pair on the CUDA cores: one CTA per bag
+// (grid-stride) with the bag's rows in shared memory, warp w taking the
+// centroids w, w + LB_WARPS, ...; writes max(LB1, LB2, LB3) to lb.
 template <int JN>
 __global__ void __launch_bounds__(LB_WARPS * 32) k_lb_pairs(LbArgs a) {
     extern __shared__ __align__(16) float lb_dyn[];
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_lb_pairs(LbArgs a) {
     float* uy = yn + rows;                                // rows
     float* mp = uy + rows;                                // d
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int d = a.d, m = a.m, K = a.K;
+    const int d = a.d, K = a.K;
     // the warp's ring for streamed centroid rows (16-byte aligned: the host
     // pads the tile to a multiple of 4 floats)
     float* ring = lb_dyn + a.ring_off + (size_t)warp * LB_XS * LB_XSTAGE;
@@ -382,6 +386,15 @@ __device__ __forceinline__ float lb_dual_cost(const LbArgs& a, int c, int n, con
     return group_sum<32>(csum);
 }
 
+// The entropic dual bound for the pairs that the cheap bounds leave above
+// each bag's threshold (the best exact value of its first candidates, with
+// the slack).  One CTA per bag (grid-stride), the bag's rows in shared
+// memory; the bag's listed pairs are dealt to the da.nw warps in turn.  Per
+// pair a warp builds the m x m_k cost matrix in its own shared memory, runs
+// the Sinkhorn iterations in log2 units (checking the bound every
+// LB_DUAL_CHECK iterations), and takes the larger of the two c-transformed
+// dual objectives of Eq. (primal)'s dual, which never exceeds W^2; it
+// replaces the pair's bound in lb when larger.
 template <int JN>
 __global__ void __launch_bounds__(LB_WARPS * 32, 1) k_lb_dual(LbArgs a, DualArgs da) {
     extern __shared__ __align__(16) float lb_dyn[];
